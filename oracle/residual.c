@@ -1,0 +1,473 @@
+/*
+ * Oracle FR residual R(q) for the compressible Navier-Stokes equations
+ * (TEST INFRASTRUCTURE ONLY; shares no code with the CUDA library).
+ *
+ * Eq. (1): dq/dt + div f = 0, f = f_inv(q) - f_visc(q, grad q).  The semi-discrete
+ * operator is used with the sign R = -div f so that dq/dt = R, which is the sign the
+ * ESDIRK (Eq. 2), Rosenbrock (Eq. 3) and Jacobian-vector (Eq. 8) formulas need.
+ * Spatial discretisation: flux reconstruction (Sec. 2.1) on tensor-product elements with
+ * Gauss-Legendre solution points and DG (Radau) correction functions; Rusanov common
+ * inviscid flux; BR2 common viscous flux.  Stages:
+ *   1 interpolate q to the flux points of every element
+ *   2 per face-point pair: common solution qs = (qL+qR)/2, jumps dq = qs - q_side
+ *   3 per element: corrected gradient at solution points; face gradient traces
+ *     (uncorrected) plus the BR2 face lifting eta g'(face) dq in the face-normal
+ *     reference direction
+ *   4 per face-point pair: common normal flux  Rusanov(qL,qR,n) - f_v(qs, avg grad).n
+ *   5 per element: transformed flux, divergence with FR corrections, R = -div / J.
+ * Arithmetic convention: see oracle.h.
+ */
+#include <math.h>
+#include <string.h>
+#include <stdlib.h>
+#include "oracle.h"
+
+#define NVMAX 5
+#define NPMAX (OR_MAXN * OR_MAXN * OR_MAXN)
+
+/* ---------------------------------------------------------------- indexing */
+static int sp_idx(int n, int d, const int *ii) {
+    return d == 2 ? ii[0] + n * ii[1] : ii[0] + n * (ii[1] + n * ii[2]);
+}
+static void sp_coords(int n, int d, int i, int *ii) {
+    ii[0] = i % n; ii[1] = (i / n) % n; ii[2] = (d == 3) ? i / (n * n) : 0;
+}
+static void tang_dirs(int d, int df, int *td) {
+    int j = 0;
+    for (int c = 0; c < d; ++c) if (c != df) td[j++] = c;
+}
+/* face point k -> normal dir df, side s, coordinates ii (ii[df] left unset) */
+static void fp_decode(int n, int d, int nf1, int k, int *df, int *s, int *ii) {
+    int f = k / nf1, t = k % nf1, td[2] = {0, 0};
+    *df = f / 2; *s = f % 2;
+    tang_dirs(d, *df, td);
+    ii[0] = ii[1] = ii[2] = 0;
+    ii[td[0]] = t % n;
+    if (d == 3) ii[td[1]] = t / n;
+}
+static int fp_encode(int n, int d, int nf1, int df, int s, const int *ii) {
+    int td[2] = {0, 0};
+    tang_dirs(d, df, td);
+    int t = ii[td[0]] + (d == 3 ? n * ii[td[1]] : 0);
+    return (2 * df + s) * nf1 + t;
+}
+
+/* ---------------------------------------------------------------- physics */
+void or_flux_inviscid(const or_ctx *C, const double *q, double f[3][5]) {
+    int d = C->d;
+    double gm1 = C->ph.gamma - 1.0;
+    double rho = q[0], E = q[d + 1], u[3], ke = 0.0;
+    for (int j = 0; j < d; ++j) u[j] = q[1 + j] / rho;
+    for (int j = 0; j < d; ++j) ke = fma(q[1 + j], u[j], ke);
+    double p = gm1 * (E - 0.5 * ke);
+    for (int c = 0; c < d; ++c) {
+        f[c][0] = q[1 + c];
+        for (int j = 0; j < d; ++j) {
+            double t = q[1 + c] * u[j];
+            if (j == c) t = t + p;
+            f[c][1 + j] = t;
+        }
+        f[c][d + 1] = (E + p) * u[c];
+    }
+}
+
+void or_flux_viscous(const or_ctx *C, const double *q, double Q[3][5], int adiabatic, double f[3][5]) {
+    int d = C->d;
+    double gamma = C->ph.gamma, mu = C->ph.mu;
+    double kappa = (gamma * mu) / C->ph.Pr, c23 = 2.0 / 3.0;
+    double rho = q[0], E = q[d + 1], u[3], Er = E / rho;
+    double du[3][3], de[3], tau[3][3];
+    for (int j = 0; j < d; ++j) u[j] = q[1 + j] / rho;
+    for (int j = 0; j < d; ++j)
+        for (int c = 0; c < d; ++c) du[j][c] = (Q[c][1 + j] - u[j] * Q[c][0]) / rho;
+    for (int c = 0; c < d; ++c) {
+        double s = 0.0;
+        for (int j = 0; j < d; ++j) s = fma(u[j], du[j][c], s);
+        de[c] = (Q[c][d + 1] - Er * Q[c][0]) / rho;
+        de[c] = de[c] - s;
+    }
+    double divu = 0.0;
+    for (int j = 0; j < d; ++j) divu = divu + du[j][j];
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double t = du[i][j] + du[j][i];
+            if (i == j) t = t - c23 * divu;
+            tau[i][j] = mu * t;
+        }
+    for (int c = 0; c < d; ++c) {
+        f[c][0] = 0.0;
+        for (int j = 0; j < d; ++j) f[c][1 + j] = tau[j][c];
+        double s = 0.0;
+        for (int j = 0; j < d; ++j) s = fma(u[j], tau[j][c], s);
+        if (!adiabatic) s = s + kappa * de[c];
+        f[c][d + 1] = s;
+    }
+}
+
+/* Rusanov (local Lax-Friedrichs) flux along the scaled normal n */
+void or_rusanov(const or_ctx *C, const double *qL, const double *qR, const double *n, double *F) {
+    int d = C->d, nv = C->nv;
+    double gamma = C->ph.gamma, gm1 = gamma - 1.0;
+    double fL[3][5], fR[3][5];
+    or_flux_inviscid(C, qL, fL);
+    or_flux_inviscid(C, qR, fR);
+    double nn = 0.0;
+    for (int c = 0; c < d; ++c) nn = fma(n[c], n[c], nn);
+    double nmag = sqrt(nn);
+    double lam[2];
+    for (int side = 0; side < 2; ++side) {
+        const double *q = side ? qR : qL;
+        double rho = q[0], E = q[d + 1], u[3], ke = 0.0, vn = 0.0;
+        for (int j = 0; j < d; ++j) u[j] = q[1 + j] / rho;
+        for (int j = 0; j < d; ++j) ke = fma(q[1 + j], u[j], ke);
+        double p = gm1 * (E - 0.5 * ke);
+        double a = sqrt((gamma * p) / rho);
+        for (int c = 0; c < d; ++c) vn = fma(u[c], n[c], vn);
+        lam[side] = fabs(vn) + a * nmag;
+    }
+    double lmax = fmax(lam[0], lam[1]);
+    for (int v = 0; v < nv; ++v) {
+        double FnL = 0.0, FnR = 0.0;
+        for (int c = 0; c < d; ++c) FnL = fma(fL[c][v], n[c], FnL);
+        for (int c = 0; c < d; ++c) FnR = fma(fR[c][v], n[c], FnR);
+        F[v] = 0.5 * (FnL + FnR) - 0.5 * lmax * (qR[v] - qL[v]);
+    }
+}
+
+/* boundary ghost state: 1 = far field (free stream), 2 = no-slip adiabatic wall */
+static void ghost(const or_ctx *C, int bc, const double *qL, double *qR) {
+    int d = C->d;
+    if (bc == 1) {
+        for (int v = 0; v < C->nv; ++v) qR[v] = C->ph.qinf[v];
+    } else {
+        qR[0] = qL[0];
+        for (int j = 0; j < d; ++j) qR[1 + j] = -qL[1 + j];
+        qR[d + 1] = qL[d + 1];
+    }
+}
+
+/* outward scaled normal of the L side of pair P */
+static void pair_normal(const or_ctx *C, const or_level *L, int P, double *nrm) {
+    int d = C->d, E = C->E, df, s, ii[3];
+    int eL = L->pe[2 * P], kL = L->pk[2 * P];
+    fp_decode(L->n, d, L->nf1, kL, &df, &s, ii);
+    for (int c = 0; c < d; ++c) {
+        double v = L->Sf[((size_t)(df * d + c) * L->nfp + kL) * E + eL];
+        nrm[c] = s ? v : -v;
+    }
+}
+
+/* --------------------------------------------------- per-element building blocks */
+/* stage 1: qfe[v][k] from qe[v][i] */
+static void interp_faces(const or_ctx *C, const or_level *L, const double *qe, double *qfe) {
+    int d = C->d, n = L->n, np = L->np, nfp = L->nfp;
+    for (int k = 0; k < nfp; ++k) {
+        int df, s, ii[3];
+        fp_decode(n, d, L->nf1, k, &df, &s, ii);
+        const double *l = s ? L->T.lp : L->T.lm;
+        for (int v = 0; v < C->nv; ++v) {
+            double acc = 0.0;
+            for (int m = 0; m < n; ++m) {
+                ii[df] = m;
+                acc = fma(l[m], qe[v * np + sp_idx(n, d, ii)], acc);
+            }
+            qfe[v * nfp + k] = acc;
+        }
+    }
+}
+
+/* face gradient with BR2 lifting from uncorrected reference gradient gf[dd] at face point k */
+static void face_grad(const or_ctx *C, const or_level *L, int e, int k, double gf[3][5],
+                      const double *dqk, double Qk[3][5]) {
+    int d = C->d, E = C->E, df, s, ii[3];
+    fp_decode(L->n, d, L->nf1, k, &df, &s, ii);
+    double etag = C->ph.eta * (s ? L->T.gRf : L->T.gLf);
+    for (int v = 0; v < C->nv; ++v) {
+        double comp[3];
+        for (int dd = 0; dd < d; ++dd) comp[dd] = gf[dd][v];
+        comp[df] = fma(etag, dqk[v], gf[df][v]);
+        for (int c = 0; c < d; ++c) {
+            double acc = 0.0;
+            for (int dd = 0; dd < d; ++dd)
+                acc = fma(L->Gf[((size_t)(dd * d + c) * L->nfp + k) * E + e], comp[dd], acc);
+            Qk[c][v] = acc;
+        }
+    }
+}
+
+/* stage 3 for element e.  Outputs: Qe[c][v][i] corrected physical gradient,
+ * gfe[dd][v][k] uncorrected reference gradient at face points, Qfe[c][v][k] face gradient
+ * with lifting. */
+static void grad_elem(const or_ctx *C, const or_level *L, int e, const double *qe,
+                      const double *qfe, const double *dqe, double *Qe, double *gfe, double *Qfe) {
+    int d = C->d, E = C->E, n = L->n, np = L->np, nfp = L->nfp, nv = C->nv;
+    const or_tab *T = &L->T;
+    for (int i = 0; i < np; ++i) {
+        int ii[3], jj[3];
+        sp_coords(n, d, i, ii);
+        for (int v = 0; v < nv; ++v) {
+            double gr[3];
+            for (int dd = 0; dd < d; ++dd) {
+                double t = 0.0;
+                memcpy(jj, ii, sizeof jj);
+                for (int m = 0; m < n; ++m) {
+                    jj[dd] = m;
+                    t = fma(T->D[ii[dd]][m], qe[v * np + sp_idx(n, d, jj)], t);
+                }
+                int kL = fp_encode(n, d, L->nf1, dd, 0, ii), kR = fp_encode(n, d, L->nf1, dd, 1, ii);
+                t = fma(T->gLd[ii[dd]], dqe[v * nfp + kL], t);
+                t = fma(T->gRd[ii[dd]], dqe[v * nfp + kR], t);
+                gr[dd] = t;
+            }
+            for (int c = 0; c < d; ++c) {
+                double acc = 0.0;
+                for (int dd = 0; dd < d; ++dd)
+                    acc = fma(L->G[((size_t)(dd * d + c) * np + i) * E + e], gr[dd], acc);
+                Qe[(c * nv + v) * np + i] = acc;
+            }
+        }
+    }
+    for (int k = 0; k < nfp; ++k) {
+        int df, s, ii[3], td[2], jj[3];
+        fp_decode(n, d, L->nf1, k, &df, &s, ii);
+        tang_dirs(d, df, td);
+        const double *dl = s ? T->dlp : T->dlm;
+        double gf[3][5], dqk[5], Qk[3][5];
+        for (int v = 0; v < nv; ++v) {
+            double t = 0.0;
+            memcpy(jj, ii, sizeof jj);
+            for (int m = 0; m < n; ++m) {
+                jj[df] = m;
+                t = fma(dl[m], qe[v * np + sp_idx(n, d, jj)], t);
+            }
+            gf[df][v] = t;
+            for (int j = 0; j < d - 1; ++j) {
+                int tdir = td[j];
+                double u = 0.0;
+                memcpy(jj, ii, sizeof jj);
+                for (int m = 0; m < n; ++m) {
+                    jj[tdir] = m;
+                    u = fma(T->D[ii[tdir]][m], qfe[v * nfp + fp_encode(n, d, L->nf1, df, s, jj)], u);
+                }
+                gf[tdir][v] = u;
+            }
+            dqk[v] = dqe[v * nfp + k];
+        }
+        for (int dd = 0; dd < d; ++dd)
+            for (int v = 0; v < nv; ++v) gfe[(dd * nv + v) * nfp + k] = gf[dd][v];
+        face_grad(C, L, e, k, gf, dqk, Qk);
+        for (int c = 0; c < d; ++c)
+            for (int v = 0; v < nv; ++v) Qfe[(c * nv + v) * nfp + k] = Qk[c][v];
+    }
+}
+
+/* stage 4 for pair P given both traces (qR, QR ignored on boundary pairs) */
+static void pair_flux(const or_ctx *C, const or_level *L, int P, const double *qL, const double *qRin,
+                      double QL[3][5], double QR[3][5], double *F) {
+    int d = C->d, nv = C->nv, bc = L->bc[P];
+    double nrm[3], qR[5], qs[5], Qs[3][5], Fr[5], fv[3][5];
+    pair_normal(C, L, P, nrm);
+    if (bc == 0) memcpy(qR, qRin, sizeof(double) * nv);
+    else ghost(C, bc, qL, qR);
+    for (int v = 0; v < nv; ++v) qs[v] = 0.5 * (qL[v] + qR[v]);
+    for (int c = 0; c < d; ++c)
+        for (int v = 0; v < nv; ++v) Qs[c][v] = (bc == 0) ? 0.5 * (QL[c][v] + QR[c][v]) : QL[c][v];
+    or_rusanov(C, qL, qR, nrm, Fr);
+    or_flux_viscous(C, qs, Qs, bc == 2, fv);
+    for (int v = 0; v < nv; ++v) {
+        double Fv = 0.0;
+        for (int c = 0; c < d; ++c) Fv = fma(fv[c][v], nrm[c], Fv);
+        F[v] = Fr[v] - Fv;
+    }
+}
+
+/* stage 5 for element e: R_e from q_e, Q_e and the common normal fluxes fne[v][k] */
+static void div_elem(const or_ctx *C, const or_level *L, int e, const double *qe, const double *Qe,
+                     const double *fne, double *Re) {
+    int d = C->d, E = C->E, n = L->n, np = L->np, nfp = L->nfp, nv = C->nv;
+    const or_tab *T = &L->T;
+    static double Ft[3 * NVMAX * NPMAX];
+    for (int i = 0; i < np; ++i) {
+        double qi[5], Qi[3][5], fi[3][5], fvi[3][5];
+        for (int v = 0; v < nv; ++v) qi[v] = qe[v * np + i];
+        for (int c = 0; c < d; ++c)
+            for (int v = 0; v < nv; ++v) Qi[c][v] = Qe[(c * nv + v) * np + i];
+        or_flux_inviscid(C, qi, fi);
+        or_flux_viscous(C, qi, Qi, 0, fvi);
+        for (int dd = 0; dd < d; ++dd)
+            for (int v = 0; v < nv; ++v) {
+                double acc = 0.0;
+                for (int c = 0; c < d; ++c)
+                    acc = fma(L->S[((size_t)(dd * d + c) * np + i) * E + e], fi[c][v] - fvi[c][v], acc);
+                Ft[(dd * nv + v) * np + i] = acc;
+            }
+    }
+    for (int i = 0; i < np; ++i) {
+        int ii[3], jj[3];
+        sp_coords(n, d, i, ii);
+        for (int v = 0; v < nv; ++v) {
+            double div = 0.0;
+            for (int dd = 0; dd < d; ++dd) {
+                const double *F = &Ft[(dd * nv + v) * np];
+                double t = 0.0, FL = 0.0, FR = 0.0;
+                memcpy(jj, ii, sizeof jj);
+                for (int m = 0; m < n; ++m) {
+                    jj[dd] = m;
+                    t = fma(T->D[ii[dd]][m], F[sp_idx(n, d, jj)], t);
+                }
+                for (int m = 0; m < n; ++m) {
+                    jj[dd] = m;
+                    FL = fma(T->lm[m], F[sp_idx(n, d, jj)], FL);
+                }
+                for (int m = 0; m < n; ++m) {
+                    jj[dd] = m;
+                    FR = fma(T->lp[m], F[sp_idx(n, d, jj)], FR);
+                }
+                int kL = fp_encode(n, d, L->nf1, dd, 0, ii), kR = fp_encode(n, d, L->nf1, dd, 1, ii);
+                double FsL = -fne[v * nfp + kL], FsR = fne[v * nfp + kR];
+                t = fma(T->gLd[ii[dd]], FsL - FL, t);
+                t = fma(T->gRd[ii[dd]], FsR - FR, t);
+                div = div + t;
+            }
+            Re[v * np + i] = -(div * L->invJ[(size_t)i * E + e]);
+        }
+    }
+}
+
+/* ------------------------------------------------------------ gather/scatter */
+static void gather(const double *g, int nrow, int E, int e, double *loc) {
+    for (int r = 0; r < nrow; ++r) loc[r] = g[(size_t)r * E + e];
+}
+static void scatter(double *g, int nrow, int E, int e, const double *loc) {
+    for (int r = 0; r < nrow; ++r) g[(size_t)r * E + e] = loc[r];
+}
+
+/* ------------------------------------------------------------ full residual */
+void or_residual(or_ctx *C, int l, const double *q, double *R) {
+    or_level *L = &C->L[l];
+    int d = C->d, E = C->E, nv = C->nv, np = L->np, nfp = L->nfp;
+    static double qe[NVMAX * NPMAX], qfe[NVMAX * NPMAX], dqe[NVMAX * NPMAX];
+    static double Qe[3 * NVMAX * NPMAX], gfe[3 * NVMAX * NPMAX], Qfe[3 * NVMAX * NPMAX];
+    static double fne[NVMAX * NPMAX], Re[NVMAX * NPMAX];
+    /* stage 1 */
+    for (int e = 0; e < E; ++e) {
+        gather(q, nv * np, E, e, qe);
+        interp_faces(C, L, qe, qfe);
+        scatter(L->qf, nv * nfp, E, e, qfe);
+    }
+    /* stage 2 */
+    for (int P = 0; P < L->npairs; ++P) {
+        int eL = L->pe[2 * P], kL = L->pk[2 * P], eR = L->pe[2 * P + 1], kR = L->pk[2 * P + 1];
+        double qL[5], qR[5];
+        for (int v = 0; v < nv; ++v) qL[v] = L->qf[((size_t)v * nfp + kL) * E + eL];
+        if (L->bc[P] == 0)
+            for (int v = 0; v < nv; ++v) qR[v] = L->qf[((size_t)v * nfp + kR) * E + eR];
+        else ghost(C, L->bc[P], qL, qR);
+        for (int v = 0; v < nv; ++v) {
+            double qs = 0.5 * (qL[v] + qR[v]);
+            L->dq[((size_t)v * nfp + kL) * E + eL] = qs - qL[v];
+            if (L->bc[P] == 0) L->dq[((size_t)v * nfp + kR) * E + eR] = qs - qR[v];
+        }
+    }
+    /* stage 3 */
+    for (int e = 0; e < E; ++e) {
+        gather(q, nv * np, E, e, qe);
+        gather(L->qf, nv * nfp, E, e, qfe);
+        gather(L->dq, nv * nfp, E, e, dqe);
+        grad_elem(C, L, e, qe, qfe, dqe, Qe, gfe, Qfe);
+        scatter(L->Q, d * nv * np, E, e, Qe);
+        scatter(L->gface, d * nv * nfp, E, e, gfe);
+        scatter(L->Qf, d * nv * nfp, E, e, Qfe);
+    }
+    /* stage 4 */
+    for (int P = 0; P < L->npairs; ++P) {
+        int eL = L->pe[2 * P], kL = L->pk[2 * P], eR = L->pe[2 * P + 1], kR = L->pk[2 * P + 1];
+        int bc = L->bc[P];
+        double qL[5], qR[5], QL[3][5], QR[3][5], F[5];
+        for (int v = 0; v < nv; ++v) {
+            qL[v] = L->qf[((size_t)v * nfp + kL) * E + eL];
+            qR[v] = bc == 0 ? L->qf[((size_t)v * nfp + kR) * E + eR] : 0.0;
+            for (int c = 0; c < d; ++c) {
+                QL[c][v] = L->Qf[((size_t)(c * nv + v) * nfp + kL) * E + eL];
+                QR[c][v] = bc == 0 ? L->Qf[((size_t)(c * nv + v) * nfp + kR) * E + eR] : 0.0;
+            }
+        }
+        pair_flux(C, L, P, qL, qR, QL, QR, F);
+        for (int v = 0; v < nv; ++v) {
+            L->fn[((size_t)v * nfp + kL) * E + eL] = F[v];
+            if (bc == 0) L->fn[((size_t)v * nfp + kR) * E + eR] = -F[v];
+        }
+    }
+    /* stage 5 */
+    for (int e = 0; e < E; ++e) {
+        gather(q, nv * np, E, e, qe);
+        gather(L->Q, d * nv * np, E, e, Qe);
+        gather(L->fn, nv * nfp, E, e, fne);
+        div_elem(C, L, e, qe, Qe, fne, Re);
+        scatter(R, nv * np, E, e, Re);
+    }
+}
+
+/* --------------------------------------------------------- element-local residual
+ * R restricted to element e when only q_e is replaced by qe_new and every other
+ * element keeps its value in q: exactly the stages above evaluated on e and on the
+ * neighbour traces that touch e (the neighbour's BR2 lifting depends on q_e through the
+ * common solution, so it is recomputed).  Requires or_residual(C, l, q, .) to have been
+ * called on the same q (it leaves the neighbours' traces in the level scratch). */
+void or_elem_residual(or_ctx *C, int l, const double *q, int e, const double *qe_new, double *Re) {
+    or_level *L = &C->L[l];
+    int d = C->d, E = C->E, nv = C->nv, nfp = L->nfp;
+    (void)q;
+    static double qfe[NVMAX * NPMAX], dqe[NVMAX * NPMAX];
+    static double Qe[3 * NVMAX * NPMAX], gfe[3 * NVMAX * NPMAX], Qfe[3 * NVMAX * NPMAX];
+    static double fne[NVMAX * NPMAX];
+    static double dqn[NVMAX * NPMAX];   /* neighbour-side jump at e's face point k */
+    interp_faces(C, L, qe_new, qfe);
+    for (int k = 0; k < nfp; ++k) {
+        int P = L->epair[(size_t)k * E + e];
+        int bc = L->bc[P];
+        int isL = (L->pe[2 * P] == e && L->pk[2 * P] == k);
+        double qme[5], qo[5];
+        for (int v = 0; v < nv; ++v) qme[v] = qfe[v * nfp + k];
+        if (bc == 0) {
+            int eo = isL ? L->pe[2 * P + 1] : L->pe[2 * P];
+            int ko = isL ? L->pk[2 * P + 1] : L->pk[2 * P];
+            for (int v = 0; v < nv; ++v) qo[v] = L->qf[((size_t)v * nfp + ko) * E + eo];
+        } else {
+            ghost(C, bc, qme, qo);
+        }
+        for (int v = 0; v < nv; ++v) {
+            double qs = 0.5 * (qme[v] + qo[v]);
+            dqe[v * nfp + k] = qs - qme[v];
+            dqn[v * nfp + k] = qs - qo[v];
+        }
+    }
+    grad_elem(C, L, e, qe_new, qfe, dqe, Qe, gfe, Qfe);
+    for (int k = 0; k < nfp; ++k) {
+        int P = L->epair[(size_t)k * E + e];
+        int bc = L->bc[P];
+        int isL = (L->pe[2 * P] == e && L->pk[2 * P] == k);
+        double qme[5], qo[5], Qme[3][5], Qo[3][5], F[5];
+        for (int v = 0; v < nv; ++v) {
+            qme[v] = qfe[v * nfp + k];
+            for (int c = 0; c < d; ++c) Qme[c][v] = Qfe[(c * nv + v) * nfp + k];
+        }
+        if (bc == 0) {
+            int eo = isL ? L->pe[2 * P + 1] : L->pe[2 * P];
+            int ko = isL ? L->pk[2 * P + 1] : L->pk[2 * P];
+            double gf[3][5], dqk[5];
+            for (int v = 0; v < nv; ++v) {
+                qo[v] = L->qf[((size_t)v * nfp + ko) * E + eo];
+                for (int dd = 0; dd < d; ++dd) gf[dd][v] = L->gface[((size_t)(dd * nv + v) * nfp + ko) * E + eo];
+                dqk[v] = dqn[v * nfp + k];
+            }
+            face_grad(C, L, eo, ko, gf, dqk, Qo);
+        } else {
+            for (int v = 0; v < nv; ++v) qo[v] = 0.0;
+        }
+        if (isL) pair_flux(C, L, P, qme, qo, Qme, Qo, F);
+        else pair_flux(C, L, P, qo, qme, Qo, Qme, F);
+        for (int v = 0; v < nv; ++v) fne[v * nfp + k] = isL ? F[v] : -F[v];
+    }
+    div_elem(C, L, e, qe_new, Qe, fne, Re);
+}

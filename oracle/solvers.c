@@ -1,0 +1,398 @@
+/*
+ * Oracle solvers (TEST INFRASTRUCTURE ONLY; shares no code with the CUDA library):
+ * FD Jacobian-vector product, nonlinear pMG preconditioner, flexible GMRES, ESDIRK with
+ * pseudo-transient continuation, Rosenbrock-Wanner steps and steady PTC with SER.
+ *
+ *  - Jv (Eq. 8):  A v = shift v - (R(q + eps v) - R(q)) / eps,  eps fixed (1e-6).
+ *  - pMG preconditioner (Sec. 3.2, Eqs. 22-26, with the V-cycle of Sec. 3.1,
+ *    Eqs. 11-16): Y approximates A^{-1} X by pseudo-time marching the nonlinear system
+ *    0 = X + R(qh) - c qh - R(q) + c q.  On level l the system is F_l(qh) = S_l with
+ *    F_l(y) = c y - R_l(y); each smoothing step is the linearised backward-Euler pseudo
+ *    step with element-diagonal blocks M_l = (1/dtau* + c) I - J_l,ee:
+ *        qh <- qh + M_l^{-1} (S_l - F_l(qh)).
+ *    S_l - F_l(qh) is evaluated as  d_l - (c (qh - b_l) - (R_l(qh) - R_l(b_l))),  where
+ *    b_0 = q, d_0 = X and, on coarser levels, b_{l+1} = Gamma qh_l^a and
+ *    d_{l+1} = Gamma (S_l - F_l(qh_l^a)) (Eqs. 13-15); grouping the differences keeps
+ *    the small preconditioned vector out of the cancellation.  When qh = b the
+ *    difference terms are exact zeros, so the first smoothing step on a level uses d_l
+ *    directly.  One V-cycle per application; Y = qh_0 - q.
+ *  - FGMRES (right preconditioned, restarted, modified Gram-Schmidt; true residual at
+ *    every restart), stopping at ||b - A x|| <= tol ||b||.  The FD product of Eq. (8) is
+ *    only ever applied to unit 2-norm directions, as it is for unpreconditioned Krylov
+ *    vectors: each preconditioned direction Z_j = P^{-1} V_j is normalised (FGMRES is
+ *    invariant to the scale of Z_j) and A x is evaluated as ||x|| A (x/||x||).
+ *  - ESDIRK stage equation (Eq. 5) solved by PTC/Newton (Eqs. 6-7):
+ *        F(q) = (q - s_i) / (a_ii dt) - R(q),  s_i = q^n + dt sum_{j<i} a_ij R(q_j);
+ *    converged when RMS(a_ii dt F) <= tol.  q^{n+1} = q^n + dt sum_i b_i R(q_i) (Eq. 2).
+ *  - ROW (Eq. 3): (I/(gamma dt) - dR/dq(q^n)) Y_i = R(q^n + sum a_ij Y_j) + (1/dt) sum c_ij Y_j;
+ *    q^{n+1} = q^n + sum m_j Y_j.
+ *  - Steady PTC with SER (Eq. 10, read with the ratio ||F^k|| / ||F^{k+1}|| so that the
+ *    pseudo step grows as the residual falls).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include "oracle.h"
+
+void or_residual(or_ctx *C, int l, const double *q, double *R);
+void or_elem_blocks(or_ctx *C, int l, const double *q, double shift, const int *elems, int ne, double *M);
+void or_lu_factor(int n, double *A, int *piv);
+void or_lu_solve(int n, const double *A, const int *piv, double *b);
+void or_restrict(or_ctx *C, int l, const double *x0, double *x1);
+void or_prolong(or_ctx *C, int l, const double *x1, double *x0);
+
+/* ------------------------------------------------------------------ vectors */
+static size_t vlen(const or_ctx *C, int l) { return (size_t)C->nv * C->L[l].np * C->E; }
+static double dot(size_t N, const double *a, const double *b) {
+    double s = 0.0;
+    for (size_t i = 0; i < N; ++i) s = fma(a[i], b[i], s);
+    return s;
+}
+
+/* ------------------------------------------------------------------ Jv, Eq. (8) */
+void or_jvp(or_ctx *C, const double *q, const double *Rq, const double *v, double eps, double shift, double *Av) {
+    size_t N = vlen(C, 0);
+    double *qp = malloc(sizeof(double) * N), *Rp = malloc(sizeof(double) * N);
+    for (size_t i = 0; i < N; ++i) qp[i] = q[i] + eps * v[i];
+    or_residual(C, 0, qp, Rp);
+    for (size_t i = 0; i < N; ++i) Av[i] = shift * v[i] - (Rp[i] - Rq[i]) / eps;
+    free(qp); free(Rp);
+}
+
+/* ------------------------------------------------------------------ pMG */
+typedef struct {
+    int nlev, nsmooth[OR_MAXLEV];
+    double c, inv_dtau_star;
+    double *M[OR_MAXLEV];
+    int *piv[OR_MAXLEV];
+    int ready;
+} or_pmg;
+
+static or_pmg g_pmg;
+
+static void pmg_free(void) {
+    for (int l = 0; l < OR_MAXLEV; ++l) { free(g_pmg.M[l]); free(g_pmg.piv[l]); g_pmg.M[l] = 0; g_pmg.piv[l] = 0; }
+    g_pmg.ready = 0;
+}
+
+/* blocks at the reference state q_ref (restricted level by level) and their LU factors */
+void or_pmg_setup(or_ctx *C, const double *q_ref, int nlev, const int *nsmooth, double c, double inv_dtau_star) {
+    pmg_free();
+    g_pmg.nlev = nlev; g_pmg.c = c; g_pmg.inv_dtau_star = inv_dtau_star;
+    for (int l = 0; l < nlev; ++l) g_pmg.nsmooth[l] = nsmooth[l];
+    int E = C->E;
+    int *all = malloc(sizeof(int) * E);
+    for (int e = 0; e < E; ++e) all[e] = e;
+    double *qr = malloc(sizeof(double) * vlen(C, 0));
+    memcpy(qr, q_ref, sizeof(double) * vlen(C, 0));
+    for (int l = 0; l < nlev; ++l) {
+        int nd = C->nv * C->L[l].np;
+        g_pmg.M[l] = malloc(sizeof(double) * (size_t)nd * nd * E);
+        g_pmg.piv[l] = malloc(sizeof(int) * (size_t)nd * E);
+        or_elem_blocks(C, l, qr, inv_dtau_star + c, all, E, g_pmg.M[l]);
+        for (int e = 0; e < E; ++e)
+            or_lu_factor(nd, &g_pmg.M[l][(size_t)e * nd * nd], &g_pmg.piv[l][(size_t)e * nd]);
+        if (l + 1 < nlev) {
+            double *qn = malloc(sizeof(double) * vlen(C, l + 1));
+            or_restrict(C, l, qr, qn);
+            free(qr);
+            qr = qn;
+        }
+    }
+    free(qr); free(all);
+    g_pmg.ready = 1;
+}
+
+/* apply M_l^{-1} element by element, in place on x[v][i][e] */
+static void block_solve(or_ctx *C, int l, double *x) {
+    int E = C->E, nd = C->nv * C->L[l].np;
+    double *b = malloc(sizeof(double) * nd);
+    for (int e = 0; e < E; ++e) {
+        for (int r = 0; r < nd; ++r) b[r] = x[(size_t)r * E + e];
+        or_lu_solve(nd, &g_pmg.M[l][(size_t)e * nd * nd], &g_pmg.piv[l][(size_t)e * nd], b);
+        for (int r = 0; r < nd; ++r) x[(size_t)r * E + e] = b[r];
+    }
+    free(b);
+}
+void or_block_solve(or_ctx *C, int l, double *x) { block_solve(C, l, x); }
+
+/* rhs = d - (c (qh - b) - (Rqh - Rb)) */
+static void pmg_rhs(size_t N, double c, const double *d, const double *qh, const double *b,
+                    const double *Rqh, const double *Rb, double *rhs) {
+    for (size_t i = 0; i < N; ++i) {
+        double t1 = qh[i] - b[i], t2 = Rqh[i] - Rb[i];
+        rhs[i] = d[i] - (c * t1 - t2);
+    }
+}
+
+static void smooth(or_ctx *C, int l, int nsteps, const double *b, const double *Rb, const double *d,
+                   double *qh, int first_is_base) {
+    size_t N = vlen(C, l);
+    double *Rqh = malloc(sizeof(double) * N), *rhs = malloc(sizeof(double) * N);
+    for (int s = 0; s < nsteps; ++s) {
+        if (s == 0 && first_is_base) memcpy(rhs, d, sizeof(double) * N);
+        else {
+            or_residual(C, l, qh, Rqh);
+            pmg_rhs(N, g_pmg.c, d, qh, b, Rqh, Rb, rhs);
+        }
+        block_solve(C, l, rhs);
+        for (size_t i = 0; i < N; ++i) qh[i] = qh[i] + rhs[i];
+    }
+    free(Rqh); free(rhs);
+}
+
+static void vcycle(or_ctx *C, int l, const double *b, const double *Rb, const double *d, double *qh) {
+    size_t N = vlen(C, l);
+    int n = g_pmg.nsmooth[l];
+    smooth(C, l, n, b, Rb, d, qh, 1);
+    if (l + 1 >= g_pmg.nlev) return;
+    size_t N1 = vlen(C, l + 1);
+    double *Rqh = malloc(sizeof(double) * N), *r = malloc(sizeof(double) * N);
+    double *b1 = malloc(sizeof(double) * N1), *Rb1 = malloc(sizeof(double) * N1);
+    double *d1 = malloc(sizeof(double) * N1), *qh1 = malloc(sizeof(double) * N1);
+    double *C0 = malloc(sizeof(double) * N);
+    /* defect d_l = S_l - F_l(qh^a), Eq. (13) */
+    if (n == 0) memcpy(r, d, sizeof(double) * N);
+    else {
+        or_residual(C, l, qh, Rqh);
+        pmg_rhs(N, g_pmg.c, d, qh, b, Rqh, Rb, r);
+    }
+    /* restriction and coarse forcing, Eqs. (14)-(15) */
+    or_restrict(C, l, qh, b1);
+    or_restrict(C, l, r, d1);
+    or_residual(C, l + 1, b1, Rb1);
+    memcpy(qh1, b1, sizeof(double) * N1);
+    vcycle(C, l + 1, b1, Rb1, d1, qh1);
+    /* prolongation of the coarse correction, Eq. (16) */
+    for (size_t i = 0; i < N1; ++i) qh1[i] = qh1[i] - b1[i];
+    or_prolong(C, l, qh1, C0);
+    for (size_t i = 0; i < N; ++i) qh[i] = qh[i] + C0[i];
+    /* post-smoothing */
+    smooth(C, l, n, b, Rb, d, qh, 0);
+    free(Rqh); free(r); free(b1); free(Rb1); free(d1); free(qh1); free(C0);
+}
+
+void or_pmg_apply(or_ctx *C, const double *q, const double *Rq, const double *X, double *Y) {
+    size_t N = vlen(C, 0);
+    double *qh = malloc(sizeof(double) * N);
+    memcpy(qh, q, sizeof(double) * N);
+    vcycle(C, 0, q, Rq, X, qh);
+    for (size_t i = 0; i < N; ++i) Y[i] = qh[i] - q[i];
+    free(qh);
+}
+
+/* ------------------------------------------------------------------ FGMRES */
+typedef struct { int iters, restarts; double relres; } or_gmres_stats;
+
+int or_gmres(or_ctx *C, const double *q, const double *Rq, const double *b, double *x,
+             int kdim, double tol, int maxit, double shift, double eps, int use_pmg,
+             or_gmres_stats *st) {
+    size_t N = vlen(C, 0);
+    double **V = malloc(sizeof(double *) * (kdim + 1)), **Z = malloc(sizeof(double *) * kdim);
+    for (int j = 0; j <= kdim; ++j) V[j] = malloc(sizeof(double) * N);
+    for (int j = 0; j < kdim; ++j) Z[j] = malloc(sizeof(double) * N);
+    double *H = calloc((size_t)(kdim + 1) * kdim, sizeof(double));
+    double *cs = malloc(sizeof(double) * kdim), *sn = malloc(sizeof(double) * kdim);
+    double *g = malloc(sizeof(double) * (kdim + 1)), *y = malloc(sizeof(double) * kdim);
+    double *w = malloc(sizeof(double) * N), *r = malloc(sizeof(double) * N);
+    memset(x, 0, sizeof(double) * N);
+    memcpy(r, b, sizeof(double) * N);
+    double bnorm = sqrt(dot(N, b, b)), beta = bnorm;
+    int total = 0, restarts = 0;
+    st->iters = 0; st->restarts = 0; st->relres = 0.0;
+    if (bnorm == 0.0) goto done;
+    for (;;) {
+        for (size_t i = 0; i < N; ++i) V[0][i] = r[i] / beta;
+        for (int j = 0; j <= kdim; ++j) g[j] = 0.0;
+        g[0] = beta;
+        int jj = 0;
+        for (int j = 0; j < kdim; ++j) {
+            if (use_pmg) {
+                or_pmg_apply(C, q, Rq, V[j], Z[j]);
+                double zn = sqrt(dot(N, Z[j], Z[j]));
+                for (size_t t = 0; t < N; ++t) Z[j][t] = Z[j][t] / zn;
+            } else memcpy(Z[j], V[j], sizeof(double) * N);
+            or_jvp(C, q, Rq, Z[j], eps, shift, w);
+            for (int i = 0; i <= j; ++i) {
+                double h = dot(N, w, V[i]);
+                H[i * kdim + j] = h;
+                for (size_t t = 0; t < N; ++t) w[t] = w[t] - h * V[i][t];
+            }
+            double hn = sqrt(dot(N, w, w));
+            H[(j + 1) * kdim + j] = hn;
+            for (size_t t = 0; t < N; ++t) V[j + 1][t] = w[t] / hn;
+            for (int i = 0; i < j; ++i) {
+                double a = H[i * kdim + j], bb = H[(i + 1) * kdim + j];
+                H[i * kdim + j] = cs[i] * a + sn[i] * bb;
+                H[(i + 1) * kdim + j] = -sn[i] * a + cs[i] * bb;
+            }
+            double a = H[j * kdim + j], bb = H[(j + 1) * kdim + j];
+            double rr = hypot(a, bb);
+            cs[j] = a / rr; sn[j] = bb / rr;
+            H[j * kdim + j] = rr; H[(j + 1) * kdim + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++total; jj = j + 1;
+            if (fabs(g[j + 1]) <= tol * bnorm || total >= maxit || hn == 0.0) break;
+        }
+        for (int i = jj - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int k = i + 1; k < jj; ++k) s -= H[i * kdim + k] * y[k];
+            y[i] = s / H[i * kdim + i];
+        }
+        for (int i = 0; i < jj; ++i)
+            for (size_t t = 0; t < N; ++t) x[t] = x[t] + y[i] * Z[i][t];
+        /* A x through the unit direction x/||x|| (the FD step is always eps in 2-norm) */
+        double xn = sqrt(dot(N, x, x));
+        for (size_t t = 0; t < N; ++t) r[t] = x[t] / xn;
+        or_jvp(C, q, Rq, r, eps, shift, w);
+        for (size_t t = 0; t < N; ++t) r[t] = b[t] - xn * w[t];
+        beta = sqrt(dot(N, r, r));
+        if (beta <= tol * bnorm || total >= maxit) break;
+        ++restarts;
+    }
+    st->iters = total; st->restarts = restarts; st->relres = beta / bnorm;
+done:
+    for (int j = 0; j <= kdim; ++j) free(V[j]);
+    for (int j = 0; j < kdim; ++j) free(Z[j]);
+    free(V); free(Z); free(H); free(cs); free(sn); free(g); free(y); free(w); free(r);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ drivers */
+typedef struct {
+    int kdim, maxit_gmres, max_ptc, nlev, nsmooth[OR_MAXLEV], use_pmg;
+    double tol_gmres, tol_newton, eps, dtau, inv_dtau_star;
+} or_solve_opts;
+
+typedef struct { int n_ptc, n_gmres, converged; double final_res; } or_step_stats;
+
+static double rms_scaled(size_t N, double a, const double *F) {
+    double s = 0.0;
+    for (size_t i = 0; i < N; ++i) { double t = a * F[i]; s = fma(t, t, s); }
+    return sqrt(s / (double)N);
+}
+
+/* ESDIRK step, Eqs. (2), (5)-(8); A is s x s row-major, b length s */
+int or_esdirk_step(or_ctx *C, int s, const double *A, const double *bw, double dt, double *q,
+                   const or_solve_opts *o, or_step_stats *st) {
+    size_t N = vlen(C, 0);
+    double *qn = malloc(sizeof(double) * N), *Rs = malloc(sizeof(double) * N * s);
+    double *sv = malloc(sizeof(double) * N), *F = malloc(sizeof(double) * N);
+    double *Rk = malloc(sizeof(double) * N), *dq = malloc(sizeof(double) * N);
+    memcpy(qn, q, sizeof(double) * N);
+    or_residual(C, 0, qn, Rs);
+    memset(st, 0, sizeof(*st));
+    st->converged = 1;
+    double aii = A[1 * s + 1];
+    double c = 1.0 / o->dtau + 1.0 / (aii * dt);
+    if (o->use_pmg) or_pmg_setup(C, qn, o->nlev, o->nsmooth, c, o->inv_dtau_star);
+    for (int i = 1; i < s; ++i) {
+        double adt = A[i * s + i] * dt;
+        for (size_t t = 0; t < N; ++t) {
+            double acc = 0.0;
+            for (int j = 0; j < i; ++j) acc = fma(A[i * s + j], Rs[(size_t)j * N + t], acc);
+            sv[t] = qn[t] + dt * acc;
+        }
+        /* guess q^n */
+        memcpy(q, qn, sizeof(double) * N);
+        int k, conv = 0;
+        double res = 0.0;
+        for (k = 0; k <= o->max_ptc; ++k) {
+            or_residual(C, 0, q, Rk);
+            for (size_t t = 0; t < N; ++t) F[t] = (q[t] - sv[t]) / adt - Rk[t];
+            res = rms_scaled(N, adt, F);
+            if (res <= o->tol_newton) { conv = 1; break; }
+            if (k == o->max_ptc) break;
+            for (size_t t = 0; t < N; ++t) F[t] = -F[t];
+            or_gmres_stats gs;
+            or_gmres(C, q, Rk, F, dq, o->kdim, o->tol_gmres, o->maxit_gmres, c, o->eps, o->use_pmg, &gs);
+            st->n_gmres += gs.iters;
+            for (size_t t = 0; t < N; ++t) q[t] = q[t] + dq[t];
+            st->n_ptc++;
+        }
+        if (!conv) st->converged = 0;
+        st->final_res = res;
+        memcpy(&Rs[(size_t)i * N], Rk, sizeof(double) * N);
+    }
+    for (size_t t = 0; t < N; ++t) {
+        double acc = 0.0;
+        for (int j = 0; j < s; ++j) acc = fma(bw[j], Rs[(size_t)j * N + t], acc);
+        q[t] = qn[t] + dt * acc;
+    }
+    free(qn); free(Rs); free(sv); free(F); free(Rk); free(dq);
+    return st->converged ? 0 : 1;
+}
+
+/* ROW step, Eq. (3): a, cc are the s x s strictly lower transformed coefficients, m the weights */
+int or_row_step(or_ctx *C, int s, double gam, const double *a, const double *cc, const double *m,
+                double dt, double *q, const or_solve_opts *o, or_step_stats *st) {
+    size_t N = vlen(C, 0);
+    double *qn = malloc(sizeof(double) * N), *Rn = malloc(sizeof(double) * N);
+    double *Y = malloc(sizeof(double) * N * s), *qi = malloc(sizeof(double) * N);
+    double *rhs = malloc(sizeof(double) * N), *Ri = malloc(sizeof(double) * N);
+    memcpy(qn, q, sizeof(double) * N);
+    or_residual(C, 0, qn, Rn);
+    memset(st, 0, sizeof(*st));
+    st->converged = 1;
+    double c = 1.0 / (gam * dt);
+    if (o->use_pmg) or_pmg_setup(C, qn, o->nlev, o->nsmooth, c, o->inv_dtau_star);
+    for (int i = 0; i < s; ++i) {
+        for (size_t t = 0; t < N; ++t) {
+            double acc = 0.0;
+            for (int j = 0; j < i; ++j) acc = fma(a[i * s + j], Y[(size_t)j * N + t], acc);
+            qi[t] = qn[t] + acc;
+        }
+        if (i == 0) memcpy(Ri, Rn, sizeof(double) * N);
+        else or_residual(C, 0, qi, Ri);
+        for (size_t t = 0; t < N; ++t) {
+            double acc = 0.0;
+            for (int j = 0; j < i; ++j) acc = fma(cc[i * s + j], Y[(size_t)j * N + t], acc);
+            rhs[t] = Ri[t] + acc / dt;
+        }
+        or_gmres_stats gs;
+        or_gmres(C, qn, Rn, rhs, &Y[(size_t)i * N], o->kdim, o->tol_gmres, o->maxit_gmres, c, o->eps,
+                 o->use_pmg, &gs);
+        st->n_gmres += gs.iters;
+        if (gs.relres > o->tol_gmres) st->converged = 0;
+        st->final_res = gs.relres;
+    }
+    for (size_t t = 0; t < N; ++t) {
+        double acc = 0.0;
+        for (int j = 0; j < s; ++j) acc = fma(m[j], Y[(size_t)j * N + t], acc);
+        q[t] = qn[t] + acc;
+    }
+    free(qn); free(Rn); free(Y); free(qi); free(rhs); free(Ri);
+    return st->converged ? 0 : 1;
+}
+
+/* steady PTC with SER; Eq. (7) without the dt terms, Eq. (10) with the growth reading */
+int or_ptc_steady(or_ctx *C, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
+                  const or_solve_opts *o, or_step_stats *st, double *hist) {
+    size_t N = vlen(C, 0);
+    double *R = malloc(sizeof(double) * N), *dq = malloc(sizeof(double) * N);
+    memset(st, 0, sizeof(*st));
+    or_residual(C, 0, q, R);
+    double r0 = sqrt(dot(N, R, R)), rk = r0, dtau = dtau_init;
+    if (hist) hist[0] = r0;
+    int k;
+    for (k = 0; k < max_it; ++k) {
+        if (rk <= tol_rel * r0) break;
+        double c = 1.0 / dtau;
+        if (o->use_pmg) or_pmg_setup(C, q, o->nlev, o->nsmooth, c, o->inv_dtau_star < 0 ? c : o->inv_dtau_star);
+        or_gmres_stats gs;
+        or_gmres(C, q, R, R, dq, o->kdim, o->tol_gmres, o->maxit_gmres, c, o->eps, o->use_pmg, &gs);
+        st->n_gmres += gs.iters;
+        for (size_t t = 0; t < N; ++t) q[t] = q[t] + dq[t];
+        or_residual(C, 0, q, R);
+        double rn = sqrt(dot(N, R, R));
+        dtau = fmin(dtau * (rk / rn), dtau_max);
+        rk = rn;
+        st->n_ptc++;
+        if (hist) hist[k + 1] = rn;
+    }
+    st->final_res = rk / r0;
+    st->converged = rk <= tol_rel * r0;
+    free(R); free(dq);
+    return st->converged ? 0 : 1;
+}

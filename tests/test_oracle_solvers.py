@@ -1,0 +1,203 @@
+"""Pins of the oracle's solver layer.
+
+  Jv (Eq. 8)         forward-difference error is O(eps) against a central difference
+  element blocks     equal, bit for bit, to the diagonal blocks of the full-residual FD
+                     Jacobian (brute force, column by column)
+  LU                 block solves equal numpy's dense solves
+  pMG (Sec. 3.2)     one fine-level pseudo step with 1/dtau* = 0 is the element-Jacobi
+                     preconditioner diag(A)^{-1} X (the special case the paper notes);
+                     a two-level cycle whose coarse level has the same degree equals the
+                     one-level smoother with 2 n0 + n1 steps; many smoothing steps reach
+                     the fixed point A^{-1} X of the preconditioner's pseudo-time system
+  FGMRES             converges to the dense direct solve of the FD Jacobian system
+  ESDIRK3 / ROS34PW2 order conditions, L-stability, observed order 3 on the NS system
+  steady PTC + SER   converges by 8 orders on a small stretched cylinder mesh
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import tableaux as TB
+from paper_2202_09733_gb300 import workloads as w
+from smooth_state import angled_flow
+
+
+@pytest.fixture(scope="module")
+def small():
+    mesh = w.box2d(3, 3, 10, 10, qg=2, warp=0.1)
+    ph = w.Physics(mu=0.02, qinf=w.freestream(2, 0.3))
+    O = oracle.Oracle(mesh, ph, [2, 1])
+    q = angled_flow(mesh, 2)
+    Rq = O.residual(q)
+    N = q.size
+    Jd = np.zeros((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1e-5
+        Jd[:, j] = (O.residual(q + e.reshape(q.shape)) - O.residual(q - e.reshape(q.shape))).ravel() / 2e-5
+    return dict(mesh=mesh, ph=ph, O=O, q=q, Rq=Rq, J=Jd, N=N)
+
+
+def test_jvp_first_order_in_eps(small):
+    O, q, Rq = small["O"], small["q"], small["Rq"]
+    v = np.random.default_rng(1).standard_normal(q.shape)
+    v /= np.linalg.norm(v)
+    ref = -(small["J"] @ v.ravel())
+    errs = [np.linalg.norm(O.jvp(q, Rq, v, eps, 0.0).ravel() - ref) / np.linalg.norm(ref)
+            for eps in (1e-3, 1e-4, 1e-5)]
+    assert 8.0 < errs[0] / errs[1] < 12.0 and 8.0 < errs[1] / errs[2] < 12.0
+    # shift term enters linearly
+    a1 = O.jvp(q, Rq, v, 1e-6, 0.0)
+    a2 = O.jvp(q, Rq, v, 1e-6, 3.0)
+    assert np.allclose(a2 - a1, 3.0 * v, rtol=0, atol=1e-14)
+
+
+def test_element_blocks_equal_full_jacobian_blocks(small):
+    O, q, Rq = small["O"], small["q"], small["Rq"]
+    nd = q.shape[0] * q.shape[1]
+    for e0 in (0, 4, 8):
+        cols = []
+        for j in range(nd):
+            qq = q.copy().reshape(nd, -1)
+            eps = 1e-7 * max(1.0, abs(qq[j, e0]))
+            qq[j, e0] = qq[j, e0] + eps
+            cols.append((O.residual(qq.reshape(q.shape)) - Rq).reshape(nd, -1)[:, e0] / eps)
+        Mfull = 2.5 * np.eye(nd) - np.stack(cols, axis=1)
+        Mb = O.elem_blocks(q, 2.5, [e0])[0]
+        off = ~np.eye(nd, dtype=bool)
+        assert np.array_equal(Mb[off], Mfull[off])
+        assert np.allclose(np.diag(Mb), np.diag(Mfull), rtol=1e-15, atol=0)
+
+
+def test_block_solve_equals_dense_solve(small):
+    O, q = small["O"], small["q"]
+    c = 3.0
+    O.pmg_setup(q, [1], c, 0.0)
+    M = O.elem_blocks(q, c, np.arange(small["mesh"]["E"]))
+    x = np.random.default_rng(2).standard_normal(q.shape)
+    y = O.block_solve(x)
+    nd = M.shape[1]
+    ref = np.stack([np.linalg.solve(M[e], x.reshape(nd, -1)[:, e]) for e in range(M.shape[0])], axis=1)
+    assert np.allclose(y.reshape(nd, -1), ref, rtol=1e-12, atol=1e-14)
+
+
+def test_pmg_one_step_is_element_jacobi(small):
+    O, q, Rq = small["O"], small["q"], small["Rq"]
+    c = 1.0 / 0.5 + 1.0 / (0.4358665215 * 0.5)
+    O.pmg_setup(q, [1], c, 0.0)
+    X = np.random.default_rng(3).standard_normal(q.shape)
+    Y = O.pmg_apply(q, Rq, X)
+    M = O.elem_blocks(q, c, np.arange(small["mesh"]["E"]))
+    nd = M.shape[1]
+    ref = np.stack([np.linalg.solve(M[e], X.reshape(nd, -1)[:, e]) for e in range(M.shape[0])], axis=1)
+    assert np.abs(Y.reshape(nd, -1) - ref).max() <= 1e-13 * np.abs(q).max()
+
+
+def test_pmg_same_degree_coarse_level_is_extra_smoothing(small):
+    mesh, ph, q, Rq = small["mesh"], small["ph"], small["q"], small["Rq"]
+    X = np.random.default_rng(4).standard_normal(q.shape)
+    c, ids = 5.0, 2.0
+    O2 = oracle.Oracle(mesh, ph, [2, 2])
+    O2.pmg_setup(q, [1, 1], c, ids)
+    Ya = O2.pmg_apply(q, Rq, X)
+    O1 = oracle.Oracle(mesh, ph, [2])
+    O1.pmg_setup(q, [3], c, ids)
+    Yb = O1.pmg_apply(q, Rq, X)
+    assert np.abs(Ya - Yb).max() <= 1e-12 * np.abs(Yb).max()
+
+
+@pytest.mark.parametrize("levels,nsmooth", [([2], [80]), ([2, 1], [40, 40])])
+def test_pmg_fixed_point_is_linear_solve(small, levels, nsmooth):
+    mesh, ph, q, Rq, J, N = small["mesh"], small["ph"], small["q"], small["Rq"], small["J"], small["N"]
+    dt = 0.5
+    c = 1.0 / dt + 1.0 / (0.4358665215 * dt)
+    O = oracle.Oracle(mesh, ph, levels)
+    O.pmg_setup(q, nsmooth, c, 0.0)
+    X = 1e-3 * np.random.default_rng(5).standard_normal(q.shape) / math.sqrt(N)
+    Y = O.pmg_apply(q, Rq, X)
+    ref = np.linalg.solve(c * np.eye(N) - J, X.ravel())
+    assert np.linalg.norm(Y.ravel() - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("use_pmg", [False, True])
+def test_fgmres_matches_dense_solve(small, use_pmg):
+    O, q, Rq, J, N = small["O"], small["q"], small["Rq"], small["J"], small["N"]
+    dt = 0.5
+    c = 1.0 / dt + 1.0 / (0.4358665215 * dt)
+    b = np.random.default_rng(6).standard_normal(q.shape)
+    ref = np.linalg.solve(c * np.eye(N) - J, b.ravel())
+    if use_pmg:
+        O.pmg_setup(q, [2, 2], c, 1.0 / dt)
+    x, st = O.gmres(q, Rq, b, kdim=N, tol=1e-9, maxit=N, shift=c, use_pmg=use_pmg)
+    assert np.linalg.norm(x.ravel() - ref) <= 1e-6 * np.linalg.norm(ref)
+    assert st["relres"] <= 1e-6
+
+
+def test_tableaux_order_conditions():
+    A, b, c = TB.esdirk3()
+    assert abs(b.sum() - 1) < 1e-15 and abs(b @ c - 0.5) < 1e-15
+    assert abs(b @ c ** 2 - 1 / 3) < 1e-15 and abs(b @ A @ c - 1 / 6) < 1e-15
+    # L-stability of a stiffly accurate ESDIRK: R(z) -> 0 as z -> -inf
+    z = -1e8
+    R = 1 + z * b @ np.linalg.solve(np.eye(4) - z * A, np.ones(4))
+    assert abs(R) < 1e-6
+    gam, alpha, G, bb = TB.ros34pw2_standard()
+    beta = alpha + G - np.diag(np.diag(G))
+    bp, al = beta.sum(1), alpha.sum(1)
+    assert abs(bb.sum() - 1) < 1e-15 and abs(bb @ bp - (0.5 - gam)) < 1e-15
+    assert abs(bb @ al ** 2 - 1 / 3) < 1e-15 and abs(bb @ (beta @ bp) - (1 / 6 - gam + gam * gam)) < 1e-15
+    # stiff accuracy: b is the last row of alpha + Gamma
+    assert np.allclose(bb, (alpha + G)[3], atol=1e-15)
+    # transformed coefficients reproduce the scalar linear test equation
+    g, a, cc, m = TB.ros34pw2()
+    lam, h = -0.7, 0.3
+    Y = []
+    for i in range(4):
+        rhs = lam * (1 + sum(a[i, j] * Y[j] for j in range(i))) + sum(cc[i, j] * Y[j] for j in range(i)) / h
+        Y.append(rhs / (1 / (g * h) - lam))
+    y1 = 1 + sum(m[j] * Y[j] for j in range(4))
+    # the same step in the standard form
+    K = []
+    for i in range(4):
+        s = lam * h * (1 + sum(alpha[i, j] * K[j] for j in range(i))) + lam * h * sum(G[i, j] * K[j] for j in range(i))
+        K.append(s / (1 - lam * h * gam))
+    assert abs(y1 - (1 + bb @ np.array(K))) < 1e-14
+
+
+def _march(O, kind, q0, T, dt):
+    q = q0.copy()
+    for _ in range(int(round(T / dt))):
+        if kind == "esdirk":
+            A, b, _ = TB.esdirk3()
+            opts = O.opts(kdim=40, maxit_gmres=200, max_ptc=30, nsmooth=(2, 2), tol_gmres=1e-3,
+                          tol_newton=1e-10, dtau=dt, inv_dtau_star=1.0 / dt)
+            q, st = O.esdirk_step(A, b, dt, q, opts)
+            assert st["converged"]
+        else:
+            g, a, c, m = TB.ros34pw2()
+            opts = O.opts(kdim=40, maxit_gmres=200, nsmooth=(2, 2), tol_gmres=1e-7, inv_dtau_star=1.0 / dt)
+            q, st = O.row_step(g, a, c, m, dt, q, opts)
+    return q
+
+
+@pytest.mark.parametrize("kind", ["esdirk", "row"])
+def test_observed_temporal_order(kind):
+    mesh = w.box2d(2, 2, 10, 10, qg=2, warp=0.1)
+    O = oracle.Oracle(mesh, w.Physics(mu=0.02, qinf=w.freestream(2, 0.3)), [2, 1])
+    q0 = angled_flow(mesh, 2, amp=0.1)
+    T = 0.4
+    ref = _march(O, kind, q0, T, 0.0125)
+    errs = np.array([np.abs(_march(O, kind, q0, T, dt) - ref).max() for dt in (0.2, 0.1)])
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > 2.6
+
+
+def test_steady_ptc_ser_converges():
+    W = w.cylinder_steady(nr=6, nt=12, p=2, levels=[2, 1], mach=0.2, re=40)
+    O = oracle.Oracle(W.mesh, W.phys, W.levels)
+    opts = O.opts(kdim=30, maxit_gmres=60, nsmooth=(2, 2), tol_gmres=1e-2, inv_dtau_star=-1.0)
+    dtau0 = 0.1 * W.mesh["h_min"] / (1.0 + 1.0 / 0.2)
+    q, st = O.ptc_steady(W.q0, dtau0, 1e6, 1e-8, 60, opts)
+    assert st["converged"] and st["final_res"] <= 1e-8
