@@ -11,7 +11,8 @@
  *
  * Dense LU: Gaussian elimination with partial pivoting (first maximal |pivot|, rows
  * swapped), multipliers l = a/u, trailing updates a = fma(-l, u, a) in ascending
- * elimination order; triangular solves as fma chains in ascending column order.
+ * elimination order; triangular solves as fma chains in the order the unknowns become
+ * known (ascending column index forward, descending column index backward).
  *
  * Transfers (Eqs. 17-18): the 1-D Gamma / Pi applied along direction 0, then 1, then 2.
  */
@@ -80,7 +81,7 @@ void or_lu_solve(int n, const double *A, const int *piv, double *b) {
     }
     for (int i = n - 1; i >= 0; --i) {
         double s = b[i];
-        for (int k = i + 1; k < n; ++k) s = fma(-A[(size_t)i * n + k], b[k], s);
+        for (int k = n - 1; k > i; --k) s = fma(-A[(size_t)i * n + k], b[k], s);
         b[i] = s / A[(size_t)i * n + i];
     }
 }

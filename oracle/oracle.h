@@ -8,6 +8,7 @@
  * Arithmetic convention (so a reader can re-derive every rounding):
  *   - every sum of products  sum_k a_k b_k  is an fma chain in ascending k that
  *     starts from +0.0:   s = 0; s = fma(a_k, b_k, s);
+ *   - divisions by the density are multiplications by one reciprocal rinv = 1/rho;
  *   - every other expression is evaluated exactly as parenthesised in the source,
  *     compiled with -ffp-contract=off (no implicit contraction, no reassociation);
  *   - operator tables are the correctly rounded doubles of their exact values

@@ -56,8 +56,8 @@ static int fp_encode(int n, int d, int nf1, int df, int s, const int *ii) {
 void or_flux_inviscid(const or_ctx *C, const double *q, double f[3][5]) {
     int d = C->d;
     double gm1 = C->ph.gamma - 1.0;
-    double rho = q[0], E = q[d + 1], u[3], ke = 0.0;
-    for (int j = 0; j < d; ++j) u[j] = q[1 + j] / rho;
+    double rho = q[0], E = q[d + 1], u[3], ke = 0.0, rinv = 1.0 / rho;
+    for (int j = 0; j < d; ++j) u[j] = q[1 + j] * rinv;
     for (int j = 0; j < d; ++j) ke = fma(q[1 + j], u[j], ke);
     double p = gm1 * (E - 0.5 * ke);
     for (int c = 0; c < d; ++c) {
@@ -75,15 +75,15 @@ void or_flux_viscous(const or_ctx *C, const double *q, double Q[3][5], int adiab
     int d = C->d;
     double gamma = C->ph.gamma, mu = C->ph.mu;
     double kappa = (gamma * mu) / C->ph.Pr, c23 = 2.0 / 3.0;
-    double rho = q[0], E = q[d + 1], u[3], Er = E / rho;
+    double rho = q[0], E = q[d + 1], u[3], rinv = 1.0 / rho, Er = E * rinv;
     double du[3][3], de[3], tau[3][3];
-    for (int j = 0; j < d; ++j) u[j] = q[1 + j] / rho;
+    for (int j = 0; j < d; ++j) u[j] = q[1 + j] * rinv;
     for (int j = 0; j < d; ++j)
-        for (int c = 0; c < d; ++c) du[j][c] = (Q[c][1 + j] - u[j] * Q[c][0]) / rho;
+        for (int c = 0; c < d; ++c) du[j][c] = (Q[c][1 + j] - u[j] * Q[c][0]) * rinv;
     for (int c = 0; c < d; ++c) {
         double s = 0.0;
         for (int j = 0; j < d; ++j) s = fma(u[j], du[j][c], s);
-        de[c] = (Q[c][d + 1] - Er * Q[c][0]) / rho;
+        de[c] = (Q[c][d + 1] - Er * Q[c][0]) * rinv;
         de[c] = de[c] - s;
     }
     double divu = 0.0;
@@ -117,11 +117,11 @@ void or_rusanov(const or_ctx *C, const double *qL, const double *qR, const doubl
     double lam[2];
     for (int side = 0; side < 2; ++side) {
         const double *q = side ? qR : qL;
-        double rho = q[0], E = q[d + 1], u[3], ke = 0.0, vn = 0.0;
-        for (int j = 0; j < d; ++j) u[j] = q[1 + j] / rho;
+        double rho = q[0], E = q[d + 1], u[3], ke = 0.0, vn = 0.0, rinv = 1.0 / rho;
+        for (int j = 0; j < d; ++j) u[j] = q[1 + j] * rinv;
         for (int j = 0; j < d; ++j) ke = fma(q[1 + j], u[j], ke);
         double p = gm1 * (E - 0.5 * ke);
-        double a = sqrt((gamma * p) / rho);
+        double a = sqrt((gamma * p) * rinv);
         for (int c = 0; c < d; ++c) vn = fma(u[c], n[c], vn);
         lam[side] = fabs(vn) + a * nmag;
     }
