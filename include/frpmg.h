@@ -1,0 +1,200 @@
+/*
+ * frpmg — GB300 (sm_103a) JFNK-pMG hot path for flux-reconstruction Navier-Stokes.
+ *
+ * C ABI.  Every array argument is a plain pointer; the comment of each call says whether
+ * it is a host or a device pointer.  Device pointers are owned by the caller (the
+ * library never frees them); the library owns the workspaces it allocates in fr_create
+ * and pmg_setup and frees them in fr_destroy.  Work is enqueued on the caller's CUDA
+ * stream (`stream` is a cudaStream_t passed as void*, NULL = legacy default stream);
+ * calls that return scalars to the host (gmres_solve, esdirk_step, row_step,
+ * ptc_steady) synchronise that stream.  A context is not thread safe: one host thread
+ * at a time per context.
+ *
+ * Errors: every call returns an int status (FR_OK = 0, negative = error) and leaves a
+ * message retrievable with fr_last_error() (thread local).  Invalid arguments are
+ * rejected before any work is enqueued.  A CUDA error is reported as FR_ERR_CUDA and
+ * leaves the context usable only for fr_destroy.
+ *
+ * Layouts.  d = dimension (2 or 3), nv = d + 2 conservative variables
+ * (rho, rho u_1..rho u_d, E), level l has degree p_l, n = p_l + 1 Gauss-Legendre
+ * points per direction, Np = n^d solution points; a state on level l is a
+ * double array q[v][i][e] of nv * Np * E values, element index fastest, solution
+ * point i = i0 + n (i1 + n i2).  An element block is nd x nd with nd = nv * Np and
+ * degree-of-freedom index r = v * Np + i; blocks are stored column-major per element:
+ * M[(e * nd + j) * nd + r] holds entry (row r, column j).
+ *
+ * Arithmetic.  The FP64 residual, Jacobian-vector product, element blocks, block LU,
+ * block solves, transfers and preconditioner cycle evaluate every sum of products as an
+ * fma chain in a fixed order with no other contraction, so they are reproducible bit
+ * for bit run to run.  GMRES inner products use a fixed two-level reduction tree.
+ */
+#ifndef FRPMG_H
+#define FRPMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FR_OK = 0,
+    FR_ERR_INVALID_ARG = -1,
+    FR_ERR_CUDA = -2,
+    FR_ERR_OOM = -3,
+    FR_ERR_NOT_CONVERGED = -4,
+    FR_ERR_NONFINITE = -5,
+    FR_ERR_BREAKDOWN = -6,
+    FR_ERR_UNIMPLEMENTED = -7,
+    FR_ERR_NOT_READY = -8
+};
+
+typedef struct fr_ctx fr_ctx;
+
+/* Mesh (all host pointers, copied during fr_create).
+ *   gnodes  [nelem][(qg+1)^dim][dim] geometry nodes on the Lobatto points {-1,(0),1} of
+ *           degree qg (1 or 2), node a = a0 + (qg+1)(a1 + (qg+1) a2)
+ *   faces   [nfaces][6] rows (eL, fL, eR, fR, orient, bc); face f = 2*dir + side, side 0
+ *           at xi_dir = -1; eR = -1 marks a boundary face with bc 1 = far field (ghost =
+ *           free stream) or 2 = no-slip adiabatic wall; orient (interior faces): 2-D bit 0
+ *           reverses the tangential index of the R side; 3-D bit 2 swaps the two
+ *           tangential indices, then bit 0 / bit 1 reverse the first / second.
+ *   plevels [nlevels] polynomial degree per p-level, finest first (p in 1..4 for 2-D,
+ *           1..3 for 3-D).  Geometry of level p has degree min(qg, p). */
+typedef struct {
+    int dim, nelem, qg;
+    const double *gnodes;
+    int nfaces;
+    const int *faces;
+    int nlevels;
+    const int *plevels;
+} fr_mesh_desc;
+
+/* gamma, Prandtl number, dynamic viscosity (1/Re in the dimensionless set-up of Sec. 2.2),
+ * BR2 penalty, free-stream conservative state (nv values) used by far-field faces. */
+typedef struct {
+    double gamma, prandtl, mu, eta;
+    double qinf[5];
+} fr_physics;
+
+/* Create a context: operator tables, geometric factors of every level, connectivity and
+ * workspaces on the current CUDA device.  *out receives the context (NULL on error). */
+int fr_create(fr_ctx **out, const fr_mesh_desc *mesh, const fr_physics *phys);
+int fr_destroy(fr_ctx *ctx);
+const char *fr_last_error(void);
+/* sizes of level l (host out-pointers, any may be NULL): degree, Np, nv*Np*E */
+int fr_level_info(const fr_ctx *ctx, int level, int *p, int *np, long long *ndof);
+/* number of element colours used to assemble the element blocks (host int*) */
+int fr_num_colors(const fr_ctx *ctx, int *ncolors);
+
+/* Sec. 2.1, Eq. (1): R(q) = -div f(q, grad q) on level `level` (flux reconstruction with
+ * Gauss-Legendre points and DG correction functions, Rusanov inviscid + BR2 viscous
+ * common fluxes), so that dq/dt = R.  q, R: device, [nv][Np][E]; q and R must not alias. */
+int fr_residual(fr_ctx *ctx, int level, const double *q, double *R, void *stream);
+
+/* Eq. (8): Av = shift v - (R(q + eps v) - Rq) / eps on the finest level; Rq must be R(q).
+ * q, Rq, v, Av: device [nv][Np][E]; Av must not alias the inputs. */
+int fr_jvp(fr_ctx *ctx, const double *q, const double *Rq, const double *v, double eps,
+           double shift, double *Av, void *stream);
+
+/* Sec. 2.2, Eq. (9) and Sec. 3.2 smoother: element-diagonal blocks of the shifted
+ * Jacobian M_e = shift I - dR_e/dq_e at q (every other element fixed), column j by the
+ * forward difference with step 1e-7 max(1, |q_j|).  q: device level state; M: device,
+ * E * nd * nd doubles, column-major per element (see Layouts). */
+int fr_elem_blocks(fr_ctx *ctx, int level, const double *q, double shift, double *M, void *stream);
+
+/* In-place LU with partial pivoting of every block (first maximal |pivot|).  M as above;
+ * perm: device int [E][nd], receives the row permutation (row i of LU is row perm[i] of
+ * the input block).  Returns FR_ERR_BREAKDOWN (after the whole batch) if a zero pivot
+ * was met. */
+int fr_block_factor(fr_ctx *ctx, int level, double *M, int *perm, void *stream);
+/* x <- M_e^{-1} x for every element using the factors of fr_block_factor.
+ * x: device [nv][Np][E], overwritten. */
+int fr_block_solve(fr_ctx *ctx, int level, const double *M, const int *perm, double *x, void *stream);
+
+/* Eqs. (17)-(18): L2 restriction level -> level+1 and prolongation level+1 -> level,
+ * tensor-product 1-D operators applied along direction 0, 1, 2 in turn.  Device arrays. */
+int fr_restrict(fr_ctx *ctx, int level, const double *x_fine, double *x_coarse, void *stream);
+int fr_prolong(fr_ctx *ctx, int level, const double *x_coarse, double *x_fine, void *stream);
+
+/* Nonlinear pMG preconditioner, Sec. 3.2, Eqs. (22)-(26) with the V-cycle of Sec. 3.1,
+ * Eqs. (11)-(16).  c = 1/dtau + 1/(a_ii dt) (ESDIRK) or 1/(gamma dt) (ROW);
+ * inv_dtau_star = 1/dtau* of the preconditioner's own pseudo step (0 = infinite).
+ * nsmooth[l] = smoothing steps on level l (pre and post on levels with a coarser one).
+ * pmg_setup evaluates and factors the element blocks (1/dtau* + c) I - J_ee on every level
+ * at q_ref restricted level by level (device state), and keeps them until the next
+ * pmg_setup or fr_destroy. */
+typedef struct {
+    int nlevels;
+    int nsmooth[4];
+    double c;
+    double inv_dtau_star;
+} fr_pmg_opts;
+int pmg_setup(fr_ctx *ctx, const double *q_ref, const fr_pmg_opts *opts, void *stream);
+/* Y ~ A^{-1} X: one V-cycle of pseudo-time marching of
+ * 0 = X + R(qh) - c qh - R(q) + c q from qh = q; Y = qh - q.  q, Rq (= R(q)), X, Y: device
+ * finest-level vectors; Y must not alias the inputs. */
+int pmg_precondition(fr_ctx *ctx, const double *q, const double *Rq, const double *X, double *Y,
+                     void *stream);
+
+/* Restarted right-preconditioned flexible GMRES (CGS2 orthogonalisation) for
+ * A x = b with A v = shift v - (R(q + eps v) - R(q))/eps (Eq. 8) and, if use_pmg, the
+ * preconditioner of the last pmg_setup.  The FD product is applied to unit-norm
+ * directions only.  Stops when ||b - A x|| <= tol ||b|| or after maxit iterations.
+ * q, Rq, b, x: device; stats: host (may be NULL). */
+typedef struct {
+    int kdim, maxit, use_pmg;
+    double tol, eps, shift;
+} fr_gmres_opts;
+typedef struct {
+    int iters, restarts;
+    double relres;
+} fr_gmres_stats;
+int gmres_solve(fr_ctx *ctx, const double *q, const double *Rq, const double *b, double *x,
+                const fr_gmres_opts *opts, fr_gmres_stats *stats, void *stream);
+
+/* Solver options for the time steppers (host struct). */
+typedef struct {
+    int kdim, maxit_gmres, max_ptc, nlevels, nsmooth[4], use_pmg;
+    double tol_gmres, tol_newton, eps, dtau, inv_dtau_star;
+} fr_solve_opts;
+typedef struct {
+    int n_ptc, n_gmres, converged;
+    double final_res;
+} fr_step_stats;
+
+/* ESDIRK step, Eq. (2): stages solved by PTC/Newton (Eqs. 5-7) with FGMRES, the
+ * preconditioner set up once per step at q^n; stage converged when
+ * RMS(a_ii dt F(q_i)) <= tol_newton.  A: host [stages][stages] row-major (A[0][*] = 0),
+ * b: host [stages]; q: device, q^n in, q^{n+1} out.  Returns FR_ERR_NOT_CONVERGED (with
+ * q^{n+1} written) when a stage missed the tolerance within max_ptc iterations. */
+typedef struct {
+    int stages;
+    double A[36];
+    double b[6];
+} fr_esdirk_tableau;
+int esdirk_step(fr_ctx *ctx, const fr_esdirk_tableau *tab, double dt, double *q,
+                const fr_solve_opts *opts, fr_step_stats *stats, void *stream);
+
+/* Rosenbrock-Wanner step in the variables of Eq. (3):
+ * (I/(gamma dt) - dR/dq(q^n)) Y_i = R(q^n + sum_j a_ij Y_j) + (1/dt) sum_j c_ij Y_j,
+ * q^{n+1} = q^n + sum_j m_j Y_j.  a, c: host [stages][stages] row-major strictly lower. */
+typedef struct {
+    int stages;
+    double gamma;
+    double a[36];
+    double c[36];
+    double m[6];
+} fr_row_tableau;
+int row_step(fr_ctx *ctx, const fr_row_tableau *tab, double dt, double *q, const fr_solve_opts *opts,
+             fr_step_stats *stats, void *stream);
+
+/* Steady PTC (Eq. 7 without the dt terms) with the SER pseudo-step of Eq. (10), read as
+ * dtau <- min(dtau ||R^k|| / ||R^{k+1}||, dtau_max); preconditioner re-set at every
+ * iteration with c = 1/dtau (inv_dtau_star < 0 selects 1/dtau* = c).  Stops at
+ * ||R|| <= tol_rel ||R_0||.  hist: host [max_it+1] residual norms (may be NULL). */
+int ptc_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
+               const fr_solve_opts *opts, fr_step_stats *stats, double *hist, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

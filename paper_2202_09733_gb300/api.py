@@ -1,0 +1,213 @@
+"""Thin Python binding of the frpmg C ABI.
+
+The functions carry the C names and only marshal arguments: torch CUDA tensors supply
+device memory (their data pointers) and the current torch stream supplies the CUDA
+stream.  Every step of the computation runs in libfrpmg.so; if the library is missing
+the first call raises (there is no CPU path)."""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev(t: torch.Tensor, dtype=torch.float64, name="tensor"):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Context:
+    handle: C.c_void_p
+    d: int
+    E: int
+    levels: list
+    nv: int
+    _keep: tuple = field(default=(), repr=False)
+
+    def np_(self, level=0):
+        return (self.levels[level] + 1) ** self.d
+
+    def shape(self, level=0):
+        return (self.nv, self.np_(level), self.E)
+
+    def nd(self, level=0):
+        return self.nv * self.np_(level)
+
+    def empty(self, level=0):
+        return torch.empty(self.shape(level), dtype=torch.float64, device="cuda")
+
+    def num_colors(self):
+        n = C.c_int()
+        N.check(N.load().fr_num_colors(self.handle, C.byref(n)), "fr_num_colors")
+        return n.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                N.load().fr_destroy(h)
+            except Exception:
+                pass
+            self.handle = C.c_void_p()
+
+
+def fr_create(mesh: dict, phys, levels) -> Context:
+    """Create a context on the current CUDA device (mesh/physics as produced by
+    paper_2202_09733_gb300.workloads)."""
+    lib = N.load()
+    torch.cuda.init()
+    g = np.ascontiguousarray(mesh["gnodes"], dtype=np.float64)
+    f = np.ascontiguousarray(mesh["faces"], dtype=np.int32)
+    pl = np.ascontiguousarray(levels, dtype=np.int32)
+    md = N.MeshDesc(mesh["d"], mesh["E"], mesh["qg"], g.ctypes.data_as(N.PD), len(f), f.ctypes.data_as(N.PI),
+                    len(pl), pl.ctypes.data_as(N.PI))
+    ph = N.Physics()
+    ph.gamma, ph.prandtl, ph.mu, ph.eta = phys.gamma, phys.Pr, phys.mu, phys.eta
+    for v, x in enumerate(phys.qinf):
+        ph.qinf[v] = float(x)
+    h = C.c_void_p()
+    N.check(lib.fr_create(C.byref(h), C.byref(md), C.byref(ph)), "fr_create")
+    return Context(h, mesh["d"], mesh["E"], list(levels), mesh["d"] + 2)
+
+
+def fr_residual(ctx: Context, level: int, q: torch.Tensor, R: torch.Tensor | None = None, stream=None):
+    R = ctx.empty(level) if R is None else R
+    N.check(N.load().fr_residual(ctx.handle, level, _dev(q, name="q"), _dev(R, name="R"), _stream(stream)),
+            "fr_residual")
+    return R
+
+
+def fr_jvp(ctx, q, Rq, v, eps=1e-6, shift=0.0, Av=None, stream=None):
+    Av = ctx.empty(0) if Av is None else Av
+    N.check(N.load().fr_jvp(ctx.handle, _dev(q), _dev(Rq), _dev(v), float(eps), float(shift), _dev(Av),
+                            _stream(stream)), "fr_jvp")
+    return Av
+
+
+def fr_elem_blocks(ctx, level, q, shift, M=None, stream=None):
+    """Blocks as a [E, nd(col j), nd(row r)] tensor (column-major per element)."""
+    nd = ctx.nd(level)
+    M = torch.empty((ctx.E, nd, nd), dtype=torch.float64, device="cuda") if M is None else M
+    N.check(N.load().fr_elem_blocks(ctx.handle, level, _dev(q), float(shift), _dev(M), _stream(stream)),
+            "fr_elem_blocks")
+    return M
+
+
+def fr_block_factor(ctx, level, M, perm=None, stream=None):
+    perm = torch.empty((ctx.E, ctx.nd(level)), dtype=torch.int32, device="cuda") if perm is None else perm
+    N.check(N.load().fr_block_factor(ctx.handle, level, _dev(M), _dev(perm, torch.int32), _stream(stream)),
+            "fr_block_factor")
+    return perm
+
+
+def fr_block_solve(ctx, level, M, perm, x, stream=None):
+    N.check(N.load().fr_block_solve(ctx.handle, level, _dev(M), _dev(perm, torch.int32), _dev(x), _stream(stream)),
+            "fr_block_solve")
+    return x
+
+
+def fr_restrict(ctx, level, xf, xc=None, stream=None):
+    xc = ctx.empty(level + 1) if xc is None else xc
+    N.check(N.load().fr_restrict(ctx.handle, level, _dev(xf), _dev(xc), _stream(stream)), "fr_restrict")
+    return xc
+
+
+def fr_prolong(ctx, level, xc, xf=None, stream=None):
+    xf = ctx.empty(level) if xf is None else xf
+    N.check(N.load().fr_prolong(ctx.handle, level, _dev(xc), _dev(xf), _stream(stream)), "fr_prolong")
+    return xf
+
+
+def pmg_setup(ctx, q_ref, nsmooth, c, inv_dtau_star, stream=None):
+    o = N.PmgOpts()
+    o.nlevels = len(nsmooth)
+    for i, n in enumerate(nsmooth):
+        o.nsmooth[i] = int(n)
+    o.c, o.inv_dtau_star = float(c), float(inv_dtau_star)
+    N.check(N.load().pmg_setup(ctx.handle, _dev(q_ref), C.byref(o), _stream(stream)), "pmg_setup")
+
+
+def pmg_precondition(ctx, q, Rq, X, Y=None, stream=None):
+    Y = ctx.empty(0) if Y is None else Y
+    N.check(N.load().pmg_precondition(ctx.handle, _dev(q), _dev(Rq), _dev(X), _dev(Y), _stream(stream)),
+            "pmg_precondition")
+    return Y
+
+
+def gmres_solve(ctx, q, Rq, b, x=None, kdim=30, maxit=300, tol=1e-1, eps=1e-6, shift=0.0, use_pmg=False,
+                stream=None):
+    x = ctx.empty(0) if x is None else x
+    o = N.GmresOpts(int(kdim), int(maxit), int(bool(use_pmg)), float(tol), float(eps), float(shift))
+    st = N.GmresStats()
+    N.check(N.load().gmres_solve(ctx.handle, _dev(q), _dev(Rq), _dev(b), _dev(x), C.byref(o), C.byref(st),
+                                 _stream(stream)), "gmres_solve")
+    return x, dict(iters=st.iters, restarts=st.restarts, relres=st.relres)
+
+
+def solve_opts(kdim=30, maxit_gmres=300, max_ptc=100, nsmooth=(2, 2), use_pmg=True, tol_gmres=1e-1,
+               tol_newton=1e-8, eps=1e-6, dtau=1.0, inv_dtau_star=0.0):
+    o = N.SolveOpts()
+    o.kdim, o.maxit_gmres, o.max_ptc, o.nlevels = int(kdim), int(maxit_gmres), int(max_ptc), len(nsmooth)
+    for i, n in enumerate(nsmooth):
+        o.nsmooth[i] = int(n)
+    o.use_pmg, o.tol_gmres, o.tol_newton, o.eps = int(bool(use_pmg)), float(tol_gmres), float(tol_newton), float(eps)
+    o.dtau, o.inv_dtau_star = float(dtau), float(inv_dtau_star)
+    return o
+
+
+def _stats(st):
+    return dict(n_ptc=st.n_ptc, n_gmres=st.n_gmres, converged=st.converged, final_res=st.final_res)
+
+
+def esdirk_step(ctx, A, b, dt, q, opts, stream=None, allow_not_converged=True):
+    A = np.asarray(A, dtype=np.float64)
+    s = len(b)
+    tab = N.EsdirkTableau()
+    tab.stages = s
+    for i in range(s):
+        tab.b[i] = float(b[i])
+        for j in range(s):
+            tab.A[i * s + j] = float(A[i, j])
+    st = N.StepStats()
+    rc = N.load().esdirk_step(ctx.handle, C.byref(tab), float(dt), _dev(q), C.byref(opts), C.byref(st),
+                              _stream(stream))
+    N.check(rc, "esdirk_step", allow=(-4,) if allow_not_converged else ())
+    return _stats(st)
+
+
+def row_step(ctx, gamma, a, c, m, dt, q, opts, stream=None, allow_not_converged=True):
+    s = len(m)
+    tab = N.RowTableau()
+    tab.stages, tab.gamma = s, float(gamma)
+    for i in range(s):
+        tab.m[i] = float(m[i])
+        for j in range(s):
+            tab.a[i * s + j] = float(a[i][j])
+            tab.c[i * s + j] = float(c[i][j])
+    st = N.StepStats()
+    rc = N.load().row_step(ctx.handle, C.byref(tab), float(dt), _dev(q), C.byref(opts), C.byref(st), _stream(stream))
+    N.check(rc, "row_step", allow=(-4,) if allow_not_converged else ())
+    return _stats(st)
+
+
+def ptc_steady(ctx, q, dtau_init, dtau_max, tol_rel, max_it, opts, stream=None):
+    hist = np.zeros(max_it + 1)
+    st = N.StepStats()
+    rc = N.load().ptc_steady(ctx.handle, _dev(q), float(dtau_init), float(dtau_max), float(tol_rel), int(max_it),
+                             C.byref(opts), C.byref(st), hist.ctypes.data_as(N.PD), _stream(stream))
+    N.check(rc, "ptc_steady", allow=(-4,))
+    out = _stats(st)
+    out["hist"] = hist[:st.n_ptc + 1]
+    return out

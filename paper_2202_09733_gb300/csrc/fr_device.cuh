@@ -1,0 +1,482 @@
+// Device building blocks of the flux-reconstruction residual (templated on dimension D,
+// degree P and scalar type T).  Included by the FP64 translation unit (compiled with
+// -fmad=false: the only contractions are the explicit fma() calls, so every FP64 result
+// is reproducible bit for bit) and by the FP32 one (preconditioner precision).
+//
+// Layouts (element index e fastest everywhere, E elements):
+//   state / residual      q[v][i][e]            v < nv = D+2, i < Np = n^D
+//   flux-point traces     qf[v][k][e]           k = f*n^(D-1) + t, f = 2*dir + side
+//   gradients             Q[c][v][i][e], Qf[c][v][k][e]
+//   geometric factors     S[dd][c][i][e] = J dxi_dd/dx_c, G = S / J, invJ[i][e],
+//                         Sf, Gf at flux points
+// Evaluation order (fixed): every sum of products is an fma chain in ascending index
+// starting from +0; everything else is evaluated as parenthesised.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define FR_MAXN 6
+#define FR_MAXP 5
+
+template <typename T>
+struct FrTab {
+    T D[FR_MAXN][FR_MAXN];
+    T lm[FR_MAXN], lp[FR_MAXN], dlm[FR_MAXN], dlp[FR_MAXN];
+    T gLd[FR_MAXN], gRd[FR_MAXN];
+};
+
+template <typename T>
+struct FrPhys {
+    T gamma, gm1, mu, kappa, c23;
+    T qinf[5];
+    T etagL, etagR;   // eta * g_L'(-1), eta * g_R'(+1) of the level
+};
+
+template <int D, int P>
+struct Sh {
+    static constexpr int n = P + 1;
+    static constexpr int nv = D + 2;
+    static constexpr int np = D == 2 ? n * n : n * n * n;
+    static constexpr int nf1 = D == 2 ? n : n * n;
+    static constexpr int nfp = 2 * D * nf1;
+};
+
+template <int D, int N>
+__device__ __forceinline__ int spi(int i0, int i1, int i2) {
+    return D == 2 ? i0 + N * i1 : i0 + N * (i1 + N * i2);
+}
+
+// face point k -> normal direction df, side s, tangential coordinates (a, b)
+template <int D, int N>
+__device__ __forceinline__ void fp_decode(int k, int &df, int &s, int &a, int &b) {
+    constexpr int nf1 = D == 2 ? N : N * N;
+    int f = k / nf1, t = k - f * nf1;
+    df = f >> 1;
+    s = f & 1;
+    a = t % N;
+    b = D == 3 ? t / N : 0;
+}
+
+// solution point on the line normal to face direction df through tangential (a, b)
+template <int D, int N>
+__device__ __forceinline__ int line_pt(int df, int a, int b, int m) {
+    if (D == 2) return df == 0 ? m + N * a : a + N * m;
+    if (df == 0) return m + N * (a + N * b);
+    if (df == 1) return a + N * (m + N * b);
+    return a + N * (b + N * m);
+}
+
+// face point of face (df, s) on the df-line through the solution point (i0, i1, i2)
+template <int D, int N>
+__device__ __forceinline__ int fp_of(int df, int s, int i0, int i1, int i2) {
+    constexpr int nf1 = D == 2 ? N : N * N;
+    int t;
+    if (D == 2) t = df == 0 ? i1 : i0;
+    else t = df == 0 ? i1 + N * i2 : (df == 1 ? i0 + N * i2 : i0 + N * i1);
+    return (2 * df + s) * nf1 + t;
+}
+
+// face point of face (df, s) whose tangential coordinates are (a, b)
+template <int D, int N>
+__device__ __forceinline__ int fp_at(int df, int s, int a, int b) {
+    constexpr int nf1 = D == 2 ? N : N * N;
+    return (2 * df + s) * nf1 + a + (D == 3 ? N * b : 0);
+}
+
+// ---------------------------------------------------------------------------- physics
+template <int D, typename T>
+__device__ __forceinline__ void flux_inviscid(const FrPhys<T> &ph, const T *q, T f[3][5]) {
+    T rho = q[0], E = q[D + 1], rinv = T(1) / rho, u[3], ke = T(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) u[j] = q[1 + j] * rinv;
+#pragma unroll
+    for (int j = 0; j < D; ++j) ke = fma(q[1 + j], u[j], ke);
+    T p = ph.gm1 * (E - T(0.5) * ke);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        f[c][0] = q[1 + c];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            T t = q[1 + c] * u[j];
+            if (j == c) t = t + p;
+            f[c][1 + j] = t;
+        }
+        f[c][D + 1] = (E + p) * u[c];
+    }
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void flux_viscous(const FrPhys<T> &ph, const T *q, const T Q[3][5], bool adiabatic,
+                                             T f[3][5]) {
+    T rho = q[0], E = q[D + 1], rinv = T(1) / rho, Er = E * rinv, u[3];
+    T du[3][3], de[3], tau[3][3];
+#pragma unroll
+    for (int j = 0; j < D; ++j) u[j] = q[1 + j] * rinv;
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int c = 0; c < D; ++c) du[j][c] = (Q[c][1 + j] - u[j] * Q[c][0]) * rinv;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) s = fma(u[j], du[j][c], s);
+        T t = (Q[c][D + 1] - Er * Q[c][0]) * rinv;
+        de[c] = t - s;
+    }
+    T divu = T(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) divu = divu + du[j][j];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            T t = du[i][j] + du[j][i];
+            if (i == j) t = t - ph.c23 * divu;
+            tau[i][j] = ph.mu * t;
+        }
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        f[c][0] = T(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) f[c][1 + j] = tau[j][c];
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) s = fma(u[j], tau[j][c], s);
+        if (!adiabatic) s = s + ph.kappa * de[c];
+        f[c][D + 1] = s;
+    }
+}
+
+// Rusanov flux along the (scaled) normal n
+template <int D, typename T>
+__device__ __forceinline__ void rusanov(const FrPhys<T> &ph, const T *qL, const T *qR, const T *n, T *F) {
+    constexpr int nv = D + 2;
+    T fL[3][5], fR[3][5];
+    flux_inviscid<D>(ph, qL, fL);
+    flux_inviscid<D>(ph, qR, fR);
+    T nn = T(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) nn = fma(n[c], n[c], nn);
+    T nmag = sqrt(nn);
+    T lam[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const T *q = side ? qR : qL;
+        T rho = q[0], E = q[D + 1], rinv = T(1) / rho, u[3], ke = T(0), vn = T(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) u[j] = q[1 + j] * rinv;
+#pragma unroll
+        for (int j = 0; j < D; ++j) ke = fma(q[1 + j], u[j], ke);
+        T p = ph.gm1 * (E - T(0.5) * ke);
+        T a = sqrt((ph.gamma * p) * rinv);
+#pragma unroll
+        for (int c = 0; c < D; ++c) vn = fma(u[c], n[c], vn);
+        lam[side] = fabs(vn) + a * nmag;
+    }
+    T lmax = fmax(lam[0], lam[1]);
+#pragma unroll
+    for (int v = 0; v < nv; ++v) {
+        T FnL = T(0), FnR = T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) FnL = fma(fL[c][v], n[c], FnL);
+#pragma unroll
+        for (int c = 0; c < D; ++c) FnR = fma(fR[c][v], n[c], FnR);
+        F[v] = T(0.5) * (FnL + FnR) - T(0.5) * lmax * (qR[v] - qL[v]);
+    }
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void ghost_state(const FrPhys<T> &ph, int bc, const T *qL, T *qR) {
+    if (bc == 1) {
+#pragma unroll
+        for (int v = 0; v < D + 2; ++v) qR[v] = ph.qinf[v];
+    } else {
+        qR[0] = qL[0];
+#pragma unroll
+        for (int j = 0; j < D; ++j) qR[1 + j] = -qL[1 + j];
+        qR[D + 1] = qL[D + 1];
+    }
+}
+
+// ---------------------------------------------------------------- residual kernels
+// Tables live in constant memory, indexed by degree; each including translation unit
+// defines the specialisation of frtab<T> for its scalar type.
+template <typename T>
+__device__ const FrTab<T> &frtab(int p);
+
+// stage 1: qf[v][k][e] = sum_m l_side[m] q[v][line(k, m)][e]
+template <int D, int P, typename T>
+__global__ void __launch_bounds__(128) k_interp(const T *__restrict__ q, T *__restrict__ qf, int E) {
+    using S = Sh<D, P>;
+    constexpr int N = S::n;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    int v = blockIdx.y / S::nfp, k = blockIdx.y - v * S::nfp;
+    int df, s, a, b;
+    fp_decode<D, N>(k, df, s, a, b);
+    const FrTab<T> &tb = frtab<T>(P);
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+        T l = s ? tb.lp[m] : tb.lm[m];
+        acc = fma(l, q[(size_t)(v * S::np + line_pt<D, N>(df, a, b, m)) * E + e], acc);
+    }
+    qf[(size_t)(v * S::nfp + k) * E + e] = acc;
+}
+
+// stage 2: common solution, jumps dq = qs - q_side on both sides
+template <int D, int P, typename T>
+__global__ void __launch_bounds__(128) k_pair_common(const int4 *__restrict__ pairs, const int *__restrict__ bcs,
+                                                     int npairs, const T *__restrict__ qf, T *__restrict__ dq, int E,
+                                                     FrPhys<T> ph) {
+    using S = Sh<D, P>;
+    int P_ = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P_ >= npairs) return;
+    int4 pr = pairs[P_];
+    int bc = bcs[P_];
+    T qL[5], qR[5];
+#pragma unroll
+    for (int v = 0; v < S::nv; ++v) qL[v] = qf[(size_t)(v * S::nfp + pr.y) * E + pr.x];
+    if (bc == 0) {
+#pragma unroll
+        for (int v = 0; v < S::nv; ++v) qR[v] = qf[(size_t)(v * S::nfp + pr.w) * E + pr.z];
+    } else {
+        ghost_state<D>(ph, bc, qL, qR);
+    }
+#pragma unroll
+    for (int v = 0; v < S::nv; ++v) {
+        T qs = T(0.5) * (qL[v] + qR[v]);
+        dq[(size_t)(v * S::nfp + pr.y) * E + pr.x] = qs - qL[v];
+        if (bc == 0) dq[(size_t)(v * S::nfp + pr.w) * E + pr.z] = qs - qR[v];
+    }
+}
+
+// stage 3a: corrected gradient at solution points
+template <int D, int P, typename T>
+__global__ void __launch_bounds__(128) k_grad_sp(const T *__restrict__ q, const T *__restrict__ dq,
+                                                 const T *__restrict__ G, T *__restrict__ Q, int E) {
+    using S = Sh<D, P>;
+    constexpr int N = S::n;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    int v = blockIdx.y / S::np, i = blockIdx.y - v * S::np;
+    int ii[3] = {i % N, (i / N) % N, D == 3 ? i / (N * N) : 0};
+    const FrTab<T> &tb = frtab<T>(P);
+    T gr[3];
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd) {
+        T t = T(0);
+        int cd = ii[dd];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            int jj0 = dd == 0 ? m : ii[0], jj1 = dd == 1 ? m : ii[1], jj2 = dd == 2 ? m : ii[2];
+            t = fma(tb.D[cd][m], q[(size_t)(v * S::np + spi<D, N>(jj0, jj1, jj2)) * E + e], t);
+        }
+        int kL = fp_of<D, N>(dd, 0, ii[0], ii[1], ii[2]), kR = fp_of<D, N>(dd, 1, ii[0], ii[1], ii[2]);
+        t = fma(tb.gLd[cd], dq[(size_t)(v * S::nfp + kL) * E + e], t);
+        t = fma(tb.gRd[cd], dq[(size_t)(v * S::nfp + kR) * E + e], t);
+        gr[dd] = t;
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        T acc = T(0);
+#pragma unroll
+        for (int dd = 0; dd < D; ++dd) acc = fma(G[(size_t)((dd * D + c) * S::np + i) * E + e], gr[dd], acc);
+        Q[(size_t)((c * S::nv + v) * S::np + i) * E + e] = acc;
+    }
+}
+
+// stage 3b: face gradient traces (uncorrected) with the BR2 lifting of the face's own jump
+template <int D, int P, typename T>
+__global__ void __launch_bounds__(128) k_grad_fp(const T *__restrict__ q, const T *__restrict__ qf,
+                                                 const T *__restrict__ dq, const T *__restrict__ Gf,
+                                                 T *__restrict__ Qf, int E, T etagL, T etagR) {
+    using S = Sh<D, P>;
+    constexpr int N = S::n;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    int v = blockIdx.y / S::nfp, k = blockIdx.y - v * S::nfp;
+    int df, s, a, b;
+    fp_decode<D, N>(k, df, s, a, b);
+    const FrTab<T> &tb = frtab<T>(P);
+    T gf[3];
+    {
+        T t = T(0);
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            T dl = s ? tb.dlp[m] : tb.dlm[m];
+            t = fma(dl, q[(size_t)(v * S::np + line_pt<D, N>(df, a, b, m)) * E + e], t);
+        }
+        gf[df] = t;
+    }
+    // tangential directions in increasing order, coordinates a then b
+    int td0 = df == 0 ? 1 : 0, td1 = df == 2 ? 1 : 2;
+    {
+        T u = T(0);
+#pragma unroll
+        for (int m = 0; m < N; ++m)
+            u = fma(tb.D[a][m], qf[(size_t)(v * S::nfp + fp_at<D, N>(df, s, m, b)) * E + e], u);
+        gf[td0] = u;
+    }
+    if (D == 3) {
+        T u = T(0);
+#pragma unroll
+        for (int m = 0; m < N; ++m)
+            u = fma(tb.D[b][m], qf[(size_t)(v * S::nfp + fp_at<D, N>(df, s, a, m)) * E + e], u);
+        gf[td1] = u;
+    }
+    T comp[3];
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd) comp[dd] = gf[dd];
+    comp[df] = fma(s ? etagR : etagL, dq[(size_t)(v * S::nfp + k) * E + e], gf[df]);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        T acc = T(0);
+#pragma unroll
+        for (int dd = 0; dd < D; ++dd) acc = fma(Gf[(size_t)((dd * D + c) * S::nfp + k) * E + e], comp[dd], acc);
+        Qf[(size_t)((c * S::nv + v) * S::nfp + k) * E + e] = acc;
+    }
+}
+
+// stage 4: common normal flux Rusanov(qL, qR, n) - f_v(qs, Qs) . n on both sides
+template <int D, int P, typename T>
+__global__ void __launch_bounds__(128) k_pair_flux(const int4 *__restrict__ pairs, const int *__restrict__ bcs,
+                                                   int npairs, const T *__restrict__ qf, const T *__restrict__ Qf,
+                                                   const T *__restrict__ Sf, T *__restrict__ fn, int E, FrPhys<T> ph) {
+    using S = Sh<D, P>;
+    constexpr int nv = S::nv;
+    int P_ = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P_ >= npairs) return;
+    int4 pr = pairs[P_];
+    int bc = bcs[P_];
+    int f = pr.y / S::nf1, df = f >> 1, side = f & 1;
+    T nrm[3];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        T sv = Sf[(size_t)((df * D + c) * S::nfp + pr.y) * E + pr.x];
+        nrm[c] = side ? sv : -sv;
+    }
+    T qL[5], qR[5], qs[5], QL[3][5], Qs[3][5];
+#pragma unroll
+    for (int v = 0; v < nv; ++v) {
+        qL[v] = qf[(size_t)(v * S::nfp + pr.y) * E + pr.x];
+#pragma unroll
+        for (int c = 0; c < D; ++c) QL[c][v] = Qf[(size_t)((c * nv + v) * S::nfp + pr.y) * E + pr.x];
+    }
+    if (bc == 0) {
+#pragma unroll
+        for (int v = 0; v < nv; ++v) {
+            qR[v] = qf[(size_t)(v * S::nfp + pr.w) * E + pr.z];
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                Qs[c][v] = T(0.5) * (QL[c][v] + Qf[(size_t)((c * nv + v) * S::nfp + pr.w) * E + pr.z]);
+        }
+    } else {
+        ghost_state<D>(ph, bc, qL, qR);
+#pragma unroll
+        for (int v = 0; v < nv; ++v)
+#pragma unroll
+            for (int c = 0; c < D; ++c) Qs[c][v] = QL[c][v];
+    }
+#pragma unroll
+    for (int v = 0; v < nv; ++v) qs[v] = T(0.5) * (qL[v] + qR[v]);
+    T Fr[5], fv[3][5];
+    rusanov<D>(ph, qL, qR, nrm, Fr);
+    flux_viscous<D>(ph, qs, Qs, bc == 2, fv);
+#pragma unroll
+    for (int v = 0; v < nv; ++v) {
+        T Fv = T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) Fv = fma(fv[c][v], nrm[c], Fv);
+        T F = Fr[v] - Fv;
+        fn[(size_t)(v * S::nfp + pr.y) * E + pr.x] = F;
+        if (bc == 0) fn[(size_t)(v * S::nfp + pr.w) * E + pr.z] = -F;
+    }
+}
+
+// stage 5a: transformed volume flux Ft[dd][v][i][e] = sum_c S[dd][c] (f_inv - f_visc)_c
+template <int D, int P, typename T>
+__global__ void __launch_bounds__(128) k_vflux(const T *__restrict__ q, const T *__restrict__ Q,
+                                               const T *__restrict__ Sm, T *__restrict__ Ft, int E, FrPhys<T> ph) {
+    using S = Sh<D, P>;
+    constexpr int nv = S::nv;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    int i = blockIdx.y;
+    T qi[5], Qi[3][5], fi[3][5], fvi[3][5];
+#pragma unroll
+    for (int v = 0; v < nv; ++v) {
+        qi[v] = q[(size_t)(v * S::np + i) * E + e];
+#pragma unroll
+        for (int c = 0; c < D; ++c) Qi[c][v] = Q[(size_t)((c * nv + v) * S::np + i) * E + e];
+    }
+    flux_inviscid<D>(ph, qi, fi);
+    flux_viscous<D>(ph, qi, Qi, false, fvi);
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd) {
+        T sm[3];
+#pragma unroll
+        for (int c = 0; c < D; ++c) sm[c] = Sm[(size_t)((dd * D + c) * S::np + i) * E + e];
+#pragma unroll
+        for (int v = 0; v < nv; ++v) {
+            T acc = T(0);
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc = fma(sm[c], fi[c][v] - fvi[c][v], acc);
+            Ft[(size_t)((dd * nv + v) * S::np + i) * E + e] = acc;
+        }
+    }
+}
+
+// stage 5b: transformed discontinuous flux at the face points (normal component)
+template <int D, int P, typename T>
+__global__ void __launch_bounds__(128) k_face_ft(const T *__restrict__ Ft, T *__restrict__ Ftf, int E) {
+    using S = Sh<D, P>;
+    constexpr int N = S::n;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    int v = blockIdx.y / S::nfp, k = blockIdx.y - v * S::nfp;
+    int df, s, a, b;
+    fp_decode<D, N>(k, df, s, a, b);
+    const FrTab<T> &tb = frtab<T>(P);
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+        T l = s ? tb.lp[m] : tb.lm[m];
+        acc = fma(l, Ft[(size_t)((df * S::nv + v) * S::np + line_pt<D, N>(df, a, b, m)) * E + e], acc);
+    }
+    Ftf[(size_t)(v * S::nfp + k) * E + e] = acc;
+}
+
+// stage 5c: divergence with FR corrections, R = -(div * invJ)
+template <int D, int P, typename T>
+__global__ void __launch_bounds__(128) k_div(const T *__restrict__ Ft, const T *__restrict__ Ftf,
+                                             const T *__restrict__ fn, const T *__restrict__ invJ,
+                                             T *__restrict__ R, int E) {
+    using S = Sh<D, P>;
+    constexpr int N = S::n;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    int v = blockIdx.y / S::np, i = blockIdx.y - v * S::np;
+    int ii[3] = {i % N, (i / N) % N, D == 3 ? i / (N * N) : 0};
+    const FrTab<T> &tb = frtab<T>(P);
+    T div = T(0);
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd) {
+        int cd = ii[dd];
+        const T *F = Ft + (size_t)((dd * S::nv + v) * S::np) * E;
+        T t = T(0);
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            int jj0 = dd == 0 ? m : ii[0], jj1 = dd == 1 ? m : ii[1], jj2 = dd == 2 ? m : ii[2];
+            t = fma(tb.D[cd][m], F[(size_t)spi<D, N>(jj0, jj1, jj2) * E + e], t);
+        }
+        int kL = fp_of<D, N>(dd, 0, ii[0], ii[1], ii[2]), kR = fp_of<D, N>(dd, 1, ii[0], ii[1], ii[2]);
+        T FsL = -fn[(size_t)(v * S::nfp + kL) * E + e];
+        T FsR = fn[(size_t)(v * S::nfp + kR) * E + e];
+        t = fma(tb.gLd[cd], FsL - Ftf[(size_t)(v * S::nfp + kL) * E + e], t);
+        t = fma(tb.gRd[cd], FsR - Ftf[(size_t)(v * S::nfp + kR) * E + e], t);
+        div = div + t;
+    }
+    R[(size_t)(v * S::np + i) * E + e] = -(div * invJ[(size_t)i * E + e]);
+}

@@ -1,0 +1,757 @@
+// frpmg C ABI: context set-up and the host-side orchestration of the JFNK-pMG hot path
+// (pMG V-cycle, FGMRES with CGS2, ESDIRK/PTC, ROW, steady PTC/SER).  Every arithmetic
+// step on solution vectors runs in the kernels of kernels64.cu; the host only keeps the
+// Krylov scalars (Hessenberg matrix, Givens rotations) and the iteration logic.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <vector>
+#include "../../include/frpmg.h"
+#include "fr_lib.h"
+#include "host_tables.h"
+
+static thread_local char g_err[1024] = "";
+
+static int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t _e = (call);                                                              \
+        if (_e != cudaSuccess)                                                                \
+            return fail(FR_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(_e)); \
+    } while (0)
+
+#define CKLAUNCH()                                                                            \
+    do {                                                                                      \
+        cudaError_t _e = cudaGetLastError();                                                  \
+        if (_e != cudaSuccess)                                                                \
+            return fail(FR_ERR_CUDA, "%s:%d kernel launch: %s", __FILE__, __LINE__, cudaGetErrorString(_e)); \
+    } while (0)
+
+#define TRY(x)                       \
+    do {                             \
+        int _r = (x);                \
+        if (_r != FR_OK) return _r;  \
+    } while (0)
+
+struct fr_ctx {
+    int d, nv, E, qg, nlev;
+    FrPhysH ph;
+    double eta;
+    FrLevel L[FRL_MAXLEV];
+    int ncolor;
+    int *color;
+    int *info;
+    std::vector<void *> allocs;
+    // residual-derived temporaries
+    double *jv_qp, *jv_Rp, *blk_R0, *blk_Rp, *blk_qp;
+    double *dots;                 // device scratch for inner products (64)
+    // pMG
+    int pmg_ready, pmg_nlev, nsmooth[FRL_MAXLEV];
+    double pmg_c, pmg_ids;
+    double *M[FRL_MAXLEV];
+    int *perm[FRL_MAXLEV];
+    size_t M_cap[FRL_MAXLEV];
+    double *pb[FRL_MAXLEV], *pRb[FRL_MAXLEV], *pd[FRL_MAXLEV], *pqh[FRL_MAXLEV], *pRqh[FRL_MAXLEV],
+        *prhs[FRL_MAXLEV], *pC[FRL_MAXLEV];
+    // GMRES
+    int gm_kdim;
+    std::vector<double *> V, Z;
+    double *gw, *gr, *gtmp;
+    // steppers
+    int st_cap;
+    std::vector<double *> stv;
+};
+
+static int dalloc(fr_ctx *C, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 8;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(FR_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    C->allocs.push_back(*p);
+    return FR_OK;
+}
+template <typename T>
+static int dalloc_t(fr_ctx *C, T **p, size_t count) {
+    return dalloc(C, (void **)p, sizeof(T) * count);
+}
+static void dfree(fr_ctx *C, void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < C->allocs.size(); ++i)
+        if (C->allocs[i] == p) { C->allocs.erase(C->allocs.begin() + i); break; }
+    cudaFree(p);
+}
+
+static cudaStream_t S_(void *s) { return (cudaStream_t)s; }
+
+extern "C" const char *fr_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------- context set-up
+static int upload_tables() {
+    static FrTabH tabs[6];
+    static double gam[6][6][6][6], pi[6][6][6][6];
+    memset(tabs, 0, sizeof tabs);
+    memset(gam, 0, sizeof gam);
+    memset(pi, 0, sizeof pi);
+    for (int p = 1; p <= 5; ++p) {
+        frh_tab T;
+        frh_make_tables(p, p < 2 ? p : 2, &T);
+        memcpy(tabs[p].D, T.D, sizeof T.D);
+        memcpy(tabs[p].lm, T.lm, sizeof T.lm);
+        memcpy(tabs[p].lp, T.lp, sizeof T.lp);
+        memcpy(tabs[p].dlm, T.dlm, sizeof T.dlm);
+        memcpy(tabs[p].dlp, T.dlp, sizeof T.dlp);
+        memcpy(tabs[p].gLd, T.gLd, sizeof T.gLd);
+        memcpy(tabs[p].gRd, T.gRd, sizeof T.gRd);
+        for (int p1 = 1; p1 <= p; ++p1) {
+            double G[FRH_MAXN][FRH_MAXN], P[FRH_MAXN][FRH_MAXN];
+            frh_make_transfer(p, p1, G, P);
+            memcpy(gam[p][p1], G, sizeof G);
+            memcpy(pi[p][p1], P, sizeof P);
+        }
+    }
+    if (frk64_upload_tables(tabs, &gam[0][0][0][0], &pi[0][0][0][0]) != 0)
+        return fail(FR_ERR_CUDA, "uploading operator tables: %s", cudaGetErrorString(cudaGetLastError()));
+    return FR_OK;
+}
+
+static int setup_level(fr_ctx *C, int l, int p, const fr_mesh_desc *m) {
+    FrLevel &L = C->L[l];
+    int d = C->d, E = C->E;
+    L.d = d; L.p = p; L.n = p + 1; L.E = E; L.nv = C->nv;
+    L.np = d == 2 ? L.n * L.n : L.n * L.n * L.n;
+    L.nf1 = d == 2 ? L.n : L.n * L.n;
+    L.nfp = 2 * d * L.nf1;
+    L.nd = L.nv * L.np;
+    L.ndof = (long long)L.nd * E;
+    frh_tab T;
+    int g = p < C->qg ? p : C->qg;
+    frh_make_tables(p, g, &T);
+    L.etagL = C->eta * T.gLf;
+    L.etagR = C->eta * T.gRf;
+    size_t nsp = (size_t)d * d * L.np * E, nfpt = (size_t)d * d * L.nfp * E;
+    std::vector<double> S(nsp), G(nsp), iJ((size_t)L.np * E), J((size_t)L.np * E), Sf(nfpt), Gf(nfpt);
+    frh_geometry(d, E, C->qg, m->gnodes, &T, S.data(), G.data(), iJ.data(), J.data(), Sf.data(), Gf.data());
+    for (size_t i = 0; i < J.size(); ++i)
+        if (!(J[i] > 0.0)) return fail(FR_ERR_INVALID_ARG, "level %d: non-positive Jacobian in element %zu", l, i % E);
+    std::vector<int> pairs((size_t)4 * m->nfaces * L.nf1), bc((size_t)m->nfaces * L.nf1);
+    int np_ = frh_pairs(d, L.n, E, m->nfaces, m->faces, pairs.data(), bc.data());
+    if (np_ < 0) return fail(FR_ERR_INVALID_ARG, "face list does not pair every face point exactly once");
+    L.npairs = np_;
+    TRY(dalloc_t(C, &L.S, nsp)); TRY(dalloc_t(C, &L.G, nsp)); TRY(dalloc_t(C, &L.invJ, (size_t)L.np * E));
+    TRY(dalloc_t(C, &L.Sf, nfpt)); TRY(dalloc_t(C, &L.Gf, nfpt));
+    TRY(dalloc_t(C, &L.pairs, (size_t)np_)); TRY(dalloc_t(C, &L.bc, (size_t)np_));
+    CK(cudaMemcpy(L.S, S.data(), sizeof(double) * nsp, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.G, G.data(), sizeof(double) * nsp, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.invJ, iJ.data(), sizeof(double) * iJ.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.Sf, Sf.data(), sizeof(double) * nfpt, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.Gf, Gf.data(), sizeof(double) * nfpt, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.bc, bc.data(), sizeof(int) * bc.size(), cudaMemcpyHostToDevice));
+    size_t nfv = (size_t)C->nv * L.nfp * E, npv = (size_t)C->nv * L.np * E;
+    TRY(dalloc_t(C, &L.qf, nfv)); TRY(dalloc_t(C, &L.dq, nfv)); TRY(dalloc_t(C, &L.fn, nfv));
+    TRY(dalloc_t(C, &L.Ftf, nfv)); TRY(dalloc_t(C, &L.Q, d * npv)); TRY(dalloc_t(C, &L.Ft, d * npv));
+    TRY(dalloc_t(C, &L.Qf, d * nfv));
+    return FR_OK;
+}
+
+extern "C" int fr_destroy(fr_ctx *C) {
+    if (!C) return FR_OK;
+    for (void *p : C->allocs) cudaFree(p);
+    delete C;
+    return FR_OK;
+}
+
+extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *ph) {
+    if (!out) return fail(FR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!m || !ph) return fail(FR_ERR_INVALID_ARG, "mesh or physics is NULL");
+    if (m->dim != 2 && m->dim != 3) return fail(FR_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (m->qg != 1 && m->qg != 2) return fail(FR_ERR_INVALID_ARG, "geometry degree must be 1 or 2");
+    if (m->nelem <= 0 || !m->gnodes || !m->faces || m->nfaces <= 0)
+        return fail(FR_ERR_INVALID_ARG, "empty mesh");
+    if (m->nlevels < 1 || m->nlevels > FRL_MAXLEV || !m->plevels)
+        return fail(FR_ERR_INVALID_ARG, "nlevels must be 1..%d", FRL_MAXLEV);
+    int pmax = m->dim == 2 ? 4 : 3;
+    for (int l = 0; l < m->nlevels; ++l) {
+        if (m->plevels[l] < 1 || m->plevels[l] > pmax)
+            return fail(FR_ERR_INVALID_ARG, "level %d degree %d outside 1..%d", l, m->plevels[l], pmax);
+        if (l > 0 && m->plevels[l] > m->plevels[l - 1])
+            return fail(FR_ERR_INVALID_ARG, "levels must be ordered finest first");
+    }
+    if (!(ph->gamma > 1.0) || !(ph->prandtl > 0.0) || !(ph->mu >= 0.0) || !(ph->eta >= 0.0))
+        return fail(FR_ERR_INVALID_ARG, "invalid physical parameters");
+    fr_ctx *C = new fr_ctx();
+    C->d = m->dim; C->nv = m->dim + 2; C->E = m->nelem; C->qg = m->qg; C->nlev = m->nlevels;
+    C->eta = ph->eta;
+    C->ph.gamma = ph->gamma;
+    C->ph.gm1 = ph->gamma - 1.0;
+    C->ph.mu = ph->mu;
+    C->ph.kappa = (ph->gamma * ph->mu) / ph->prandtl;
+    C->ph.c23 = 2.0 / 3.0;
+    for (int v = 0; v < 5; ++v) C->ph.qinf[v] = v < C->nv ? ph->qinf[v] : 0.0;
+    int rc = upload_tables();
+    for (int l = 0; rc == FR_OK && l < m->nlevels; ++l) rc = setup_level(C, l, m->plevels[l], m);
+    if (rc == FR_OK) {
+        std::vector<int> col(C->E);
+        C->ncolor = frh_color(C->E, m->nfaces, m->faces, col.data());
+        rc = dalloc_t(C, &C->color, C->E);
+        if (rc == FR_OK && cudaMemcpy(C->color, col.data(), sizeof(int) * C->E, cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = fail(FR_ERR_CUDA, "copying colours");
+    }
+    long long n0 = C->L[0].ndof;
+    if (rc == FR_OK) rc = dalloc_t(C, &C->info, 1);
+    if (rc == FR_OK) rc = dalloc_t(C, &C->dots, 64);
+    if (rc == FR_OK) rc = dalloc_t(C, &C->jv_qp, n0);
+    if (rc == FR_OK) rc = dalloc_t(C, &C->jv_Rp, n0);
+    if (rc != FR_OK) { fr_destroy(C); return rc; }
+    *out = C;
+    return FR_OK;
+}
+
+extern "C" int fr_level_info(const fr_ctx *C, int l, int *p, int *np, long long *ndof) {
+    if (!C || l < 0 || l >= C->nlev) return fail(FR_ERR_INVALID_ARG, "bad context or level");
+    if (p) *p = C->L[l].p;
+    if (np) *np = C->L[l].np;
+    if (ndof) *ndof = C->L[l].ndof;
+    return FR_OK;
+}
+extern "C" int fr_num_colors(const fr_ctx *C, int *n) {
+    if (!C || !n) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    *n = C->ncolor;
+    return FR_OK;
+}
+
+// ------------------------------------------------------------------ residual, Jv
+static int residual(fr_ctx *C, int l, const double *q, double *R, cudaStream_t s) {
+    if (frk64_residual(C->L[l], C->ph, q, R, s) != 0) return fail(FR_ERR_UNIMPLEMENTED, "no kernel for d=%d p=%d", C->d, C->L[l].p);
+    CKLAUNCH();
+    return FR_OK;
+}
+
+extern "C" int fr_residual(fr_ctx *C, int l, const double *q, double *R, void *stream) {
+    if (!C || l < 0 || l >= C->nlev || !q || !R) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    if (q == R) return fail(FR_ERR_INVALID_ARG, "q and R must not alias");
+    return residual(C, l, q, R, S_(stream));
+}
+
+static int jvp(fr_ctx *C, const double *q, const double *Rq, const double *v, double eps, double shift, double *Av,
+               cudaStream_t s) {
+    long long n = C->L[0].ndof;
+    frk64_axpy_perturb(n, q, eps, v, C->jv_qp, s);
+    TRY(residual(C, 0, C->jv_qp, C->jv_Rp, s));
+    frk64_jv_finish(n, shift, v, C->jv_Rp, Rq, eps, Av, s);
+    CKLAUNCH();
+    return FR_OK;
+}
+
+extern "C" int fr_jvp(fr_ctx *C, const double *q, const double *Rq, const double *v, double eps, double shift,
+                      double *Av, void *stream) {
+    if (!C || !q || !Rq || !v || !Av) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    if (Av == q || Av == Rq || Av == v) return fail(FR_ERR_INVALID_ARG, "Av must not alias the inputs");
+    if (!(eps != 0.0)) return fail(FR_ERR_INVALID_ARG, "eps must be non-zero");
+    return jvp(C, q, Rq, v, eps, shift, Av, S_(stream));
+}
+
+// ---------------------------------------------------------------- element blocks
+static int ensure_blk_tmp(fr_ctx *C) {
+    if (C->blk_R0) return FR_OK;
+    long long n0 = C->L[0].ndof;
+    TRY(dalloc_t(C, &C->blk_R0, n0));
+    TRY(dalloc_t(C, &C->blk_Rp, n0));
+    TRY(dalloc_t(C, &C->blk_qp, n0));
+    return FR_OK;
+}
+
+static int elem_blocks(fr_ctx *C, int l, const double *q, double shift, double *M, cudaStream_t s) {
+    TRY(ensure_blk_tmp(C));
+    FrLevel &L = C->L[l];
+    TRY(residual(C, l, q, C->blk_R0, s));
+    frk64_copy(L.ndof, q, C->blk_qp, s);
+    for (int col = 0; col < C->ncolor; ++col)
+        for (int j = 0; j < L.nd; ++j) {
+            frk64_perturb_color(L, C->color, col, j, q, C->blk_qp, s);
+            TRY(residual(C, l, C->blk_qp, C->blk_Rp, s));
+            frk64_block_column(L, C->color, col, j, q, C->blk_R0, C->blk_Rp, shift, M, s);
+            frk64_restore_color(L, C->color, col, j, q, C->blk_qp, s);
+        }
+    CKLAUNCH();
+    return FR_OK;
+}
+
+extern "C" int fr_elem_blocks(fr_ctx *C, int l, const double *q, double shift, double *M, void *stream) {
+    if (!C || l < 0 || l >= C->nlev || !q || !M) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    return elem_blocks(C, l, q, shift, M, S_(stream));
+}
+
+static int block_factor(fr_ctx *C, int l, double *M, int *perm, cudaStream_t s) {
+    CK(cudaMemsetAsync(C->info, 0, sizeof(int), s));
+    frk64_lu_factor(C->L[l], M, perm, C->info, s);
+    CKLAUNCH();
+    return FR_OK;
+}
+
+extern "C" int fr_block_factor(fr_ctx *C, int l, double *M, int *perm, void *stream) {
+    if (!C || l < 0 || l >= C->nlev || !M || !perm) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t s = S_(stream);
+    TRY(block_factor(C, l, M, perm, s));
+    int info = 0;
+    CK(cudaMemcpyAsync(&info, C->info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (info) return fail(FR_ERR_BREAKDOWN, "zero pivot in an element block");
+    return FR_OK;
+}
+
+extern "C" int fr_block_solve(fr_ctx *C, int l, const double *M, const int *perm, double *x, void *stream) {
+    if (!C || l < 0 || l >= C->nlev || !M || !perm || !x) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    if (frk64_lu_solve(C->L[l], M, perm, x, S_(stream)) != 0) return fail(FR_ERR_UNIMPLEMENTED, "block size %d", C->L[l].nd);
+    CKLAUNCH();
+    return FR_OK;
+}
+
+static int transfer(fr_ctx *C, int l, bool r, const double *x, double *y, cudaStream_t s) {
+    if (frk64_transfer(C->L[l], C->L[l + 1], r, x, y, s) != 0)
+        return fail(FR_ERR_UNIMPLEMENTED, "no transfer kernel p%d <-> p%d", C->L[l].p, C->L[l + 1].p);
+    CKLAUNCH();
+    return FR_OK;
+}
+extern "C" int fr_restrict(fr_ctx *C, int l, const double *xf, double *xc, void *stream) {
+    if (!C || l < 0 || l + 1 >= C->nlev || !xf || !xc) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    return transfer(C, l, true, xf, xc, S_(stream));
+}
+extern "C" int fr_prolong(fr_ctx *C, int l, const double *xc, double *xf, void *stream) {
+    if (!C || l < 0 || l + 1 >= C->nlev || !xf || !xc) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    return transfer(C, l, false, xc, xf, S_(stream));
+}
+
+// ------------------------------------------------------------------------- pMG
+static int pmg_alloc(fr_ctx *C, int nlev) {
+    for (int l = 0; l < nlev; ++l) {
+        FrLevel &L = C->L[l];
+        size_t need = (size_t)L.E * L.nd * L.nd;
+        if (C->M_cap[l] < need) {
+            dfree(C, C->M[l]);
+            dfree(C, C->perm[l]);
+            C->M[l] = nullptr; C->perm[l] = nullptr; C->M_cap[l] = 0;
+            TRY(dalloc_t(C, &C->M[l], need));
+            TRY(dalloc_t(C, &C->perm[l], (size_t)L.E * L.nd));
+            C->M_cap[l] = need;
+        }
+        if (!C->pqh[l]) {
+            long long n = L.ndof;
+            if (l > 0) { TRY(dalloc_t(C, &C->pb[l], n)); TRY(dalloc_t(C, &C->pRb[l], n)); TRY(dalloc_t(C, &C->pd[l], n)); }
+            TRY(dalloc_t(C, &C->pqh[l], n)); TRY(dalloc_t(C, &C->pRqh[l], n));
+            TRY(dalloc_t(C, &C->prhs[l], n)); TRY(dalloc_t(C, &C->pC[l], n));
+        }
+    }
+    return FR_OK;
+}
+
+static int pmg_setup_(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, cudaStream_t s) {
+    C->pmg_ready = 0;
+    TRY(pmg_alloc(C, o->nlevels));
+    C->pmg_nlev = o->nlevels;
+    for (int l = 0; l < o->nlevels; ++l) C->nsmooth[l] = o->nsmooth[l];
+    C->pmg_c = o->c;
+    C->pmg_ids = o->inv_dtau_star;
+    double shift = o->inv_dtau_star + o->c;
+    const double *qr = q_ref;
+    for (int l = 0; l < o->nlevels; ++l) {
+        if (l > 0) {
+            // reference state restricted level by level (kept in pb[l] as scratch)
+            TRY(transfer(C, l - 1, true, qr, C->pb[l], s));
+            qr = C->pb[l];
+        }
+        TRY(elem_blocks(C, l, qr, shift, C->M[l], s));
+        TRY(block_factor(C, l, C->M[l], C->perm[l], s));
+    }
+    int info = 0;
+    CK(cudaMemcpyAsync(&info, C->info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (info) return fail(FR_ERR_BREAKDOWN, "zero pivot in an element block");
+    C->pmg_ready = 1;
+    return FR_OK;
+}
+
+extern "C" int pmg_setup(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, void *stream) {
+    if (!C || !q_ref || !o) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    if (o->nlevels < 1 || o->nlevels > C->nlev) return fail(FR_ERR_INVALID_ARG, "nlevels %d outside 1..%d", o->nlevels, C->nlev);
+    for (int l = 0; l < o->nlevels; ++l)
+        if (o->nsmooth[l] < 0) return fail(FR_ERR_INVALID_ARG, "negative smoothing count");
+    return pmg_setup_(C, q_ref, o, S_(stream));
+}
+
+// smoothing steps on level l: qh <- qh + M^{-1} (d - (c (qh - b) - (R(qh) - Rb)))
+static int smooth(fr_ctx *C, int l, int nsteps, const double *b, const double *Rb, const double *d, double *qh,
+                  bool first_is_base, cudaStream_t s) {
+    FrLevel &L = C->L[l];
+    for (int k = 0; k < nsteps; ++k) {
+        if (k == 0 && first_is_base) frk64_copy(L.ndof, d, C->prhs[l], s);
+        else {
+            TRY(residual(C, l, qh, C->pRqh[l], s));
+            frk64_pmg_rhs(L.ndof, C->pmg_c, d, qh, b, C->pRqh[l], Rb, C->prhs[l], s);
+        }
+        frk64_lu_solve(L, C->M[l], C->perm[l], C->prhs[l], s);
+        frk64_add(L.ndof, qh, C->prhs[l], qh, s);
+    }
+    CKLAUNCH();
+    return FR_OK;
+}
+
+static int vcycle(fr_ctx *C, int l, const double *b, const double *Rb, const double *d, double *qh, cudaStream_t s) {
+    int n = C->nsmooth[l];
+    TRY(smooth(C, l, n, b, Rb, d, qh, true, s));
+    if (l + 1 >= C->pmg_nlev) return FR_OK;
+    FrLevel &L = C->L[l];
+    double *r = C->prhs[l];
+    if (n == 0) frk64_copy(L.ndof, d, r, s);
+    else {
+        TRY(residual(C, l, qh, C->pRqh[l], s));
+        frk64_pmg_rhs(L.ndof, C->pmg_c, d, qh, b, C->pRqh[l], Rb, r, s);
+    }
+    double *b1 = C->pb[l + 1], *Rb1 = C->pRb[l + 1], *d1 = C->pd[l + 1], *qh1 = C->pqh[l + 1];
+    TRY(transfer(C, l, true, qh, b1, s));
+    TRY(transfer(C, l, true, r, d1, s));
+    TRY(residual(C, l + 1, b1, Rb1, s));
+    frk64_copy(C->L[l + 1].ndof, b1, qh1, s);
+    TRY(vcycle(C, l + 1, b1, Rb1, d1, qh1, s));
+    frk64_sub(C->L[l + 1].ndof, qh1, b1, qh1, s);
+    TRY(transfer(C, l, false, qh1, C->pC[l], s));
+    frk64_add(L.ndof, qh, C->pC[l], qh, s);
+    TRY(smooth(C, l, n, b, Rb, d, qh, false, s));
+    return FR_OK;
+}
+
+static int pmg_apply(fr_ctx *C, const double *q, const double *Rq, const double *X, double *Y, cudaStream_t s) {
+    long long n = C->L[0].ndof;
+    frk64_copy(n, q, C->pqh[0], s);
+    TRY(vcycle(C, 0, q, Rq, X, C->pqh[0], s));
+    frk64_sub(n, C->pqh[0], q, Y, s);
+    CKLAUNCH();
+    return FR_OK;
+}
+
+extern "C" int pmg_precondition(fr_ctx *C, const double *q, const double *Rq, const double *X, double *Y, void *stream) {
+    if (!C || !q || !Rq || !X || !Y) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    if (!C->pmg_ready) return fail(FR_ERR_NOT_READY, "pmg_setup has not been called");
+    if (Y == q || Y == Rq || Y == X) return fail(FR_ERR_INVALID_ARG, "Y must not alias the inputs");
+    return pmg_apply(C, q, Rq, X, Y, S_(stream));
+}
+
+// ------------------------------------------------------------------------ FGMRES
+static int dots(fr_ctx *C, long long n, int m, const double *w, const double *const *V, double *host, cudaStream_t s) {
+    if (frk64_multidot(n, m, w, V, C->dots, s) != 0) return fail(FR_ERR_OOM, "reduction scratch");
+    CKLAUNCH();
+    CK(cudaMemcpyAsync(host, C->dots, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return FR_OK;
+}
+static int norm2(fr_ctx *C, long long n, const double *w, double *out, cudaStream_t s) {
+    const double *V[1] = {w};
+    TRY(dots(C, n, 1, w, V, out, s));
+    *out = sqrt(*out);
+    return FR_OK;
+}
+
+static int gmres_alloc(fr_ctx *C, int kdim) {
+    long long n = C->L[0].ndof;
+    while ((int)C->V.size() < kdim + 1) {
+        double *p;
+        TRY(dalloc_t(C, &p, n));
+        C->V.push_back(p);
+    }
+    while ((int)C->Z.size() < kdim) {
+        double *p;
+        TRY(dalloc_t(C, &p, n));
+        C->Z.push_back(p);
+    }
+    if (!C->gw) { TRY(dalloc_t(C, &C->gw, n)); TRY(dalloc_t(C, &C->gr, n)); TRY(dalloc_t(C, &C->gtmp, n)); }
+    return FR_OK;
+}
+
+static int gmres(fr_ctx *C, const double *q, const double *Rq, const double *b, double *x, const fr_gmres_opts *o,
+                 fr_gmres_stats *st, cudaStream_t s) {
+    int K = o->kdim;
+    TRY(gmres_alloc(C, K));
+    long long n = C->L[0].ndof;
+    double *w = C->gw, *r = C->gr;
+    std::vector<double> H((size_t)(K + 1) * K, 0.0), cs(K), sn(K), g(K + 1), y(K), h(32), h2(32);
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    frk64_copy(n, b, r, s);
+    double bnorm, beta;
+    TRY(norm2(C, n, b, &bnorm, s));
+    beta = bnorm;
+    int total = 0, restarts = 0;
+    fr_gmres_stats loc = {0, 0, 0.0};
+    if (bnorm == 0.0) { if (st) *st = loc; return FR_OK; }
+    if (!isfinite(bnorm)) return fail(FR_ERR_NONFINITE, "non-finite right-hand side");
+    std::vector<const double *> Zp(K);
+    for (;;) {
+        frk64_div_scalar(n, r, beta, C->V[0], s);
+        for (int j = 0; j <= K; ++j) g[j] = 0.0;
+        g[0] = beta;
+        int jj = 0;
+        for (int j = 0; j < K; ++j) {
+            const double *zj;
+            if (o->use_pmg) {
+                TRY(pmg_apply(C, q, Rq, C->V[j], C->Z[j], s));
+                double zn;
+                TRY(norm2(C, n, C->Z[j], &zn, s));
+                if (!(zn > 0.0) || !isfinite(zn)) return fail(FR_ERR_NONFINITE, "preconditioner output norm %g", zn);
+                frk64_div_scalar(n, C->Z[j], zn, C->Z[j], s);
+                zj = C->Z[j];
+            } else {
+                zj = C->V[j];
+            }
+            Zp[j] = zj;
+            TRY(jvp(C, q, Rq, zj, o->eps, o->shift, w, s));
+            // CGS2
+            const double *const *Vp = (const double *const *)C->V.data();
+            TRY(dots(C, n, j + 1, w, Vp, h.data(), s));      // h also left in C->dots
+            frk64_multi_axpy(n, j + 1, C->dots, Vp, w, s);
+            TRY(dots(C, n, j + 1, w, Vp, h2.data(), s));
+            frk64_multi_axpy(n, j + 1, C->dots, Vp, w, s);
+            for (int i = 0; i <= j; ++i) H[(size_t)i * K + j] = h[i] + h2[i];
+            double hn;
+            TRY(norm2(C, n, w, &hn, s));
+            if (!isfinite(hn)) return fail(FR_ERR_NONFINITE, "non-finite Arnoldi vector");
+            H[(size_t)(j + 1) * K + j] = hn;
+            if (hn > 0.0) frk64_div_scalar(n, w, hn, C->V[j + 1], s);
+            for (int i = 0; i < j; ++i) {
+                double a = H[(size_t)i * K + j], bb = H[(size_t)(i + 1) * K + j];
+                H[(size_t)i * K + j] = cs[i] * a + sn[i] * bb;
+                H[(size_t)(i + 1) * K + j] = -sn[i] * a + cs[i] * bb;
+            }
+            double a = H[(size_t)j * K + j], bb = H[(size_t)(j + 1) * K + j];
+            double rr = hypot(a, bb);
+            cs[j] = a / rr; sn[j] = bb / rr;
+            H[(size_t)j * K + j] = rr; H[(size_t)(j + 1) * K + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++total; jj = j + 1;
+            if (fabs(g[j + 1]) <= o->tol * bnorm || total >= o->maxit || hn == 0.0) break;
+        }
+        for (int i = jj - 1; i >= 0; --i) {
+            double sacc = g[i];
+            for (int k = i + 1; k < jj; ++k) sacc -= H[(size_t)i * K + k] * y[k];
+            y[i] = sacc / H[(size_t)i * K + i];
+        }
+        frk64_update_x(n, jj, y.data(), Zp.data(), x, s);
+        double xn;
+        TRY(norm2(C, n, x, &xn, s));
+        if (xn > 0.0) {
+            frk64_div_scalar(n, x, xn, r, s);
+            TRY(jvp(C, q, Rq, r, o->eps, o->shift, w, s));
+            frk64_scale(n, xn, w, C->gtmp, s);
+            frk64_sub(n, b, C->gtmp, r, s);
+        } else {
+            frk64_copy(n, b, r, s);
+        }
+        TRY(norm2(C, n, r, &beta, s));
+        if (!isfinite(beta)) return fail(FR_ERR_NONFINITE, "non-finite GMRES residual");
+        if (beta <= o->tol * bnorm || total >= o->maxit) break;
+        ++restarts;
+    }
+    loc.iters = total; loc.restarts = restarts; loc.relres = beta / bnorm;
+    if (st) *st = loc;
+    return FR_OK;
+}
+
+extern "C" int gmres_solve(fr_ctx *C, const double *q, const double *Rq, const double *b, double *x,
+                           const fr_gmres_opts *o, fr_gmres_stats *st, void *stream) {
+    if (!C || !q || !Rq || !b || !x || !o) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    if (o->kdim < 1 || o->kdim > 512 || o->maxit < 1) return fail(FR_ERR_INVALID_ARG, "kdim must be 1..512, maxit >= 1");
+    if (o->use_pmg && !C->pmg_ready) return fail(FR_ERR_NOT_READY, "pmg_setup has not been called");
+    if (x == b || x == q || x == Rq) return fail(FR_ERR_INVALID_ARG, "x must not alias the inputs");
+    return gmres(C, q, Rq, b, x, o, st, S_(stream));
+}
+
+// --------------------------------------------------------------------- steppers
+static int stepper_alloc(fr_ctx *C, int nvec) {
+    long long n = C->L[0].ndof;
+    while ((int)C->stv.size() < nvec) {
+        double *p;
+        TRY(dalloc_t(C, &p, n));
+        C->stv.push_back(p);
+    }
+    return FR_OK;
+}
+
+static fr_gmres_opts gm_opts(const fr_solve_opts *o, double shift) {
+    fr_gmres_opts g;
+    g.kdim = o->kdim; g.maxit = o->maxit_gmres; g.use_pmg = o->use_pmg;
+    g.tol = o->tol_gmres; g.eps = o->eps; g.shift = shift;
+    return g;
+}
+
+static int check_solve_opts(const fr_ctx *C, const fr_solve_opts *o) {
+    if (o->kdim < 1 || o->kdim > 512 || o->maxit_gmres < 1 || o->max_ptc < 0)
+        return fail(FR_ERR_INVALID_ARG, "bad solver options");
+    if (o->use_pmg && (o->nlevels < 1 || o->nlevels > C->nlev))
+        return fail(FR_ERR_INVALID_ARG, "nlevels outside 1..%d", C->nlev);
+    return FR_OK;
+}
+
+extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, double *q, const fr_solve_opts *o,
+                           fr_step_stats *st, void *stream) {
+    if (!C || !tab || !q || !o) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    if (tab->stages < 2 || tab->stages > 6 || !(dt > 0.0)) return fail(FR_ERR_INVALID_ARG, "bad tableau or dt");
+    TRY(check_solve_opts(C, o));
+    cudaStream_t s = S_(stream);
+    int ns = tab->stages;
+    TRY(stepper_alloc(C, ns + 5));
+    long long n = C->L[0].ndof;
+    double *qn = C->stv[0], *sv = C->stv[1], *F = C->stv[2], *Rk = C->stv[3], *dq = C->stv[4];
+    double **Rs = &C->stv[5];
+    fr_step_stats loc = {0, 0, 1, 0.0};
+    frk64_copy(n, q, qn, s);
+    TRY(residual(C, 0, qn, Rs[0], s));
+    double aii = tab->A[1 * ns + 1];
+    double c = 1.0 / o->dtau + 1.0 / (aii * dt);
+    if (o->use_pmg) {
+        fr_pmg_opts po;
+        po.nlevels = o->nlevels;
+        for (int l = 0; l < 4; ++l) po.nsmooth[l] = o->nsmooth[l];
+        po.c = c;
+        po.inv_dtau_star = o->inv_dtau_star;
+        TRY(pmg_setup_(C, qn, &po, s));
+    }
+    fr_gmres_opts go = gm_opts(o, c);
+    for (int i = 1; i < ns; ++i) {
+        double adt = tab->A[i * ns + i] * dt;
+        double coef[6];
+        for (int j = 0; j < i; ++j) coef[j] = tab->A[i * ns + j];
+        frk64_lincomb(n, i, coef, (const double *const *)Rs, qn, dt, sv, s);
+        frk64_copy(n, qn, q, s);
+        int conv = 0;
+        double res = 0.0;
+        for (int k = 0; k <= o->max_ptc; ++k) {
+            TRY(residual(C, 0, q, Rk, s));
+            frk64_stage_F(n, q, sv, adt, Rk, F, s);
+            double fn;
+            TRY(norm2(C, n, F, &fn, s));
+            res = fabs(adt) * fn / sqrt((double)n);
+            if (!isfinite(res)) return fail(FR_ERR_NONFINITE, "non-finite stage residual (stage %d, iteration %d)", i, k);
+            if (res <= o->tol_newton) { conv = 1; break; }
+            if (k == o->max_ptc) break;
+            frk64_neg(n, F, F, s);
+            fr_gmres_stats gs;
+            TRY(gmres(C, q, Rk, F, dq, &go, &gs, s));
+            loc.n_gmres += gs.iters;
+            frk64_add(n, q, dq, q, s);
+            loc.n_ptc++;
+        }
+        if (!conv) loc.converged = 0;
+        loc.final_res = res;
+        frk64_copy(n, Rk, Rs[i], s);
+    }
+    frk64_lincomb(n, ns, tab->b, (const double *const *)Rs, qn, dt, q, s);
+    CKLAUNCH();
+    CK(cudaStreamSynchronize(s));
+    if (st) *st = loc;
+    return loc.converged ? FR_OK : fail(FR_ERR_NOT_CONVERGED, "a stage did not reach the Newton tolerance");
+}
+
+extern "C" int row_step(fr_ctx *C, const fr_row_tableau *tab, double dt, double *q, const fr_solve_opts *o,
+                        fr_step_stats *st, void *stream) {
+    if (!C || !tab || !q || !o) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    if (tab->stages < 1 || tab->stages > 6 || !(dt > 0.0) || !(tab->gamma > 0.0)) return fail(FR_ERR_INVALID_ARG, "bad tableau or dt");
+    TRY(check_solve_opts(C, o));
+    cudaStream_t s = S_(stream);
+    int ns = tab->stages;
+    TRY(stepper_alloc(C, ns + 5));
+    long long n = C->L[0].ndof;
+    double *qn = C->stv[0], *Rn = C->stv[1], *qi = C->stv[2], *rhs = C->stv[3], *Ri = C->stv[4];
+    double **Y = &C->stv[5];
+    fr_step_stats loc = {0, 0, 1, 0.0};
+    frk64_copy(n, q, qn, s);
+    TRY(residual(C, 0, qn, Rn, s));
+    double c = 1.0 / (tab->gamma * dt);
+    if (o->use_pmg) {
+        fr_pmg_opts po;
+        po.nlevels = o->nlevels;
+        for (int l = 0; l < 4; ++l) po.nsmooth[l] = o->nsmooth[l];
+        po.c = c;
+        po.inv_dtau_star = o->inv_dtau_star;
+        TRY(pmg_setup_(C, qn, &po, s));
+    }
+    fr_gmres_opts go = gm_opts(o, c);
+    for (int i = 0; i < ns; ++i) {
+        double coef[6];
+        for (int j = 0; j < i; ++j) coef[j] = tab->a[i * ns + j];
+        frk64_lincomb(n, i, coef, (const double *const *)Y, qn, 1.0, qi, s);
+        if (i == 0) frk64_copy(n, Rn, Ri, s);
+        else TRY(residual(C, 0, qi, Ri, s));
+        for (int j = 0; j < i; ++j) coef[j] = tab->c[i * ns + j];
+        frk64_lincomb(n, i, coef, (const double *const *)Y, nullptr, 1.0, rhs, s);
+        frk64_add_div(n, Ri, rhs, dt, rhs, s);
+        fr_gmres_stats gs;
+        TRY(gmres(C, qn, Rn, rhs, Y[i], &go, &gs, s));
+        loc.n_gmres += gs.iters;
+        if (gs.relres > o->tol_gmres) loc.converged = 0;
+        loc.final_res = gs.relres;
+    }
+    frk64_lincomb(n, ns, tab->m, (const double *const *)Y, qn, 1.0, q, s);
+    CKLAUNCH();
+    CK(cudaStreamSynchronize(s));
+    if (st) *st = loc;
+    return loc.converged ? FR_OK : fail(FR_ERR_NOT_CONVERGED, "a stage's linear solve missed its tolerance");
+}
+
+extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
+                          const fr_solve_opts *o, fr_step_stats *st, double *hist, void *stream) {
+    if (!C || !q || !o) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    if (!(dtau_init > 0.0) || !(dtau_max >= dtau_init) || max_it < 0) return fail(FR_ERR_INVALID_ARG, "bad pseudo-time parameters");
+    TRY(check_solve_opts(C, o));
+    cudaStream_t s = S_(stream);
+    TRY(stepper_alloc(C, 2));
+    long long n = C->L[0].ndof;
+    double *R = C->stv[0], *dq = C->stv[1];
+    fr_step_stats loc = {0, 0, 0, 0.0};
+    TRY(residual(C, 0, q, R, s));
+    double r0, rk, dtau = dtau_init;
+    TRY(norm2(C, n, R, &r0, s));
+    rk = r0;
+    if (hist) hist[0] = r0;
+    for (int k = 0; k < max_it; ++k) {
+        if (rk <= tol_rel * r0) break;
+        double c = 1.0 / dtau;
+        if (o->use_pmg) {
+            fr_pmg_opts po;
+            po.nlevels = o->nlevels;
+            for (int l = 0; l < 4; ++l) po.nsmooth[l] = o->nsmooth[l];
+            po.c = c;
+            po.inv_dtau_star = o->inv_dtau_star < 0 ? c : o->inv_dtau_star;
+            TRY(pmg_setup_(C, q, &po, s));
+        }
+        fr_gmres_opts go = gm_opts(o, c);
+        fr_gmres_stats gs;
+        TRY(gmres(C, q, R, R, dq, &go, &gs, s));
+        loc.n_gmres += gs.iters;
+        frk64_add(n, q, dq, q, s);
+        TRY(residual(C, 0, q, R, s));
+        double rn;
+        TRY(norm2(C, n, R, &rn, s));
+        if (!isfinite(rn)) return fail(FR_ERR_NONFINITE, "non-finite residual at pseudo step %d", k);
+        dtau = fmin(dtau * (rk / rn), dtau_max);
+        rk = rn;
+        loc.n_ptc++;
+        if (hist) hist[k + 1] = rn;
+    }
+    loc.final_res = rk / r0;
+    loc.converged = rk <= tol_rel * r0;
+    if (st) *st = loc;
+    return loc.converged ? FR_OK : fail(FR_ERR_NOT_CONVERGED, "steady PTC stopped at %g relative residual", loc.final_res);
+}
