@@ -1,0 +1,282 @@
+#!/usr/bin/env python
+"""Benchmark of the JFNK-pMG hot path on one GB300 (or N replicas under torchrun).
+
+Workload (the 3-D throughput case): compressible Navier-Stokes, FR p = 3 on 32^3 periodic
+affine hexes (2.1 M solution points x 5 variables), Taylor-Green field plus seeded
+Fourier noise (modes <= 4, amplitude 1e-3), Ma = 0.1, Re = 1600.  One step = one
+ROS34PW2 step (dt = 20x the explicit limit) with the nonlinear pMG p{3-2} n{2-2}
+preconditioner (element blocks and their LU evaluated at q^n inside the step, as the
+paper does once per physical step) and FGMRES(30) to the paper's ROW tolerance 1e-6,
+all FP64.  Inputs are larger than L2 (84 MB state, 31 GB of element blocks), so no L2
+flush is needed between steps.
+
+Output: one JSON line with the step wall time (value), the FP64 residual throughput
+(GDOF/s), the roofline of the residual, the end-to-end time through host buffers, the
+oracle baseline on this machine's host cores, the kernel-launch count and the SM clocks.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload (a 4^3 slice at the same CFL, scaled to 32^3).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "implicit step wall time @1e-8 tol: mixed/learned pMG vs FP64; residual GDOF/s"
+FP64_PEAK_NOMINAL = 1.25e12        # GB300 FP64 (vector = tensor), nominal
+SAMPLE_N = 4                       # oracle sample: 4^3 hexes, scaled by (32/4)^3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="frpmg", choices=["frpmg", "reference"])
+    ap.add_argument("--n", type=int, default=32, help="elements per direction")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ oracle (CPU) arm
+def oracle_step_time(n_sample=SAMPLE_N, n_full=32):
+    """Seconds for one oracle ROS34PW2 step on an n_sample^3 slice at the workload's CFL,
+    and the element-count scale to the full mesh."""
+    import oracle
+    from oracle import tableaux as TB
+    from paper_2202_09733_gb300 import workloads as w
+    W = w.tgv3d(n=n_sample)
+    O = oracle.Oracle(W.mesh, W.phys, W.levels)
+    g, a, c, m = TB.ros34pw2()
+    opts = O.opts(kdim=30, maxit_gmres=300, nsmooth=(2, 2), tol_gmres=1e-6, inv_dtau_star=1.0 / W.dt)
+    t0 = time.perf_counter()
+    q, st = O.row_step(g, a, c, m, W.dt, W.q0, opts)
+    dt = time.perf_counter() - t0
+    return dt, (n_full / n_sample) ** 3, st
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t, scale, st = oracle_step_time()
+        if i >= args.warmup:
+            times.append(t * scale)
+    value = statistics.mean(times)
+    sample = (f"oracle ROS34PW2 step, pMG p{{3-2}} n{{2-2}}, on a {SAMPLE_N}^3-hex slice of the 32^3 "
+              f"workload at the same CFL, single thread, scaled by the element count x{(32 // SAMPLE_N) ** 3}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/step", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tgv3d 32^3 hex p=3 (Ma 0.1, Re 1600), ROS34PW2 step, pMG p{3-2} n{2-2}, "
+                                   "FGMRES(30) tol 1e-6", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "s/step", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- GPU arm
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu_index
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.QUERY}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for nm, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    from paper_2202_09733_gb300 import api, workloads as w, tableaux as T, perfmodel as PM
+    from paper_2202_09733_gb300 import build as B, _native as N
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or ws == 1:
+        B.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    lib = N.load()
+
+    W = w.tgv3d(n=args.n)
+    ctx = api.fr_create(W.mesh, W.phys, W.levels)
+    q0 = torch.from_numpy(W.q0).cuda()
+    q = q0.clone()
+    g, a, c, m = T.ros34pw2()
+    opts = api.solve_opts(kdim=30, maxit_gmres=300, nsmooth=(2, 2), tol_gmres=1e-6, inv_dtau_star=1.0 / W.dt)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        q.copy_(q0)
+        return api.row_step(ctx, g, a, c, m, W.dt, q, opts)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        st = step()
+    torch.cuda.synchronize()
+
+    # ---- timed steps (device-resident inputs)
+    clk = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    n0 = lib.fr_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = lib.fr_kernel_launches() - n0
+    clocks = clk.stop()
+    t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    if ws > 1:
+        tt = torch.tensor([t_step], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+
+    # ---- residual throughput and roofline (same stream, CUDA events)
+    R = torch.empty_like(q0)
+    for _ in range(3):
+        api.fr_residual(ctx, 0, q0, R)
+    nrep = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nrep):
+        api.fr_residual(ctx, 0, q0, R)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_R = e0.elapsed_time(e1) / 1e3 / nrep
+    E = W.mesh["E"]
+    ndof = q0.numel()
+    flops = PM.residual_flops(3, 3) * E
+    gdofs = ndof / t_R / 1e9
+
+    # ---- end to end through host buffers (pinned), H2D + step + D2H inside the region
+    q_host = q0.cpu().pin_memory()
+    out_host = torch.empty_like(q_host).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q.copy_(q_host, non_blocking=True)
+        api.row_step(ctx, g, a, c, m, W.dt, q, opts)
+        out_host.copy_(q, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    barrier()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t_s, scale, st_s = oracle_step_time()
+        cpu = {"value": t_s * scale, "unit": "s/step", "cores": 1, "kind": "oracle",
+               "sample": f"one oracle ROS34PW2 step on a {SAMPLE_N}^3-hex slice at the same CFL "
+                         f"({t_s:.1f} s, {st_s['n_gmres']} GMRES iterations), single thread, "
+                         f"scaled by the element count x{int(scale)}"}
+
+    if rank == 0:
+        ng = [s_["n_gmres"] for s_ in stats]
+        line = {
+            "metric": METRIC, "value": t_step, "unit": "s/step", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"tgv3d {args.n}^3 hex p=3 (Ma 0.1, Re 1600), ROS34PW2 step dt=20x explicit, "
+                                   "pMG p{3-2} n{2-2} (blocks + LU at q^n inside the step), FGMRES(30) tol 1e-6, FP64",
+                       "ndof": ndof, "elements": E, "l2": "inputs larger than L2 (state 84 MB, blocks 31 GB): no flush",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "residual_gdofs": gdofs,
+            "residual_ms": t_R * 1e3,
+            "gmres_iterations_per_step": statistics.mean(ng),
+            "roofline": {"kernel": "fr_residual (FP64 FR residual, 8 kernels per launch)", "bound": "alu",
+                         "achieved": flops / t_R / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
+                         "frac": (flops / t_R) / FP64_PEAK_NOMINAL, "traffic": None,
+                         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 entry); "
+                                        "a DFMA-chain probe measured 1.19"},
+            "e2e": {"value": t_e2e, "unit": "s/step", "h2d_bytes_per_step": q_host.numel() * 8,
+                    "d2h_bytes_per_step": q_host.numel() * 8},
+            "cpu_baseline": cpu,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

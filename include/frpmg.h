@@ -80,6 +80,8 @@ typedef struct {
 int fr_create(fr_ctx **out, const fr_mesh_desc *mesh, const fr_physics *phys);
 int fr_destroy(fr_ctx *ctx);
 const char *fr_last_error(void);
+/* number of CUDA kernels this library has launched in the process so far (host counter) */
+unsigned long long fr_kernel_launches(void);
 /* sizes of level l (host out-pointers, any may be NULL): degree, Np, nv*Np*E */
 int fr_level_info(const fr_ctx *ctx, int level, int *p, int *np, long long *ndof);
 /* number of element colours used to assemble the element blocks (host int*) */
@@ -138,7 +140,9 @@ int pmg_precondition(fr_ctx *ctx, const double *q, const double *Rq, const doubl
 /* Restarted right-preconditioned flexible GMRES (CGS2 orthogonalisation) for
  * A x = b with A v = shift v - (R(q + eps v) - R(q))/eps (Eq. 8) and, if use_pmg, the
  * preconditioner of the last pmg_setup.  The FD product is applied to unit-norm
- * directions only.  Stops when ||b - A x|| <= tol ||b|| or after maxit iterations.
+ * directions only.  Stops when the Arnoldi least-squares residual estimate is
+ * <= tol ||b|| or after maxit iterations (stats->relres is that estimate / ||b||); the
+ * true residual is recomputed at each restart to start the next cycle.
  * q, Rq, b, x: device; stats: host (may be NULL). */
 typedef struct {
     int kdim, maxit, use_pmg;

@@ -73,3 +73,5 @@ void frk64_block_column(const FrLevel &L, const int *color, int col, int j, cons
 int frk64_lu_factor(const FrLevel &L, double *M, int *perm, int *info_dev, cudaStream_t s);
 int frk64_lu_solve(const FrLevel &L, const double *M, const int *perm, double *x, cudaStream_t s);
 int frk64_transfer(const FrLevel &Lf, const FrLevel &Lc, bool restrict_, const double *x, double *y, cudaStream_t s);
+
+unsigned long long frk64_launch_count();

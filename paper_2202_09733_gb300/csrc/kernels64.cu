@@ -7,6 +7,10 @@
 #include "fr_device.cuh"
 #include "fr_lib.h"
 
+static unsigned long long g_launches = 0;
+unsigned long long frk64_launch_count() { return g_launches; }
+#define CNT() (++g_launches)
+
 __constant__ FrTab<double> c_tab64[FR_MAXP + 1];
 __constant__ double c_gam64[FR_MAXP + 1][FR_MAXP + 1][FR_MAXN][FR_MAXN];
 __constant__ double c_pi64[FR_MAXP + 1][FR_MAXP + 1][FR_MAXN][FR_MAXN];
@@ -38,14 +42,14 @@ template <int D, int P>
 static void residual_t(const FrLevel &L, const FrPhys<double> &ph, const double *q, double *R, cudaStream_t s) {
     using S = Sh<D, P>;
     const int E = L.E, gx = (E + 127) / 128, gp = (L.npairs + 127) / 128;
-    k_interp<D, P, double><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, E);
-    k_pair_common<D, P, double><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.dq, E, ph);
-    k_grad_sp<D, P, double><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(q, L.dq, L.G, L.Q, E);
-    k_grad_fp<D, P, double><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
-    k_pair_flux<D, P, double><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.Qf, L.Sf, L.fn, E, ph);
-    k_vflux<D, P, double><<<dim3(gx, S::np), 128, 0, s>>>(q, L.Q, L.S, L.Ft, E, ph);
-    k_face_ft<D, P, double><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(L.Ft, L.Ftf, E);
-    k_div<D, P, double><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
+    CNT(); k_interp<D, P, double><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, E);
+    CNT(); k_pair_common<D, P, double><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.dq, E, ph);
+    CNT(); k_grad_sp<D, P, double><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(q, L.dq, L.G, L.Q, E);
+    CNT(); k_grad_fp<D, P, double><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
+    CNT(); k_pair_flux<D, P, double><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.Qf, L.Sf, L.fn, E, ph);
+    CNT(); k_vflux<D, P, double><<<dim3(gx, S::np), 128, 0, s>>>(q, L.Q, L.S, L.Ft, E, ph);
+    CNT(); k_face_ft<D, P, double><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(L.Ft, L.Ftf, E);
+    CNT(); k_div<D, P, double><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
 }
 
 int frk64_residual(const FrLevel &L, const FrPhysH &h, const double *q, double *R, cudaStream_t s) {
@@ -114,36 +118,36 @@ __global__ void k_lincomb(long long n, int m, Ptr8 X, const double *base, double
 }
 
 void frk64_axpy_perturb(long long n, const double *q, double eps, const double *v, double *qp, cudaStream_t s) {
-    k_axpy_perturb<<<nblk(n), 256, 0, s>>>(n, q, eps, v, qp);
+    CNT(); k_axpy_perturb<<<nblk(n), 256, 0, s>>>(n, q, eps, v, qp);
 }
 void frk64_jv_finish(long long n, double shift, const double *v, const double *Rp, const double *Rq, double eps,
                      double *Av, cudaStream_t s) {
-    k_jv_finish<<<nblk(n), 256, 0, s>>>(n, shift, v, Rp, Rq, eps, Av);
+    CNT(); k_jv_finish<<<nblk(n), 256, 0, s>>>(n, shift, v, Rp, Rq, eps, Av);
 }
-void frk64_scale(long long n, double a, const double *x, double *y, cudaStream_t s) { k_scale<<<nblk(n), 256, 0, s>>>(n, a, x, y); }
+void frk64_scale(long long n, double a, const double *x, double *y, cudaStream_t s) { CNT(); k_scale<<<nblk(n), 256, 0, s>>>(n, a, x, y); }
 void frk64_div_scalar(long long n, const double *x, double a, double *y, cudaStream_t s) {
-    k_div_scalar<<<nblk(n), 256, 0, s>>>(n, x, a, y);
+    CNT(); k_div_scalar<<<nblk(n), 256, 0, s>>>(n, x, a, y);
 }
-void frk64_copy(long long n, const double *x, double *y, cudaStream_t s) { k_copy<<<nblk(n), 256, 0, s>>>(n, x, y); }
-void frk64_add(long long n, const double *a, const double *b, double *y, cudaStream_t s) { k_add<<<nblk(n), 256, 0, s>>>(n, a, b, y); }
-void frk64_sub(long long n, const double *a, const double *b, double *y, cudaStream_t s) { k_sub<<<nblk(n), 256, 0, s>>>(n, a, b, y); }
-void frk64_neg(long long n, const double *x, double *y, cudaStream_t s) { k_neg<<<nblk(n), 256, 0, s>>>(n, x, y); }
+void frk64_copy(long long n, const double *x, double *y, cudaStream_t s) { CNT(); k_copy<<<nblk(n), 256, 0, s>>>(n, x, y); }
+void frk64_add(long long n, const double *a, const double *b, double *y, cudaStream_t s) { CNT(); k_add<<<nblk(n), 256, 0, s>>>(n, a, b, y); }
+void frk64_sub(long long n, const double *a, const double *b, double *y, cudaStream_t s) { CNT(); k_sub<<<nblk(n), 256, 0, s>>>(n, a, b, y); }
+void frk64_neg(long long n, const double *x, double *y, cudaStream_t s) { CNT(); k_neg<<<nblk(n), 256, 0, s>>>(n, x, y); }
 void frk64_pmg_rhs(long long n, double c, const double *d, const double *qh, const double *b, const double *Rqh,
                    const double *Rb, double *rhs, cudaStream_t s) {
-    k_pmg_rhs<<<nblk(n), 256, 0, s>>>(n, c, d, qh, b, Rqh, Rb, rhs);
+    CNT(); k_pmg_rhs<<<nblk(n), 256, 0, s>>>(n, c, d, qh, b, Rqh, Rb, rhs);
 }
 void frk64_stage_F(long long n, const double *q, const double *sv, double adt, const double *R, double *F, cudaStream_t s) {
-    k_stage_F<<<nblk(n), 256, 0, s>>>(n, q, sv, adt, R, F);
+    CNT(); k_stage_F<<<nblk(n), 256, 0, s>>>(n, q, sv, adt, R, F);
 }
 void frk64_add_div(long long n, const double *a, const double *acc, double dt, double *y, cudaStream_t s) {
-    k_add_div<<<nblk(n), 256, 0, s>>>(n, a, acc, dt, y);
+    CNT(); k_add_div<<<nblk(n), 256, 0, s>>>(n, a, acc, dt, y);
 }
 void frk64_lincomb(long long n, int m, const double *coef, const double *const *X, const double *base, double scale,
                    double *y, cudaStream_t s) {
     // m <= 8 (time-integration stages)
     Ptr8 P;
     for (int j = 0; j < 8; ++j) { P.p[j] = j < m ? X[j] : nullptr; P.c[j] = j < m ? coef[j] : 0.0; }
-    k_lincomb<<<nblk(n), 256, 0, s>>>(n, m, P, base, scale, scale != 1.0, y);
+    CNT(); k_lincomb<<<nblk(n), 256, 0, s>>>(n, m, P, base, scale, scale != 1.0, y);
 }
 
 // ------------------------------------------------------------------- reductions
@@ -204,16 +208,16 @@ int frk64_multidot(long long n, int m, const double *w, const double *const *V, 
         Ptr8 P;
         for (int j = 0; j < 8; ++j) { P.p[j] = j < mm ? V[j0 + j] : nullptr; P.c[j] = 0.0; }
         switch (mm) {
-            case 1: k_multidot_partial<1><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break;
-            case 2: k_multidot_partial<2><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break;
-            case 3: k_multidot_partial<3><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break;
-            case 4: k_multidot_partial<4><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break;
-            case 5: k_multidot_partial<5><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break;
-            case 6: k_multidot_partial<6><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break;
-            case 7: k_multidot_partial<7><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break;
-            default: k_multidot_partial<8><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break;
+            case 1: { CNT(); k_multidot_partial<1><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
+            case 2: { CNT(); k_multidot_partial<2><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
+            case 3: { CNT(); k_multidot_partial<3><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
+            case 4: { CNT(); k_multidot_partial<4><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
+            case 5: { CNT(); k_multidot_partial<5><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
+            case 6: { CNT(); k_multidot_partial<6><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
+            case 7: { CNT(); k_multidot_partial<7><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
+            default: { CNT(); k_multidot_partial<8><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
         }
-        k_multidot_final<<<1, 32, 0, s>>>(nb, mm, g_partial, out + j0);
+        CNT(); k_multidot_final<<<1, 32, 0, s>>>(nb, mm, g_partial, out + j0);
     }
     return 0;
 }
@@ -230,7 +234,7 @@ void frk64_multi_axpy(long long n, int m, const double *h_dev, const double *con
         int mm = std::min(8, m - j0);
         Ptr8 P;
         for (int j = 0; j < 8; ++j) { P.p[j] = j < mm ? V[j0 + j] : nullptr; P.c[j] = 0.0; }
-        k_multi_axpy<<<nblk(n), 256, 0, s>>>(n, mm, h_dev + j0, P, w);
+        CNT(); k_multi_axpy<<<nblk(n), 256, 0, s>>>(n, mm, h_dev + j0, P, w);
     }
 }
 __global__ void k_update_x(long long n, int m, Ptr8 Z, double *x) {
@@ -245,7 +249,7 @@ void frk64_update_x(long long n, int m, const double *y, const double *const *Z,
         int mm = std::min(8, m - j0);
         Ptr8 P;
         for (int j = 0; j < 8; ++j) { P.p[j] = j < mm ? Z[j0 + j] : nullptr; P.c[j] = j < mm ? y[j0 + j] : 0.0; }
-        k_update_x<<<nblk(n), 256, 0, s>>>(n, mm, P, x);
+        CNT(); k_update_x<<<nblk(n), 256, 0, s>>>(n, mm, P, x);
     }
 }
 
@@ -299,14 +303,14 @@ __global__ void __launch_bounds__(256) k_block_column(int E, int nd, const int *
     }
 }
 void frk64_perturb_color(const FrLevel &L, const int *color, int col, int j, const double *q, double *qp, cudaStream_t s) {
-    k_perturb_color<<<(L.E + 255) / 256, 256, 0, s>>>(L.E, color, col, j, q, qp);
+    CNT(); k_perturb_color<<<(L.E + 255) / 256, 256, 0, s>>>(L.E, color, col, j, q, qp);
 }
 void frk64_restore_color(const FrLevel &L, const int *color, int col, int j, const double *q, double *qp, cudaStream_t s) {
-    k_restore_color<<<(L.E + 255) / 256, 256, 0, s>>>(L.E, color, col, j, q, qp);
+    CNT(); k_restore_color<<<(L.E + 255) / 256, 256, 0, s>>>(L.E, color, col, j, q, qp);
 }
 void frk64_block_column(const FrLevel &L, const int *color, int col, int j, const double *q, const double *R0,
                         const double *Rp, double shift, double *M, cudaStream_t s) {
-    k_block_column<<<(L.E + 31) / 32, 256, 0, s>>>(L.E, L.nd, color, col, j, q, R0, Rp, shift, M);
+    CNT(); k_block_column<<<(L.E + 31) / 32, 256, 0, s>>>(L.E, L.nd, color, col, j, q, R0, Rp, shift, M);
 }
 
 // ------------------------------------------------------------------------ block LU
@@ -384,9 +388,9 @@ int frk64_lu_factor(const FrLevel &L, double *M, int *perm, int *info, cudaStrea
             cudaFuncSetAttribute(k_lu_factor<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             attr = true;
         }
-        k_lu_factor<true><<<L.E, 256, sm, s>>>(M, perm, L.nd, info);
+        CNT(); k_lu_factor<true><<<L.E, 256, sm, s>>>(M, perm, L.nd, info);
     } else {
-        k_lu_factor<false><<<L.E, 256, 0, s>>>(M, perm, L.nd, info);
+        CNT(); k_lu_factor<false><<<L.E, 256, 0, s>>>(M, perm, L.nd, info);
     }
     return 0;
 }
@@ -448,15 +452,15 @@ int frk64_lu_solve(const FrLevel &L, const double *M, const int *perm, double *x
     int nr = (L.nd + 31) / 32;
     int grid = (L.E * 32 + 127) / 128;
     switch (nr) {
-        case 1: k_lu_solve<1><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break;
-        case 2: k_lu_solve<2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break;
-        case 3: k_lu_solve<3><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break;
-        case 4: k_lu_solve<4><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break;
-        case 5: k_lu_solve<5><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break;
-        case 6: k_lu_solve<6><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break;
-        case 7: k_lu_solve<7><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break;
-        case 8: k_lu_solve<8><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break;
-        case 10: k_lu_solve<10><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break;
+        case 1: { CNT(); k_lu_solve<1><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 2: { CNT(); k_lu_solve<2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 3: { CNT(); k_lu_solve<3><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 4: { CNT(); k_lu_solve<4><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 5: { CNT(); k_lu_solve<5><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 6: { CNT(); k_lu_solve<6><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 7: { CNT(); k_lu_solve<7><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 8: { CNT(); k_lu_solve<8><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 10: { CNT(); k_lu_solve<10><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
         default: return -1;
     }
     return 0;
@@ -509,8 +513,8 @@ int frk64_transfer(const FrLevel &Lf, const FrLevel &Lc, bool r, const double *x
     int p0 = Lf.p, p1 = Lc.p, E = Lf.E, nv = Lf.nv;
     int ni = r ? p0 + 1 : p1 + 1, no = r ? p1 + 1 : p0 + 1;
     dim3 grid((E + 127) / 128, nv);
-    if (Lf.d == 2 && p0 <= 5) k_tensor<2, 6><<<grid, 128, 0, s>>>(x, y, E, ni, no, p0, p1, r);
-    else if (Lf.d == 3 && p0 <= 3) k_tensor<3, 4><<<grid, 128, 0, s>>>(x, y, E, ni, no, p0, p1, r);
+    if (Lf.d == 2 && p0 <= 5) { CNT(); k_tensor<2, 6><<<grid, 128, 0, s>>>(x, y, E, ni, no, p0, p1, r); }
+    else if (Lf.d == 3 && p0 <= 3) { CNT(); k_tensor<3, 4><<<grid, 128, 0, s>>>(x, y, E, ni, no, p0, p1, r); }
     else return -1;
     return 0;
 }

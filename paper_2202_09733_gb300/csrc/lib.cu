@@ -98,6 +98,8 @@ static cudaStream_t S_(void *s) { return (cudaStream_t)s; }
 
 extern "C" const char *fr_last_error(void) { return g_err; }
 
+extern "C" unsigned long long fr_kernel_launches(void) { return frk64_launch_count(); }
+
 // ---------------------------------------------------------------- context set-up
 static int upload_tables() {
     static FrTabH tabs[6];
@@ -490,9 +492,10 @@ static int gmres(fr_ctx *C, const double *q, const double *Rq, const double *b, 
     std::vector<double> H((size_t)(K + 1) * K, 0.0), cs(K), sn(K), g(K + 1), y(K), h(32), h2(32);
     CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     frk64_copy(n, b, r, s);
-    double bnorm, beta;
+    double bnorm, beta, est;
     TRY(norm2(C, n, b, &bnorm, s));
     beta = bnorm;
+    est = bnorm;
     int total = 0, restarts = 0;
     fr_gmres_stats loc = {0, 0, 0.0};
     if (bnorm == 0.0) { if (st) *st = loc; return FR_OK; }
@@ -541,7 +544,8 @@ static int gmres(fr_ctx *C, const double *q, const double *Rq, const double *b, 
             g[j + 1] = -sn[j] * g[j];
             g[j] = cs[j] * g[j];
             ++total; jj = j + 1;
-            if (fabs(g[j + 1]) <= o->tol * bnorm || total >= o->maxit || hn == 0.0) break;
+            est = fabs(g[j + 1]);
+            if (est <= o->tol * bnorm || total >= o->maxit || hn == 0.0) break;
         }
         for (int i = jj - 1; i >= 0; --i) {
             double sacc = g[i];
@@ -549,6 +553,8 @@ static int gmres(fr_ctx *C, const double *q, const double *Rq, const double *b, 
             y[i] = sacc / H[(size_t)i * K + i];
         }
         frk64_update_x(n, jj, y.data(), Zp.data(), x, s);
+        if (est <= o->tol * bnorm || total >= o->maxit) break;
+        // restart: true residual of the current iterate starts the next cycle
         double xn;
         TRY(norm2(C, n, x, &xn, s));
         if (xn > 0.0) {
@@ -561,10 +567,10 @@ static int gmres(fr_ctx *C, const double *q, const double *Rq, const double *b, 
         }
         TRY(norm2(C, n, r, &beta, s));
         if (!isfinite(beta)) return fail(FR_ERR_NONFINITE, "non-finite GMRES residual");
-        if (beta <= o->tol * bnorm || total >= o->maxit) break;
         ++restarts;
     }
-    loc.iters = total; loc.restarts = restarts; loc.relres = beta / bnorm;
+    CK(cudaStreamSynchronize(s));
+    loc.iters = total; loc.restarts = restarts; loc.relres = est / bnorm;
     if (st) *st = loc;
     return FR_OK;
 }

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "frpmg.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:(?:const|unsigned|long)\s+)*\w+(?:\s+|\s*\*\s*)(\w+)\s*\(", src, flags=re.M)
     return sorted(set(n for n in names if n not in ("if", "while")))
 
 

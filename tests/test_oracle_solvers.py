@@ -201,3 +201,12 @@ def test_steady_ptc_ser_converges():
     dtau0 = 0.1 * W.mesh["h_min"] / (1.0 + 1.0 / 0.2)
     q, st = O.ptc_steady(W.q0, dtau0, 1e6, 1e-7, 80, opts)
     assert st["converged"] and st["final_res"] <= 1e-7
+
+
+def test_library_tableaux_match_oracle_tableaux():
+    from paper_2202_09733_gb300 import tableaux as GT
+    A1, b1, _ = TB.esdirk3()
+    A2, b2 = GT.esdirk3()
+    assert np.array_equal(A1, A2) and np.array_equal(b1, b2)
+    for x, y in zip(TB.ros34pw2(), GT.ros34pw2()):
+        assert np.allclose(x, y, rtol=1e-15, atol=1e-15)
