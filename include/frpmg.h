@@ -92,6 +92,23 @@ int fr_num_colors(const fr_ctx *ctx, int *ncolors);
  * common fluxes), so that dq/dt = R.  q, R: device, [nv][Np][E]; q and R must not alias. */
 int fr_residual(fr_ctx *ctx, int level, const double *q, double *R, void *stream);
 
+/* The same residual as fr_residual (same kernels, same result bit for bit), for callers
+ * that cannot allocate device memory when they call it: code under CUDA stream capture
+ * in the global capture mode, where cudaMalloc is refused; hosts whose device memory is
+ * owned by another allocator with a fixed budget; real-time loops that must not pay for,
+ * or risk the failure of, an allocation.  The paper has no counterpart: this is a
+ * property of the library, not of the method.  The stage scratch (flux-point traces,
+ * gradients, common fluxes) comes from one file-scope device array of 16 MiB
+ * (2 Mi doubles) that every GPU loading the library holds until the process exits; no
+ * cudaMalloc, cudaFree or allocating routine is called.  A level whose scratch needs
+ * more than the array (4 nv Nfp E + 2 d nv Np E + d nv Nfp E doubles, each part rounded
+ * up to 32) is rejected with FR_ERR_INVALID_ARG.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress), so make it before any stream
+ * capture.  Every scratch value is written before it is read within a call; all calls
+ * share the array, so calls whose GPU work overlaps (other streams, contexts or host
+ * threads) race on it.  q, R: device [nv][Np][E], not aliased. */
+int fr_residual_noalloc(fr_ctx *ctx, int level, const double *q, double *R, void *stream);
+
 /* Eq. (8): Av = shift v - (R(q + eps v) - Rq) / eps on the finest level; Rq must be R(q).
  * q, Rq, v, Av: device [nv][Np][E]; Av must not alias the inputs. */
 int fr_jvp(fr_ctx *ctx, const double *q, const double *Rq, const double *v, double eps,

@@ -17,7 +17,8 @@ ERRORS = {-1: "FR_ERR_INVALID_ARG", -2: "FR_ERR_CUDA", -3: "FR_ERR_OOM", -4: "FR
           -5: "FR_ERR_NONFINITE", -6: "FR_ERR_BREAKDOWN", -7: "FR_ERR_UNIMPLEMENTED", -8: "FR_ERR_NOT_READY"}
 
 # every symbol the header declares
-EXPORTS = ["fr_create", "fr_destroy", "fr_last_error", "fr_kernel_launches", "fr_level_info", "fr_num_colors", "fr_residual", "fr_jvp",
+EXPORTS = ["fr_create", "fr_destroy", "fr_last_error", "fr_kernel_launches", "fr_level_info", "fr_num_colors", "fr_residual",
+           "fr_residual_noalloc", "fr_jvp",
            "fr_elem_blocks", "fr_block_factor", "fr_block_solve", "fr_restrict", "fr_prolong", "pmg_setup",
            "pmg_precondition", "gmres_solve", "esdirk_step", "row_step", "ptc_steady"]
 
@@ -84,6 +85,7 @@ def load(path: str = LIB_PATH):
         "fr_level_info": ([VP, C.c_int, PI, PI, C.POINTER(C.c_longlong)], C.c_int),
         "fr_num_colors": ([VP, PI], C.c_int),
         "fr_residual": ([VP, C.c_int, VP, VP, VP], C.c_int),
+        "fr_residual_noalloc": ([VP, C.c_int, VP, VP, VP], C.c_int),
         "fr_jvp": ([VP, VP, VP, VP, C.c_double, C.c_double, VP, VP], C.c_int),
         "fr_elem_blocks": ([VP, C.c_int, VP, C.c_double, VP, VP], C.c_int),
         "fr_block_factor": ([VP, C.c_int, VP, VP, VP], C.c_int),

@@ -3,6 +3,7 @@
 Translation units:
   csrc/kernels64.cu   FP64 kernels, nvcc -fmad=false (only explicit fma contractions)
   csrc/lib.cu         C ABI and host orchestration
+  csrc/noalloc.cu     fr_residual_noalloc (stage scratch in a fixed device array)
   csrc/host_tables.c  binary128 operator tables         (gcc -ffp-contract=off)
   csrc/host_geometry.c geometric factors, connectivity  (gcc -ffp-contract=off)
 """
@@ -35,6 +36,7 @@ def _units():
     return [
         ([nv] + common + ["-fmad=false", "-c"], "kernels64.cu"),
         ([nv] + common + ["-c"], "lib.cu"),
+        ([nv] + common + ["-c"], "noalloc.cu"),
         (["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC"] + inc + ["-c"], "host_tables.c"),
         (["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC"] + inc + ["-c"], "host_geometry.c"),
     ]

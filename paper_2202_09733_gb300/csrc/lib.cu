@@ -236,6 +236,15 @@ extern "C" int fr_num_colors(const fr_ctx *C, int *n) {
     return FR_OK;
 }
 
+// read-only access to a level for other translation units of the library
+int fr_internal_level(const fr_ctx *C, int l, FrLevel *out, FrPhysH *ph) {
+    if (l < 0 || l >= C->nlev) return FR_ERR_INVALID_ARG;
+    *out = C->L[l];
+    *ph = C->ph;
+    return FR_OK;
+}
+int fr_internal_fail(int code, const char *msg) { return fail(code, "%s", msg); }
+
 // ------------------------------------------------------------------ residual, Jv
 static int residual(fr_ctx *C, int l, const double *q, double *R, cudaStream_t s) {
     if (frk64_residual(C->L[l], C->ph, q, R, s) != 0) return fail(FR_ERR_UNIMPLEMENTED, "no kernel for d=%d p=%d", C->d, C->L[l].p);
