@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--impl", default="frpmg", choices=["frpmg", "reference"])
     ap.add_argument("--n", type=int, default=32, help="elements per direction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="preconditioner precision of the timed step (the FP64 step is timed alongside)")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
 
 
@@ -164,12 +167,15 @@ def gpu_arm(args):
     q0 = torch.from_numpy(W.q0).cuda()
     q = q0.clone()
     g, a, c, m = T.ros34pw2()
-    opts = api.solve_opts(kdim=30, maxit_gmres=300, nsmooth=(2, 2), tol_gmres=1e-6, inv_dtau_star=1.0 / W.dt)
+    opts = api.solve_opts(kdim=30, maxit_gmres=300, nsmooth=(2, 2), tol_gmres=1e-6, inv_dtau_star=1.0 / W.dt,
+                          precision=args.precision)
+    opts64 = api.solve_opts(kdim=30, maxit_gmres=300, nsmooth=(2, 2), tol_gmres=1e-6, inv_dtau_star=1.0 / W.dt,
+                            precision="fp64")
     stream = torch.cuda.current_stream()
 
-    def step():
+    def step(o=opts):
         q.copy_(q0)
-        return api.row_step(ctx, g, a, c, m, W.dt, q, opts)
+        return api.row_step(ctx, g, a, c, m, W.dt, q, o)
 
     def barrier():
         if ws > 1:
@@ -199,6 +205,21 @@ def gpu_arm(args):
         tt = torch.tensor([t_step], device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_step = float(tt.item())
+
+    q_mixed = q.clone()
+
+    # ---- the plain FP64 JFNK-pMG step on the same input, for comparison
+    t_fp64, st64, dq = None, None, None
+    if args.precision != "fp64" and not args.no_fp64_compare:
+        st64 = step(opts64)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        st64 = step(opts64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t_fp64 = f0.elapsed_time(f1) / 1e3
+        dq = float(((q_mixed - q).abs().max() / q.abs().max()).item())
 
     # ---- residual throughput and roofline (same stream, CUDA events)
     R = torch.empty_like(q0)
@@ -246,11 +267,18 @@ def gpu_arm(args):
         line = {
             "metric": METRIC, "value": t_step, "unit": "s/step", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic",
             "config": {"workload": f"tgv3d {args.n}^3 hex p=3 (Ma 0.1, Re 1600), ROS34PW2 step dt=20x explicit, "
-                                   "pMG p{3-2} n{2-2} (blocks + LU at q^n inside the step), FGMRES(30) tol 1e-6, FP64",
+                                   "pMG p{3-2} n{2-2} (blocks + LU at q^n inside the step), FGMRES(30) tol 1e-6",
+                       "precision": ("FP64 throughout" if args.precision == "fp64" else
+                                     "mixed: FP64 residual, Jv, Gram-Schmidt, update; FP32 pMG cycle, blocks, LU"),
                        "ndof": ndof, "elements": E, "l2": "inputs larger than L2 (state 84 MB, blocks 31 GB): no flush",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "fp64_step_s": t_fp64,
+            "speedup_vs_fp64_step": (t_fp64 / t_step) if t_fp64 else None,
+            "fp64_step_gmres_iterations": st64["n_gmres"] if st64 else None,
+            "mixed_vs_fp64_state_maxrel": dq,
             "residual_gdofs": gdofs,
             "residual_ms": t_R * 1e3,
             "gmres_iterations_per_step": statistics.mean(ng),

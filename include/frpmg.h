@@ -140,12 +140,19 @@ int fr_prolong(fr_ctx *ctx, int level, const double *x_coarse, double *x_fine, v
  * nsmooth[l] = smoothing steps on level l (pre and post on levels with a coarser one).
  * pmg_setup evaluates and factors the element blocks (1/dtau* + c) I - J_ee on every level
  * at q_ref restricted level by level (device state), and keeps them until the next
- * pmg_setup or fr_destroy. */
+ * pmg_setup or fr_destroy.
+ * precision 0: everything in FP64 (reproducible, see Arithmetic).  precision 1 (mixed):
+ * the cycle, its residuals on every level, the element blocks and their LU factors and
+ * solves run in FP32, the blocks' columns by forward-mode differentiation of the FP32
+ * residual (exact derivatives, no finite-difference noise); X is scaled on the
+ * device so that ||Y||_inf ~ 1e-3 ||q_ref||_inf inside the cycle (keeping R(qh) - R(q)
+ * clear of FP32 rounding) and Y is scaled back and returned in FP64. */
 typedef struct {
     int nlevels;
     int nsmooth[4];
     double c;
     double inv_dtau_star;
+    int precision;
 } fr_pmg_opts;
 int pmg_setup(fr_ctx *ctx, const double *q_ref, const fr_pmg_opts *opts, void *stream);
 /* Y ~ A^{-1} X: one V-cycle of pseudo-time marching of
@@ -176,6 +183,7 @@ int gmres_solve(fr_ctx *ctx, const double *q, const double *Rq, const double *b,
 typedef struct {
     int kdim, maxit_gmres, max_ptc, nlevels, nsmooth[4], use_pmg;
     double tol_gmres, tol_newton, eps, dtau, inv_dtau_star;
+    int precision;   /* preconditioner precision, as fr_pmg_opts.precision */
 } fr_solve_opts;
 typedef struct {
     int n_ptc, n_gmres, converged;

@@ -34,7 +34,8 @@ class Physics(C.Structure):
 
 
 class PmgOpts(C.Structure):
-    _fields_ = [("nlevels", C.c_int), ("nsmooth", C.c_int * 4), ("c", C.c_double), ("inv_dtau_star", C.c_double)]
+    _fields_ = [("nlevels", C.c_int), ("nsmooth", C.c_int * 4), ("c", C.c_double), ("inv_dtau_star", C.c_double),
+                ("precision", C.c_int)]
 
 
 class GmresOpts(C.Structure):
@@ -50,7 +51,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("kdim", C.c_int), ("maxit_gmres", C.c_int), ("max_ptc", C.c_int), ("nlevels", C.c_int),
                 ("nsmooth", C.c_int * 4), ("use_pmg", C.c_int), ("tol_gmres", C.c_double),
                 ("tol_newton", C.c_double), ("eps", C.c_double), ("dtau", C.c_double),
-                ("inv_dtau_star", C.c_double)]
+                ("inv_dtau_star", C.c_double), ("precision", C.c_int)]
 
 
 class StepStats(C.Structure):

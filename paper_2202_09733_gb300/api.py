@@ -130,12 +130,14 @@ def fr_prolong(ctx, level, xc, xf=None, stream=None):
     return xf
 
 
-def pmg_setup(ctx, q_ref, nsmooth, c, inv_dtau_star, stream=None):
+def pmg_setup(ctx, q_ref, nsmooth, c, inv_dtau_star, precision="fp64", stream=None):
+    """precision: "fp64" (reproducible) or "mixed" (FP32 cycle, blocks and LU)."""
     o = N.PmgOpts()
     o.nlevels = len(nsmooth)
     for i, n in enumerate(nsmooth):
         o.nsmooth[i] = int(n)
     o.c, o.inv_dtau_star = float(c), float(inv_dtau_star)
+    o.precision = _prec(precision)
     N.check(N.load().pmg_setup(ctx.handle, _dev(q_ref), C.byref(o), _stream(stream)), "pmg_setup")
 
 
@@ -156,14 +158,23 @@ def gmres_solve(ctx, q, Rq, b, x=None, kdim=30, maxit=300, tol=1e-1, eps=1e-6, s
     return x, dict(iters=st.iters, restarts=st.restarts, relres=st.relres)
 
 
+def _prec(p):
+    if p in ("fp64", 0, None):
+        return 0
+    if p in ("mixed", "fp32", 1):
+        return 1
+    raise ValueError(f"precision must be 'fp64' or 'mixed', not {p!r}")
+
+
 def solve_opts(kdim=30, maxit_gmres=300, max_ptc=100, nsmooth=(2, 2), use_pmg=True, tol_gmres=1e-1,
-               tol_newton=1e-8, eps=1e-6, dtau=1.0, inv_dtau_star=0.0):
+               tol_newton=1e-8, eps=1e-6, dtau=1.0, inv_dtau_star=0.0, precision="fp64"):
     o = N.SolveOpts()
     o.kdim, o.maxit_gmres, o.max_ptc, o.nlevels = int(kdim), int(maxit_gmres), int(max_ptc), len(nsmooth)
     for i, n in enumerate(nsmooth):
         o.nsmooth[i] = int(n)
     o.use_pmg, o.tol_gmres, o.tol_newton, o.eps = int(bool(use_pmg)), float(tol_gmres), float(tol_newton), float(eps)
     o.dtau, o.inv_dtau_star = float(dtau), float(inv_dtau_star)
+    o.precision = _prec(precision)
     return o
 
 

@@ -2,6 +2,8 @@
 
 Translation units:
   csrc/kernels64.cu   FP64 kernels, nvcc -fmad=false (only explicit fma contractions)
+  csrc/kernels32.cu   FP32 kernels of the mixed-precision preconditioner
+  csrc/kernelsad.cu   FP32 forward-mode (dual-number) residual for the FP32 element blocks
   csrc/lib.cu         C ABI and host orchestration
   csrc/noalloc.cu     fr_residual_noalloc (stage scratch in a fixed device array)
   csrc/host_tables.c  binary128 operator tables         (gcc -ffp-contract=off)
@@ -35,6 +37,8 @@ def _units():
     common = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"] + inc
     return [
         ([nv] + common + ["-fmad=false", "-c"], "kernels64.cu"),
+        ([nv] + common + ["-c"], "kernels32.cu"),
+        ([nv] + common + ["-c"], "kernelsad.cu"),
         ([nv] + common + ["-c"], "lib.cu"),
         ([nv] + common + ["-c"], "noalloc.cu"),
         (["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC"] + inc + ["-c"], "host_tables.c"),

@@ -14,6 +14,10 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include "fr_dual.cuh"
+
+// Arithmetic type T of a kernel and the base type B = FrBase<T>::type of its operator
+// tables and geometric factors: B = T for double and float; float for DualF.
 
 #define FR_MAXN 6
 #define FR_MAXP 5
@@ -84,8 +88,8 @@ __device__ __forceinline__ int fp_at(int df, int s, int a, int b) {
 }
 
 // ---------------------------------------------------------------------------- physics
-template <int D, typename T>
-__device__ __forceinline__ void flux_inviscid(const FrPhys<T> &ph, const T *q, T f[3][5]) {
+template <int D, typename T, typename B>
+__device__ __forceinline__ void flux_inviscid(const FrPhys<B> &ph, const T *q, T f[3][5]) {
     T rho = q[0], E = q[D + 1], rinv = T(1) / rho, u[3], ke = T(0);
 #pragma unroll
     for (int j = 0; j < D; ++j) u[j] = q[1 + j] * rinv;
@@ -105,8 +109,8 @@ __device__ __forceinline__ void flux_inviscid(const FrPhys<T> &ph, const T *q, T
     }
 }
 
-template <int D, typename T>
-__device__ __forceinline__ void flux_viscous(const FrPhys<T> &ph, const T *q, const T Q[3][5], bool adiabatic,
+template <int D, typename T, typename B>
+__device__ __forceinline__ void flux_viscous(const FrPhys<B> &ph, const T *q, const T Q[3][5], bool adiabatic,
                                              T f[3][5]) {
     T rho = q[0], E = q[D + 1], rinv = T(1) / rho, Er = E * rinv, u[3];
     T du[3][3], de[3], tau[3][3];
@@ -149,16 +153,16 @@ __device__ __forceinline__ void flux_viscous(const FrPhys<T> &ph, const T *q, co
 }
 
 // Rusanov flux along the (scaled) normal n
-template <int D, typename T>
-__device__ __forceinline__ void rusanov(const FrPhys<T> &ph, const T *qL, const T *qR, const T *n, T *F) {
+template <int D, typename T, typename B>
+__device__ __forceinline__ void rusanov(const FrPhys<B> &ph, const T *qL, const T *qR, const B *n, T *F) {
     constexpr int nv = D + 2;
     T fL[3][5], fR[3][5];
-    flux_inviscid<D>(ph, qL, fL);
-    flux_inviscid<D>(ph, qR, fR);
-    T nn = T(0);
+    flux_inviscid<D, T, B>(ph, qL, fL);
+    flux_inviscid<D, T, B>(ph, qR, fR);
+    B nn = B(0);
 #pragma unroll
     for (int c = 0; c < D; ++c) nn = fma(n[c], n[c], nn);
-    T nmag = sqrt(nn);
+    B nmag = sqrt(nn);
     T lam[2];
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
@@ -186,11 +190,11 @@ __device__ __forceinline__ void rusanov(const FrPhys<T> &ph, const T *qL, const 
     }
 }
 
-template <int D, typename T>
-__device__ __forceinline__ void ghost_state(const FrPhys<T> &ph, int bc, const T *qL, T *qR) {
+template <int D, typename T, typename B>
+__device__ __forceinline__ void ghost_state(const FrPhys<B> &ph, int bc, const T *qL, T *qR) {
     if (bc == 1) {
 #pragma unroll
-        for (int v = 0; v < D + 2; ++v) qR[v] = ph.qinf[v];
+        for (int v = 0; v < D + 2; ++v) qR[v] = T(ph.qinf[v]);
     } else {
         qR[0] = qL[0];
 #pragma unroll
@@ -215,7 +219,8 @@ __global__ void __launch_bounds__(128) k_interp(const T *__restrict__ q, T *__re
     int v = blockIdx.y / S::nfp, k = blockIdx.y - v * S::nfp;
     int df, s, a, b;
     fp_decode<D, N>(k, df, s, a, b);
-    const FrTab<T> &tb = frtab<T>(P);
+    typedef typename FrBase<T>::type B;
+    const FrTab<B> &tb = frtab<B>(P);
     T acc = T(0);
 #pragma unroll
     for (int m = 0; m < N; ++m) {
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(128) k_interp(const T *__restrict__ q, T *__re
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(128) k_pair_common(const int4 *__restrict__ pairs, const int *__restrict__ bcs,
                                                      int npairs, const T *__restrict__ qf, T *__restrict__ dq, int E,
-                                                     FrPhys<T> ph) {
+                                                     FrPhys<typename FrBase<T>::type> ph) {
     using S = Sh<D, P>;
     int P_ = blockIdx.x * blockDim.x + threadIdx.x;
     if (P_ >= npairs) return;
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(128) k_pair_common(const int4 *__restrict__ pa
 #pragma unroll
         for (int v = 0; v < S::nv; ++v) qR[v] = qf[(size_t)(v * S::nfp + pr.w) * E + pr.z];
     } else {
-        ghost_state<D>(ph, bc, qL, qR);
+        ghost_state<D, T, typename FrBase<T>::type>(ph, bc, qL, qR);
     }
 #pragma unroll
     for (int v = 0; v < S::nv; ++v) {
@@ -255,14 +260,16 @@ __global__ void __launch_bounds__(128) k_pair_common(const int4 *__restrict__ pa
 // stage 3a: corrected gradient at solution points
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(128) k_grad_sp(const T *__restrict__ q, const T *__restrict__ dq,
-                                                 const T *__restrict__ G, T *__restrict__ Q, int E) {
+                                                 const typename FrBase<T>::type *__restrict__ G, T *__restrict__ Q,
+                                                 int E) {
     using S = Sh<D, P>;
     constexpr int N = S::n;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     int v = blockIdx.y / S::np, i = blockIdx.y - v * S::np;
     int ii[3] = {i % N, (i / N) % N, D == 3 ? i / (N * N) : 0};
-    const FrTab<T> &tb = frtab<T>(P);
+    typedef typename FrBase<T>::type B;
+    const FrTab<B> &tb = frtab<B>(P);
     T gr[3];
 #pragma unroll
     for (int dd = 0; dd < D; ++dd) {
@@ -290,8 +297,9 @@ __global__ void __launch_bounds__(128) k_grad_sp(const T *__restrict__ q, const 
 // stage 3b: face gradient traces (uncorrected) with the BR2 lifting of the face's own jump
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(128) k_grad_fp(const T *__restrict__ q, const T *__restrict__ qf,
-                                                 const T *__restrict__ dq, const T *__restrict__ Gf,
-                                                 T *__restrict__ Qf, int E, T etagL, T etagR) {
+                                                 const T *__restrict__ dq, const typename FrBase<T>::type *__restrict__ Gf,
+                                                 T *__restrict__ Qf, int E, typename FrBase<T>::type etagL,
+                                                 typename FrBase<T>::type etagR) {
     using S = Sh<D, P>;
     constexpr int N = S::n;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -299,7 +307,8 @@ __global__ void __launch_bounds__(128) k_grad_fp(const T *__restrict__ q, const 
     int v = blockIdx.y / S::nfp, k = blockIdx.y - v * S::nfp;
     int df, s, a, b;
     fp_decode<D, N>(k, df, s, a, b);
-    const FrTab<T> &tb = frtab<T>(P);
+    typedef typename FrBase<T>::type B;
+    const FrTab<B> &tb = frtab<B>(P);
     T gf[3];
     {
         T t = T(0);
@@ -343,18 +352,20 @@ __global__ void __launch_bounds__(128) k_grad_fp(const T *__restrict__ q, const 
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(128) k_pair_flux(const int4 *__restrict__ pairs, const int *__restrict__ bcs,
                                                    int npairs, const T *__restrict__ qf, const T *__restrict__ Qf,
-                                                   const T *__restrict__ Sf, T *__restrict__ fn, int E, FrPhys<T> ph) {
+                                                   const typename FrBase<T>::type *__restrict__ Sf, T *__restrict__ fn,
+                                                   int E, FrPhys<typename FrBase<T>::type> ph) {
     using S = Sh<D, P>;
+    typedef typename FrBase<T>::type B;
     constexpr int nv = S::nv;
     int P_ = blockIdx.x * blockDim.x + threadIdx.x;
     if (P_ >= npairs) return;
     int4 pr = pairs[P_];
     int bc = bcs[P_];
     int f = pr.y / S::nf1, df = f >> 1, side = f & 1;
-    T nrm[3];
+    B nrm[3];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-        T sv = Sf[(size_t)((df * D + c) * S::nfp + pr.y) * E + pr.x];
+        B sv = Sf[(size_t)((df * D + c) * S::nfp + pr.y) * E + pr.x];
         nrm[c] = side ? sv : -sv;
     }
     T qL[5], qR[5], qs[5], QL[3][5], Qs[3][5];
@@ -373,7 +384,7 @@ __global__ void __launch_bounds__(128) k_pair_flux(const int4 *__restrict__ pair
                 Qs[c][v] = T(0.5) * (QL[c][v] + Qf[(size_t)((c * nv + v) * S::nfp + pr.w) * E + pr.z]);
         }
     } else {
-        ghost_state<D>(ph, bc, qL, qR);
+        ghost_state<D, T, B>(ph, bc, qL, qR);
 #pragma unroll
         for (int v = 0; v < nv; ++v)
 #pragma unroll
@@ -382,8 +393,8 @@ __global__ void __launch_bounds__(128) k_pair_flux(const int4 *__restrict__ pair
 #pragma unroll
     for (int v = 0; v < nv; ++v) qs[v] = T(0.5) * (qL[v] + qR[v]);
     T Fr[5], fv[3][5];
-    rusanov<D>(ph, qL, qR, nrm, Fr);
-    flux_viscous<D>(ph, qs, Qs, bc == 2, fv);
+    rusanov<D, T, B>(ph, qL, qR, nrm, Fr);
+    flux_viscous<D, T, B>(ph, qs, Qs, bc == 2, fv);
 #pragma unroll
     for (int v = 0; v < nv; ++v) {
         T Fv = T(0);
@@ -398,8 +409,10 @@ __global__ void __launch_bounds__(128) k_pair_flux(const int4 *__restrict__ pair
 // stage 5a: transformed volume flux Ft[dd][v][i][e] = sum_c S[dd][c] (f_inv - f_visc)_c
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(128) k_vflux(const T *__restrict__ q, const T *__restrict__ Q,
-                                               const T *__restrict__ Sm, T *__restrict__ Ft, int E, FrPhys<T> ph) {
+                                               const typename FrBase<T>::type *__restrict__ Sm, T *__restrict__ Ft, int E,
+                                               FrPhys<typename FrBase<T>::type> ph) {
     using S = Sh<D, P>;
+    typedef typename FrBase<T>::type B;
     constexpr int nv = S::nv;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
@@ -411,11 +424,11 @@ __global__ void __launch_bounds__(128) k_vflux(const T *__restrict__ q, const T 
 #pragma unroll
         for (int c = 0; c < D; ++c) Qi[c][v] = Q[(size_t)((c * nv + v) * S::np + i) * E + e];
     }
-    flux_inviscid<D>(ph, qi, fi);
-    flux_viscous<D>(ph, qi, Qi, false, fvi);
+    flux_inviscid<D, T, B>(ph, qi, fi);
+    flux_viscous<D, T, B>(ph, qi, Qi, false, fvi);
 #pragma unroll
     for (int dd = 0; dd < D; ++dd) {
-        T sm[3];
+        B sm[3];
 #pragma unroll
         for (int c = 0; c < D; ++c) sm[c] = Sm[(size_t)((dd * D + c) * S::np + i) * E + e];
 #pragma unroll
@@ -438,7 +451,8 @@ __global__ void __launch_bounds__(128) k_face_ft(const T *__restrict__ Ft, T *__
     int v = blockIdx.y / S::nfp, k = blockIdx.y - v * S::nfp;
     int df, s, a, b;
     fp_decode<D, N>(k, df, s, a, b);
-    const FrTab<T> &tb = frtab<T>(P);
+    typedef typename FrBase<T>::type B;
+    const FrTab<B> &tb = frtab<B>(P);
     T acc = T(0);
 #pragma unroll
     for (int m = 0; m < N; ++m) {
@@ -451,7 +465,7 @@ __global__ void __launch_bounds__(128) k_face_ft(const T *__restrict__ Ft, T *__
 // stage 5c: divergence with FR corrections, R = -(div * invJ)
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(128) k_div(const T *__restrict__ Ft, const T *__restrict__ Ftf,
-                                             const T *__restrict__ fn, const T *__restrict__ invJ,
+                                             const T *__restrict__ fn, const typename FrBase<T>::type *__restrict__ invJ,
                                              T *__restrict__ R, int E) {
     using S = Sh<D, P>;
     constexpr int N = S::n;
@@ -459,7 +473,8 @@ __global__ void __launch_bounds__(128) k_div(const T *__restrict__ Ft, const T *
     if (e >= E) return;
     int v = blockIdx.y / S::np, i = blockIdx.y - v * S::np;
     int ii[3] = {i % N, (i / N) % N, D == 3 ? i / (N * N) : 0};
-    const FrTab<T> &tb = frtab<T>(P);
+    typedef typename FrBase<T>::type B;
+    const FrTab<B> &tb = frtab<B>(P);
     T div = T(0);
 #pragma unroll
     for (int dd = 0; dd < D; ++dd) {

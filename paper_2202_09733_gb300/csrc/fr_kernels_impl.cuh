@@ -1,0 +1,410 @@
+// Kernels and launchers of the hot path, generic in the scalar type.  Included once per
+// precision by a translation unit that defines
+//   FRT            scalar type (double or float)
+//   FRK(name)      launcher prefix (frk64_name / frk32_name)
+//   FR_DOUBLE      1 for the FP64 unit (adds the Krylov/time-stepping vector kernels)
+// The FP64 unit is compiled with -fmad=false, so there the only fused multiply-adds are
+// the explicit fma() calls and every result follows the documented evaluation order.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include "fr_device.cuh"
+#include "fr_lib.h"
+
+static unsigned long long g_launches = 0;
+unsigned long long FRK(launch_count)() { return g_launches; }
+#define CNT() (++g_launches)
+
+__constant__ FrTab<FRT> c_tab[FR_MAXP + 1];
+__constant__ FRT c_gam[FR_MAXP + 1][FR_MAXP + 1][FR_MAXN][FR_MAXN];
+__constant__ FRT c_pi[FR_MAXP + 1][FR_MAXP + 1][FR_MAXN][FR_MAXN];
+
+template <>
+__device__ __forceinline__ const FrTab<FRT> &frtab<FRT>(int p) {
+    return c_tab[p];
+}
+
+int FRK(upload_tables)(const FrTabH *tabs, const double *gam, const double *pi) {
+    static FrTab<FRT> t[FR_MAXP + 1];
+    static FRT g[(FR_MAXP + 1) * (FR_MAXP + 1) * FR_MAXN * FR_MAXN], p[(FR_MAXP + 1) * (FR_MAXP + 1) * FR_MAXN * FR_MAXN];
+    for (int k = 0; k <= FR_MAXP; ++k)
+        for (int i = 0; i < FR_MAXN; ++i) {
+            for (int m = 0; m < FR_MAXN; ++m) t[k].D[i][m] = (FRT)tabs[k].D[i][m];
+            t[k].lm[i] = (FRT)tabs[k].lm[i]; t[k].lp[i] = (FRT)tabs[k].lp[i];
+            t[k].dlm[i] = (FRT)tabs[k].dlm[i]; t[k].dlp[i] = (FRT)tabs[k].dlp[i];
+            t[k].gLd[i] = (FRT)tabs[k].gLd[i]; t[k].gRd[i] = (FRT)tabs[k].gRd[i];
+        }
+    for (size_t i = 0; i < sizeof(g) / sizeof(g[0]); ++i) { g[i] = (FRT)gam[i]; p[i] = (FRT)pi[i]; }
+    if (cudaMemcpyToSymbol(c_tab, t, sizeof t) != cudaSuccess) return -1;
+    if (cudaMemcpyToSymbol(c_gam, g, sizeof g) != cudaSuccess) return -1;
+    if (cudaMemcpyToSymbol(c_pi, p, sizeof p) != cudaSuccess) return -1;
+    return 0;
+}
+
+static FrPhys<FRT> to_phys(const FrPhysH &h, const FrLevelT<FRT> &L) {
+    FrPhys<FRT> p;
+    p.gamma = (FRT)h.gamma; p.gm1 = (FRT)h.gm1; p.mu = (FRT)h.mu; p.kappa = (FRT)h.kappa; p.c23 = (FRT)h.c23;
+    for (int v = 0; v < 5; ++v) p.qinf[v] = (FRT)h.qinf[v];
+    p.etagL = (FRT)L.etagL; p.etagR = (FRT)L.etagR;
+    return p;
+}
+
+// ------------------------------------------------------------------------ residual
+template <int D, int P>
+static void residual_t(const FrLevelT<FRT> &L, const FrPhys<FRT> &ph, const FRT *q, FRT *R, cudaStream_t s) {
+    using S = Sh<D, P>;
+    const int E = L.E, gx = (E + 127) / 128, gp = (L.npairs + 127) / 128;
+    CNT(); k_interp<D, P, FRT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, E);
+    CNT(); k_pair_common<D, P, FRT><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.dq, E, ph);
+    CNT(); k_grad_sp<D, P, FRT><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(q, L.dq, L.G, L.Q, E);
+    CNT(); k_grad_fp<D, P, FRT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
+    CNT(); k_pair_flux<D, P, FRT><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.Qf, L.Sf, L.fn, E, ph);
+    CNT(); k_vflux<D, P, FRT><<<dim3(gx, S::np), 128, 0, s>>>(q, L.Q, L.S, L.Ft, E, ph);
+    CNT(); k_face_ft<D, P, FRT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(L.Ft, L.Ftf, E);
+    CNT(); k_div<D, P, FRT><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
+}
+
+int FRK(residual)(const FrLevelT<FRT> &L, const FrPhysH &h, const FRT *q, FRT *R, cudaStream_t s) {
+    FrPhys<FRT> ph = to_phys(h, L);
+    if (L.d == 2) {
+        switch (L.p) {
+            case 1: residual_t<2, 1>(L, ph, q, R, s); return 0;
+            case 2: residual_t<2, 2>(L, ph, q, R, s); return 0;
+            case 3: residual_t<2, 3>(L, ph, q, R, s); return 0;
+            case 4: residual_t<2, 4>(L, ph, q, R, s); return 0;
+        }
+    } else if (L.d == 3) {
+        switch (L.p) {
+            case 1: residual_t<3, 1>(L, ph, q, R, s); return 0;
+            case 2: residual_t<3, 2>(L, ph, q, R, s); return 0;
+            case 3: residual_t<3, 3>(L, ph, q, R, s); return 0;
+        }
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------------- elementwise
+static inline int nblk(long long n, int b = 256) {
+    long long g = (n + b - 1) / b;
+    return (int)std::min<long long>(g, 152LL * 32);
+}
+#define GRID_STRIDE(i, n) \
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+
+__global__ void k_copy(long long n, const FRT *x, FRT *y) { GRID_STRIDE(i, n) y[i] = x[i]; }
+__global__ void k_add(long long n, const FRT *a, const FRT *b, FRT *y) { GRID_STRIDE(i, n) y[i] = a[i] + b[i]; }
+__global__ void k_sub(long long n, const FRT *a, const FRT *b, FRT *y) { GRID_STRIDE(i, n) y[i] = a[i] - b[i]; }
+__global__ void k_pmg_rhs(long long n, FRT c, const FRT *d, const FRT *qh, const FRT *b, const FRT *Rqh, const FRT *Rb,
+                          FRT *rhs) {
+    GRID_STRIDE(i, n) {
+        FRT t1 = qh[i] - b[i], t2 = Rqh[i] - Rb[i];
+        rhs[i] = d[i] - (c * t1 - t2);
+    }
+}
+void FRK(copy)(long long n, const FRT *x, FRT *y, cudaStream_t s) { CNT(); k_copy<<<nblk(n), 256, 0, s>>>(n, x, y); }
+void FRK(add)(long long n, const FRT *a, const FRT *b, FRT *y, cudaStream_t s) { CNT(); k_add<<<nblk(n), 256, 0, s>>>(n, a, b, y); }
+void FRK(sub)(long long n, const FRT *a, const FRT *b, FRT *y, cudaStream_t s) { CNT(); k_sub<<<nblk(n), 256, 0, s>>>(n, a, b, y); }
+void FRK(pmg_rhs)(long long n, double c, const FRT *d, const FRT *qh, const FRT *b, const FRT *Rqh, const FRT *Rb,
+                  FRT *rhs, cudaStream_t s) {
+    CNT(); k_pmg_rhs<<<nblk(n), 256, 0, s>>>(n, (FRT)c, d, qh, b, Rqh, Rb, rhs);
+}
+
+// ------------------------------------------------------------------ element blocks
+// Column j of the blocks of every element of colour `col`: forward difference with the
+// step epsrel * max(1, |q_j|) on that element alone (elements of one colour share no
+// face, so their perturbations do not interact in R restricted to each of them).
+__global__ void k_perturb_color(int E, const int *color, int col, int j, const FRT *q, FRT *qp, FRT epsrel) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E || color[e] != col) return;
+    FRT x = q[(size_t)j * E + e];
+    FRT eps = epsrel * fmax((FRT)1, fabs(x));
+    qp[(size_t)j * E + e] = x + eps;
+}
+__global__ void k_restore_color(int E, const int *color, int col, int j, const FRT *q, FRT *qp) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E || color[e] != col) return;
+    qp[(size_t)j * E + e] = q[(size_t)j * E + e];
+}
+// tile: 32 elements x 32 rows through shared memory (coalesced on both sides)
+__global__ void __launch_bounds__(256) k_block_column(int E, int nd, const int *color, int col, int j, const FRT *q,
+                                                      const FRT *R0, const FRT *Rp, FRT shift, FRT epsrel, FRT *M) {
+    __shared__ FRT tile[32][33];
+    __shared__ int s_col[32];
+    __shared__ FRT s_eps[32];
+    int e0 = blockIdx.x * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (threadIdx.x < 32) {
+        int e = e0 + tx;
+        int ok = e < E && color[e] == col;
+        s_col[tx] = ok;
+        FRT x = ok ? q[(size_t)j * E + e] : (FRT)0;
+        s_eps[tx] = epsrel * fmax((FRT)1, fabs(x));
+    }
+    __syncthreads();
+    for (int r0 = 0; r0 < nd; r0 += 32) {
+        for (int rr = ty; rr < 32; rr += 8) {
+            int r = r0 + rr, e = e0 + tx;
+            FRT val = 0;
+            if (r < nd && e < E && s_col[tx]) {
+                FRT m = (Rp[(size_t)r * E + e] - R0[(size_t)r * E + e]) / s_eps[tx];
+                val = (r == j) ? shift - m : -m;
+            }
+            tile[rr][tx] = val;
+        }
+        __syncthreads();
+        for (int ee = ty; ee < 32; ee += 8) {
+            int e = e0 + ee, r = r0 + tx;
+            if (e < E && s_col[ee] && r < nd) M[((size_t)e * nd + j) * nd + r] = tile[tx][ee];
+        }
+        __syncthreads();
+    }
+}
+void FRK(perturb_color)(const FrLevelT<FRT> &L, const int *color, int col, int j, const FRT *q, FRT *qp, double epsrel,
+                        cudaStream_t s) {
+    CNT(); k_perturb_color<<<(L.E + 255) / 256, 256, 0, s>>>(L.E, color, col, j, q, qp, (FRT)epsrel);
+}
+void FRK(restore_color)(const FrLevelT<FRT> &L, const int *color, int col, int j, const FRT *q, FRT *qp, cudaStream_t s) {
+    CNT(); k_restore_color<<<(L.E + 255) / 256, 256, 0, s>>>(L.E, color, col, j, q, qp);
+}
+void FRK(block_column)(const FrLevelT<FRT> &L, const int *color, int col, int j, const FRT *q, const FRT *R0,
+                       const FRT *Rp, double shift, double epsrel, FRT *M, cudaStream_t s) {
+    CNT(); k_block_column<<<(L.E + 31) / 32, 256, 0, s>>>(L.E, L.nd, color, col, j, q, R0, Rp, (FRT)shift, (FRT)epsrel, M);
+}
+
+// ------------------------------------------------------------------------ block LU
+// One CTA per element block, column-major A(r, c) = A[c * nd + r]; right-looking
+// elimination with partial pivoting (first maximal |a|, whole rows swapped),
+// multipliers l = a / pivot, trailing updates a = fma(-l, u, a) in elimination order.
+template <bool SMEM>
+__global__ void __launch_bounds__(256) k_lu_factor(FRT *M, int *perm, int nd, int *info) {
+    extern __shared__ __align__(16) unsigned char dsm_raw[];
+    FRT *dsm = reinterpret_cast<FRT *>(dsm_raw);
+    __shared__ FRT s_best[8];
+    __shared__ int s_idx[8];
+    __shared__ int s_p;
+    int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    FRT *Ag = M + (size_t)e * nd * nd;
+    FRT *A = SMEM ? dsm : Ag;
+    int *pv = perm + (size_t)e * nd;
+    if (SMEM)
+        for (int t = tid; t < nd * nd; t += nt) A[t] = Ag[t];
+    for (int t = tid; t < nd; t += nt) pv[t] = t;
+    __syncthreads();
+    int lane = tid & 31, wid = tid >> 5;
+    for (int k = 0; k < nd; ++k) {
+        FRT best = -1;
+        int bi = nd;
+        for (int i = k + tid; i < nd; i += nt) {
+            FRT a = fabs(A[(size_t)k * nd + i]);
+            if (a > best) { best = a; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            FRT ob = __shfl_down_sync(0xffffffffu, best, o);
+            int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { s_best[wid] = best; s_idx[wid] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            FRT b = s_best[0];
+            int ix = s_idx[0];
+            for (int w = 1; w < nt / 32; ++w)
+                if (s_best[w] > b || (s_best[w] == b && s_idx[w] < ix)) { b = s_best[w]; ix = s_idx[w]; }
+            if (ix >= nd) ix = k;
+            s_p = ix;
+            if (b == (FRT)0) atomicExch(info, 1);
+            if (ix != k) { int t = pv[k]; pv[k] = pv[ix]; pv[ix] = t; }
+        }
+        __syncthreads();
+        int p = s_p;
+        if (p != k)
+            for (int c = tid; c < nd; c += nt) {
+                FRT t = A[(size_t)c * nd + k];
+                A[(size_t)c * nd + k] = A[(size_t)c * nd + p];
+                A[(size_t)c * nd + p] = t;
+            }
+        __syncthreads();
+        FRT piv = A[(size_t)k * nd + k];
+        for (int i = k + 1 + tid; i < nd; i += nt) A[(size_t)k * nd + i] = A[(size_t)k * nd + i] / piv;
+        __syncthreads();
+        int m = nd - k - 1;
+        for (int t = tid; t < m * m; t += nt) {
+            int c = k + 1 + t / m, i = k + 1 + t % m;
+            A[(size_t)c * nd + i] = fma(-A[(size_t)k * nd + i], A[(size_t)c * nd + k], A[(size_t)c * nd + i]);
+        }
+        __syncthreads();
+    }
+    if (SMEM)
+        for (int t = tid; t < nd * nd; t += nt) Ag[t] = A[t];
+}
+
+int FRK(lu_factor)(const FrLevelT<FRT> &L, FRT *M, int *perm, int *info, cudaStream_t s) {
+    size_t sm = sizeof(FRT) * (size_t)L.nd * L.nd;
+    if (sm <= 200 * 1024) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_lu_factor<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        CNT(); k_lu_factor<true><<<L.E, 256, sm, s>>>(M, perm, L.nd, info);
+    } else {
+        CNT(); k_lu_factor<false><<<L.E, 256, 0, s>>>(M, perm, L.nd, info);
+    }
+    return 0;
+}
+
+// One warp per element: rows i = lane + 32 s held in registers.  Forward substitution
+// with the unit lower factor applies y_k to every later row in ascending k; backward
+// substitution applies x_k to every earlier row in descending k (the order the unknowns
+// become known), x_k = b_k / u_kk.  Columns are fetched G at a time ahead of the
+// dependent fma chain so that G column loads are in flight per step.
+template <int NR>
+__device__ __forceinline__ FRT pick(const FRT (&b)[NR], int slot) {
+    FRT v = b[0];
+#pragma unroll
+    for (int s = 1; s < NR; ++s)
+        if (s == slot) v = b[s];
+    return v;
+}
+
+template <int NR, int G>
+__global__ void __launch_bounds__(128) k_lu_solve(const FRT *__restrict__ M, const int *__restrict__ perm,
+                                                  FRT *__restrict__ x, int nd, int E) {
+    int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (e >= E) return;
+    const FRT *A = M + (size_t)e * nd * nd;
+    const int *pv = perm + (size_t)e * nd;
+    FRT b[NR];
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+        int i = lane + 32 * s;
+        b[s] = i < nd ? x[(size_t)pv[i] * E + e] : (FRT)0;
+    }
+    for (int k0 = 0; k0 < nd; k0 += G) {
+        FRT cv[G][NR];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            int k = k0 + g;
+            const FRT *col = A + (size_t)(k < nd ? k : nd - 1) * nd;
+#pragma unroll
+            for (int s = 0; s < NR; ++s) {
+                int i = lane + 32 * s;
+                cv[g][s] = (k < nd && i > k && i < nd) ? col[i] : (FRT)0;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            int k = k0 + g;
+            if (k >= nd) break;
+            FRT yk = __shfl_sync(0xffffffffu, pick<NR>(b, k >> 5), k & 31);
+#pragma unroll
+            for (int s = 0; s < NR; ++s) {
+                int i = lane + 32 * s;
+                if (i > k && i < nd) b[s] = fma(-cv[g][s], yk, b[s]);
+            }
+        }
+    }
+    for (int kt = nd - 1; kt >= 0; kt -= G) {
+        FRT cv[G][NR];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            int k = kt - g;
+            const FRT *col = A + (size_t)(k >= 0 ? k : 0) * nd;
+#pragma unroll
+            for (int s = 0; s < NR; ++s) {
+                int i = lane + 32 * s;
+                cv[g][s] = (k >= 0 && i <= k) ? col[i] : (FRT)0;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            int k = kt - g;
+            if (k < 0) break;
+            int owner = k & 31, slot = k >> 5;
+            FRT xk = (FRT)0;
+            if (lane == owner) xk = pick<NR>(b, slot) / pick<NR>(cv[g], slot);
+            xk = __shfl_sync(0xffffffffu, xk, owner);
+#pragma unroll
+            for (int s = 0; s < NR; ++s) {
+                int i = lane + 32 * s;
+                if (i == k) b[s] = xk;
+                else if (i < k) b[s] = fma(-cv[g][s], xk, b[s]);
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+        int i = lane + 32 * s;
+        if (i < nd) x[(size_t)i * E + e] = b[s];
+    }
+}
+
+int FRK(lu_solve)(const FrLevelT<FRT> &L, const FRT *M, const int *perm, FRT *x, cudaStream_t s) {
+    int nr = (L.nd + 31) / 32;
+    int grid = (L.E * 32 + 127) / 128;
+    switch (nr) {
+        case 1: { CNT(); k_lu_solve<1, 8><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 2: { CNT(); k_lu_solve<2, 8><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 3: { CNT(); k_lu_solve<3, 4><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 4: { CNT(); k_lu_solve<4, 4><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 5: { CNT(); k_lu_solve<5, 4><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 6: { CNT(); k_lu_solve<6, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 7: { CNT(); k_lu_solve<7, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 8: { CNT(); k_lu_solve<8, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 10: { CNT(); k_lu_solve<10, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        default: return -1;
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------------ transfers
+// thread per (e, v); 1-D operator along direction 0, then 1, then 2 (fma chains over the
+// source index); sizes at run time (ni -> no points per direction), NM = max points.
+template <int D, int NM>
+__global__ void __launch_bounds__(128) k_tensor(const FRT *__restrict__ x, FRT *__restrict__ y, int E, int ni, int no,
+                                                int p0, int p1, int restrict_) {
+    constexpr int BUF = D == 2 ? NM * NM : NM * NM * NM;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    int v = blockIdx.y;
+    int npi = D == 2 ? ni * ni : ni * ni * ni, npo = D == 2 ? no * no : no * no * no;
+    FRT a[BUF], b[BUF];
+#pragma unroll 1
+    for (int i = 0; i < npi; ++i) a[i] = x[(size_t)(v * npi + i) * E + e];
+    int dims[3] = {ni, ni, D == 3 ? ni : 1};
+#pragma unroll 1
+    for (int dir = 0; dir < D; ++dir) {
+        int nd0 = dir == 0 ? no : dims[0], nd1 = dir == 1 ? no : dims[1], nd2 = dir == 2 ? no : dims[2];
+#pragma unroll 1
+        for (int i2 = 0; i2 < nd2; ++i2)
+#pragma unroll 1
+            for (int i1 = 0; i1 < nd1; ++i1)
+#pragma unroll 1
+                for (int i0 = 0; i0 < nd0; ++i0) {
+                    int o = dir == 0 ? i0 : (dir == 1 ? i1 : i2);
+                    FRT acc = 0;
+#pragma unroll 1
+                    for (int m = 0; m < ni; ++m) {
+                        int s0 = dir == 0 ? m : i0, s1 = dir == 1 ? m : i1, s2 = dir == 2 ? m : i2;
+                        FRT op = restrict_ ? c_gam[p0][p1][o][m] : c_pi[p0][p1][o][m];
+                        acc = fma(op, a[s0 + dims[0] * (s1 + dims[1] * s2)], acc);
+                    }
+                    b[i0 + nd0 * (i1 + nd1 * i2)] = acc;
+                }
+        dims[0] = nd0; dims[1] = nd1; dims[2] = nd2;
+        int cnt = dims[0] * dims[1] * dims[2];
+#pragma unroll 1
+        for (int i = 0; i < cnt; ++i) a[i] = b[i];
+    }
+#pragma unroll 1
+    for (int i = 0; i < npo; ++i) y[(size_t)(v * npo + i) * E + e] = a[i];
+}
+
+int FRK(transfer)(const FrLevelT<FRT> &Lf, const FrLevelT<FRT> &Lc, bool r, const FRT *x, FRT *y, cudaStream_t s) {
+    int p0 = Lf.p, p1 = Lc.p, E = Lf.E, nv = Lf.nv;
+    int ni = r ? p0 + 1 : p1 + 1, no = r ? p1 + 1 : p0 + 1;
+    dim3 grid((E + 127) / 128, nv);
+    if (Lf.d == 2 && p0 <= 5) { CNT(); k_tensor<2, 6><<<grid, 128, 0, s>>>(x, y, E, ni, no, p0, p1, r); }
+    else if (Lf.d == 3 && p0 <= 3) { CNT(); k_tensor<3, 4><<<grid, 128, 0, s>>>(x, y, E, ni, no, p0, p1, r); }
+    else return -1;
+    return 0;
+}

@@ -1,0 +1,47 @@
+// FP32 kernels of the mixed-precision preconditioner (residuals on every p-level,
+// element blocks, block LU and solves, transfers), plus the FP64 <-> FP32 conversions at
+// the preconditioner's boundary.  Contraction is allowed in this unit.
+#define FRT float
+#define FRK(name) frk32_##name
+#define FR_DOUBLE 0
+#include "fr_kernels_impl.cuh"
+
+// --------------------------------------------------------- precision boundary
+__global__ void k_d2f(long long n, const double *x, float *y) { GRID_STRIDE(i, n) y[i] = (float)x[i]; }
+__global__ void k_f2d_scaled(long long n, const float *x, double inv_s, double *y) {
+    GRID_STRIDE(i, n) y[i] = (double)x[i] * inv_s;
+}
+// y = float(x * s), s = target / max|x| read from the device (no host round trip)
+__global__ void k_d2f_scaled(long long n, const double *x, const double *xmax, double target, float *y) {
+    double m = *xmax;
+    double s = m > 0.0 ? target / m : 1.0;
+    GRID_STRIDE(i, n) y[i] = (float)(x[i] * s);
+}
+__global__ void k_absmax(long long n, const double *x, unsigned long long *out) {
+    double m = 0.0;
+    GRID_STRIDE(i, n) m = fmax(m, fabs(x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+void frk32_d2f(long long n, const double *x, float *y, cudaStream_t s) { CNT(); k_d2f<<<nblk(n), 256, 0, s>>>(n, x, y); }
+void frk32_f2d_scaled(long long n, const float *x, double inv_s, double *y, cudaStream_t s) {
+    CNT(); k_f2d_scaled<<<nblk(n), 256, 0, s>>>(n, x, inv_s, y);
+}
+void frk32_d2f_scaled(long long n, const double *x, const double *xmax_dev, double target, float *y, cudaStream_t s) {
+    CNT(); k_d2f_scaled<<<nblk(n), 256, 0, s>>>(n, x, xmax_dev, target, y);
+}
+int frk32_absmax(long long n, const double *x, double *out_dev, cudaStream_t s) {
+    if (cudaMemsetAsync(out_dev, 0, sizeof(double), s) != cudaSuccess) return -1;
+    CNT(); k_absmax<<<nblk(n), 256, 0, s>>>(n, x, (unsigned long long *)out_dev);
+    return 0;
+}
+// y = double(x) * (max / target): undoes the input scaling of the FP32 cycle
+__global__ void k_f2d_unscale(long long n, const float *x, const double *xmax, double target, double *y) {
+    double m = *xmax;
+    double inv_s = m > 0.0 ? m / target : 1.0;
+    GRID_STRIDE(i, n) y[i] = (double)x[i] * inv_s;
+}
+void frk32_f2d_unscale(long long n, const float *x, const double *xmax_dev, double target, double *y, cudaStream_t s) {
+    CNT(); k_f2d_unscale<<<nblk(n), 256, 0, s>>>(n, x, xmax_dev, target, y);
+}

@@ -1,0 +1,116 @@
+// FP32 element-diagonal Jacobian blocks by forward-mode differentiation: the residual
+// kernels run on DualF with derivative seed 1 in degree of freedom j of every element of
+// one colour (elements of a colour share no face), so R.d restricted to each of those
+// elements is column j of its block dR_e/dq_e, exact up to FP32 rounding of each term.
+#include <algorithm>
+#include "fr_device.cuh"
+#include "fr_lib.h"
+
+static unsigned long long g_launches = 0;
+unsigned long long frkad_launch_count() { return g_launches; }
+#define CNT() (++g_launches)
+
+__constant__ FrTab<float> c_tab_ad[FR_MAXP + 1];
+template <>
+__device__ __forceinline__ const FrTab<float> &frtab<float>(int p) {
+    return c_tab_ad[p];
+}
+
+int frkad_upload_tables(const FrTabH *tabs) {
+    static FrTab<float> t[FR_MAXP + 1];
+    for (int k = 0; k <= FR_MAXP; ++k)
+        for (int i = 0; i < FR_MAXN; ++i) {
+            for (int m = 0; m < FR_MAXN; ++m) t[k].D[i][m] = (float)tabs[k].D[i][m];
+            t[k].lm[i] = (float)tabs[k].lm[i]; t[k].lp[i] = (float)tabs[k].lp[i];
+            t[k].dlm[i] = (float)tabs[k].dlm[i]; t[k].dlp[i] = (float)tabs[k].dlp[i];
+            t[k].gLd[i] = (float)tabs[k].gLd[i]; t[k].gRd[i] = (float)tabs[k].gRd[i];
+        }
+    return cudaMemcpyToSymbol(c_tab_ad, t, sizeof t) == cudaSuccess ? 0 : -1;
+}
+
+template <int D, int P>
+static void residual_ad(const FrLevelAD &L, const FrPhys<float> &ph, const DualF *q, DualF *R, cudaStream_t s) {
+    using S = Sh<D, P>;
+    const int E = L.E, gx = (E + 127) / 128, gp = (L.npairs + 127) / 128;
+    CNT(); k_interp<D, P, DualF><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, E);
+    CNT(); k_pair_common<D, P, DualF><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.dq, E, ph);
+    CNT(); k_grad_sp<D, P, DualF><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(q, L.dq, L.G, L.Q, E);
+    CNT(); k_grad_fp<D, P, DualF><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
+    CNT(); k_pair_flux<D, P, DualF><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.Qf, L.Sf, L.fn, E, ph);
+    CNT(); k_vflux<D, P, DualF><<<dim3(gx, S::np), 128, 0, s>>>(q, L.Q, L.S, L.Ft, E, ph);
+    CNT(); k_face_ft<D, P, DualF><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(L.Ft, L.Ftf, E);
+    CNT(); k_div<D, P, DualF><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
+}
+
+int frkad_residual(const FrLevelAD &L, const FrPhysH &h, const DualF *q, DualF *R, cudaStream_t s) {
+    FrPhys<float> ph;
+    ph.gamma = (float)h.gamma; ph.gm1 = (float)h.gm1; ph.mu = (float)h.mu; ph.kappa = (float)h.kappa;
+    ph.c23 = (float)h.c23;
+    for (int v = 0; v < 5; ++v) ph.qinf[v] = (float)h.qinf[v];
+    ph.etagL = (float)L.etagL; ph.etagR = (float)L.etagR;
+    if (L.d == 2) {
+        switch (L.p) {
+            case 1: residual_ad<2, 1>(L, ph, q, R, s); return 0;
+            case 2: residual_ad<2, 2>(L, ph, q, R, s); return 0;
+            case 3: residual_ad<2, 3>(L, ph, q, R, s); return 0;
+            case 4: residual_ad<2, 4>(L, ph, q, R, s); return 0;
+        }
+    } else if (L.d == 3) {
+        switch (L.p) {
+            case 1: residual_ad<3, 1>(L, ph, q, R, s); return 0;
+            case 2: residual_ad<3, 2>(L, ph, q, R, s); return 0;
+            case 3: residual_ad<3, 3>(L, ph, q, R, s); return 0;
+        }
+    }
+    return -1;
+}
+
+__global__ void k_ad_init(long long n, const float *q, DualF *qd) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        qd[i] = DualF(q[i], 0.f);
+}
+void frkad_init(long long n, const float *q, DualF *qd, cudaStream_t s) {
+    int g = (int)std::min<long long>((n + 255) / 256, 152LL * 32);
+    CNT(); k_ad_init<<<g, 256, 0, s>>>(n, q, qd);
+}
+__global__ void k_ad_seed(int E, const int *color, int col, int j, DualF *qd, float seed) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E || color[e] != col) return;
+    qd[(size_t)j * E + e].d = seed;
+}
+void frkad_seed(const FrLevelAD &L, const int *color, int col, int j, DualF *qd, float seed, cudaStream_t s) {
+    CNT(); k_ad_seed<<<(L.E + 255) / 256, 256, 0, s>>>(L.E, color, col, j, qd, seed);
+}
+// M[e][j][r] = (r == j ? shift : 0) - dR_r/dq_j for the elements of the colour (tiled)
+__global__ void __launch_bounds__(256) k_ad_column(int E, int nd, const int *color, int col, int j, const DualF *Rd,
+                                                   float shift, float *M) {
+    __shared__ float tile[32][33];
+    __shared__ int s_col[32];
+    int e0 = blockIdx.x * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (threadIdx.x < 32) {
+        int e = e0 + tx;
+        s_col[tx] = e < E && color[e] == col;
+    }
+    __syncthreads();
+    for (int r0 = 0; r0 < nd; r0 += 32) {
+        for (int rr = ty; rr < 32; rr += 8) {
+            int r = r0 + rr, e = e0 + tx;
+            float val = 0.f;
+            if (r < nd && e < E && s_col[tx]) {
+                float dr = Rd[(size_t)r * E + e].d;
+                val = (r == j) ? shift - dr : -dr;
+            }
+            tile[rr][tx] = val;
+        }
+        __syncthreads();
+        for (int ee = ty; ee < 32; ee += 8) {
+            int e = e0 + ee, r = r0 + tx;
+            if (e < E && s_col[ee] && r < nd) M[((size_t)e * nd + j) * nd + r] = tile[tx][ee];
+        }
+        __syncthreads();
+    }
+}
+void frkad_block_column(const FrLevelAD &L, const int *color, int col, int j, const DualF *Rd, double shift, float *M,
+                        cudaStream_t s) {
+    CNT(); k_ad_column<<<(L.E + 31) / 32, 256, 0, s>>>(L.E, L.nd, color, col, j, Rd, (float)shift, M);
+}

@@ -1,7 +1,8 @@
 // frpmg C ABI: context set-up and the host-side orchestration of the JFNK-pMG hot path
-// (pMG V-cycle, FGMRES with CGS2, ESDIRK/PTC, ROW, steady PTC/SER).  Every arithmetic
-// step on solution vectors runs in the kernels of kernels64.cu; the host only keeps the
-// Krylov scalars (Hessenberg matrix, Givens rotations) and the iteration logic.
+// (pMG V-cycle in FP64 or FP32, FGMRES with CGS2, ESDIRK/PTC, ROW, steady PTC/SER).
+// Every arithmetic step on solution vectors runs in the kernels of kernels64.cu and
+// kernels32.cu; the host only keeps the Krylov scalars (Hessenberg matrix, Givens
+// rotations) and the iteration logic.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -43,32 +44,42 @@ static int fail(int code, const char *fmt, ...) {
         if (_r != FR_OK) return _r;  \
     } while (0)
 
+template <typename T>
+struct PmgBuf {
+    T *M[FRL_MAXLEV];
+    int *perm[FRL_MAXLEV];
+    size_t M_cap[FRL_MAXLEV];
+    T *b[FRL_MAXLEV], *Rb[FRL_MAXLEV], *d[FRL_MAXLEV], *qh[FRL_MAXLEV], *Rqh[FRL_MAXLEV], *rhs[FRL_MAXLEV],
+        *C[FRL_MAXLEV];
+    T *blk_R0, *blk_Rp, *blk_qp;  // element-block assembly temporaries (finest-level size)
+};
+
 struct fr_ctx {
     int d, nv, E, qg, nlev;
     FrPhysH ph;
     double eta;
     FrLevel L[FRL_MAXLEV];
+    FrLevel32 L32[FRL_MAXLEV];    // FP32 copies of the levels (mixed preconditioner)
+    FrLevelAD LA[FRL_MAXLEV];     // forward-mode (FP32 dual) residual workspace for the FP32 blocks
+    int have32, haveAD;
+    DualF *qd, *Rd;
     int ncolor;
     int *color;
     int *info;
     std::vector<void *> allocs;
-    // residual-derived temporaries
-    double *jv_qp, *jv_Rp, *blk_R0, *blk_Rp, *blk_qp;
+    double *jv_qp, *jv_Rp;
     double *dots;                 // device scratch for inner products (64)
     // pMG
-    int pmg_ready, pmg_nlev, nsmooth[FRL_MAXLEV];
-    double pmg_c, pmg_ids;
-    double *M[FRL_MAXLEV];
-    int *perm[FRL_MAXLEV];
-    size_t M_cap[FRL_MAXLEV];
-    double *pb[FRL_MAXLEV], *pRb[FRL_MAXLEV], *pd[FRL_MAXLEV], *pqh[FRL_MAXLEV], *pRqh[FRL_MAXLEV],
-        *prhs[FRL_MAXLEV], *pC[FRL_MAXLEV];
+    int pmg_ready, pmg_nlev, pmg_prec, nsmooth[FRL_MAXLEV];
+    double pmg_c, pmg_ids, pmg_qmax;
+    PmgBuf<double> p64;
+    PmgBuf<float> p32;
+    float *x32, *q32, *Rq32, *y32;
+    double *xmax;
     // GMRES
-    int gm_kdim;
     std::vector<double *> V, Z;
     double *gw, *gr, *gtmp;
     // steppers
-    int st_cap;
     std::vector<double *> stv;
 };
 
@@ -98,7 +109,9 @@ static cudaStream_t S_(void *s) { return (cudaStream_t)s; }
 
 extern "C" const char *fr_last_error(void) { return g_err; }
 
-extern "C" unsigned long long fr_kernel_launches(void) { return frk64_launch_count(); }
+extern "C" unsigned long long fr_kernel_launches(void) {
+    return frk64_launch_count() + frk32_launch_count() + frkad_launch_count();
+}
 
 // ---------------------------------------------------------------- context set-up
 static int upload_tables() {
@@ -124,7 +137,8 @@ static int upload_tables() {
             memcpy(pi[p][p1], P, sizeof P);
         }
     }
-    if (frk64_upload_tables(tabs, &gam[0][0][0][0], &pi[0][0][0][0]) != 0)
+    if (frk64_upload_tables(tabs, &gam[0][0][0][0], &pi[0][0][0][0]) != 0 ||
+        frk32_upload_tables(tabs, &gam[0][0][0][0], &pi[0][0][0][0]) != 0 || frkad_upload_tables(tabs) != 0)
         return fail(FR_ERR_CUDA, "uploading operator tables: %s", cudaGetErrorString(cudaGetLastError()));
     return FR_OK;
 }
@@ -247,7 +261,8 @@ int fr_internal_fail(int code, const char *msg) { return fail(code, "%s", msg); 
 
 // ------------------------------------------------------------------ residual, Jv
 static int residual(fr_ctx *C, int l, const double *q, double *R, cudaStream_t s) {
-    if (frk64_residual(C->L[l], C->ph, q, R, s) != 0) return fail(FR_ERR_UNIMPLEMENTED, "no kernel for d=%d p=%d", C->d, C->L[l].p);
+    if (frk64_residual(C->L[l], C->ph, q, R, s) != 0)
+        return fail(FR_ERR_UNIMPLEMENTED, "no kernel for d=%d p=%d", C->d, C->L[l].p);
     CKLAUNCH();
     return FR_OK;
 }
@@ -276,27 +291,167 @@ extern "C" int fr_jvp(fr_ctx *C, const double *q, const double *Rq, const double
     return jvp(C, q, Rq, v, eps, shift, Av, S_(stream));
 }
 
-// ---------------------------------------------------------------- element blocks
-static int ensure_blk_tmp(fr_ctx *C) {
-    if (C->blk_R0) return FR_OK;
-    long long n0 = C->L[0].ndof;
-    TRY(dalloc_t(C, &C->blk_R0, n0));
-    TRY(dalloc_t(C, &C->blk_Rp, n0));
-    TRY(dalloc_t(C, &C->blk_qp, n0));
+// ------------------------------------------------- kernel dispatch per precision
+template <typename T>
+struct Kn;
+#define KN_BODY(P, T)                                                                                            \
+    static int residual(const FrLevelT<T> &L, const FrPhysH &ph, const T *q, T *R, cudaStream_t s) {             \
+        return P##_residual(L, ph, q, R, s);                                                                     \
+    }                                                                                                            \
+    static void copy(long long n, const T *x, T *y, cudaStream_t s) { P##_copy(n, x, y, s); }                  \
+    static void add(long long n, const T *a, const T *b, T *y, cudaStream_t s) { P##_add(n, a, b, y, s); }     \
+    static void sub(long long n, const T *a, const T *b, T *y, cudaStream_t s) { P##_sub(n, a, b, y, s); }     \
+    static void pmg_rhs(long long n, double c, const T *d, const T *qh, const T *b, const T *Rqh, const T *Rb,  \
+                        T *r, cudaStream_t s) {                                                                  \
+        P##_pmg_rhs(n, c, d, qh, b, Rqh, Rb, r, s);                                                              \
+    }                                                                                                            \
+    static void perturb(const FrLevelT<T> &L, const int *c, int col, int j, const T *q, T *qp, double er,      \
+                        cudaStream_t s) {                                                                        \
+        P##_perturb_color(L, c, col, j, q, qp, er, s);                                                           \
+    }                                                                                                            \
+    static void restore(const FrLevelT<T> &L, const int *c, int col, int j, const T *q, T *qp, cudaStream_t s) { \
+        P##_restore_color(L, c, col, j, q, qp, s);                                                               \
+    }                                                                                                            \
+    static void column(const FrLevelT<T> &L, const int *c, int col, int j, const T *q, const T *R0,             \
+                       const T *Rp, double shift, double er, T *M, cudaStream_t s) {                             \
+        P##_block_column(L, c, col, j, q, R0, Rp, shift, er, M, s);                                              \
+    }                                                                                                            \
+    static int factor(const FrLevelT<T> &L, T *M, int *perm, int *info, cudaStream_t s) {                      \
+        return P##_lu_factor(L, M, perm, info, s);                                                               \
+    }                                                                                                            \
+    static int solve(const FrLevelT<T> &L, const T *M, const int *perm, T *x, cudaStream_t s) {                \
+        return P##_lu_solve(L, M, perm, x, s);                                                                   \
+    }                                                                                                            \
+    static int transfer(const FrLevelT<T> &Lf, const FrLevelT<T> &Lc, bool r, const T *x, T *y,               \
+                        cudaStream_t s) {                                                                        \
+        return P##_transfer(Lf, Lc, r, x, y, s);                                                                 \
+    }
+template <>
+struct Kn<double> {
+    KN_BODY(frk64, double)
+    static constexpr double epsrel = 1e-7;   // FD step of the FP64 blocks: 1e-7 max(1, |q_j|)
+};
+template <>
+struct Kn<float> {
+    KN_BODY(frk32, float)
+    static constexpr double epsrel = 3e-4;   // FP32 blocks: about the square root of FP32 unit roundoff
+};
+
+template <typename T> static FrLevelT<T> *levels(fr_ctx *C);
+template <> FrLevelT<double> *levels<double>(fr_ctx *C) { return C->L; }
+template <> FrLevelT<float> *levels<float>(fr_ctx *C) { return C->L32; }
+template <typename T> static PmgBuf<T> &pbuf(fr_ctx *C);
+template <> PmgBuf<double> &pbuf<double>(fr_ctx *C) { return C->p64; }
+template <> PmgBuf<float> &pbuf<float>(fr_ctx *C) { return C->p32; }
+
+template <typename T>
+static int residual_t(fr_ctx *C, int l, const T *q, T *R, cudaStream_t s) {
+    if (Kn<T>::residual(levels<T>(C)[l], C->ph, q, R, s) != 0)
+        return fail(FR_ERR_UNIMPLEMENTED, "no kernel for d=%d p=%d", C->d, C->L[l].p);
+    CKLAUNCH();
     return FR_OK;
 }
 
-static int elem_blocks(fr_ctx *C, int l, const double *q, double shift, double *M, cudaStream_t s) {
-    TRY(ensure_blk_tmp(C));
-    FrLevel &L = C->L[l];
-    TRY(residual(C, l, q, C->blk_R0, s));
-    frk64_copy(L.ndof, q, C->blk_qp, s);
+// FP32 copies of every level: geometric factors converted on the device, own workspace
+static int ensure_levels32(fr_ctx *C) {
+    if (C->have32) return FR_OK;
+    for (int l = 0; l < C->nlev; ++l) {
+        FrLevel &L = C->L[l];
+        FrLevel32 &M = C->L32[l];
+        M.d = L.d; M.p = L.p; M.n = L.n; M.np = L.np; M.nf1 = L.nf1; M.nfp = L.nfp; M.nv = L.nv; M.E = L.E;
+        M.ndof = L.ndof; M.nd = L.nd; M.npairs = L.npairs; M.pairs = L.pairs; M.bc = L.bc;
+        M.etagL = L.etagL; M.etagR = L.etagR;
+        size_t E = L.E, nsp = (size_t)L.d * L.d * L.np * E, nfpt = (size_t)L.d * L.d * L.nfp * E;
+        TRY(dalloc_t(C, &M.S, nsp)); TRY(dalloc_t(C, &M.G, nsp)); TRY(dalloc_t(C, &M.invJ, (size_t)L.np * E));
+        TRY(dalloc_t(C, &M.Sf, nfpt)); TRY(dalloc_t(C, &M.Gf, nfpt));
+        frk32_d2f(nsp, L.S, M.S, 0); frk32_d2f(nsp, L.G, M.G, 0); frk32_d2f((long long)L.np * E, L.invJ, M.invJ, 0);
+        frk32_d2f(nfpt, L.Sf, M.Sf, 0); frk32_d2f(nfpt, L.Gf, M.Gf, 0);
+        size_t nfv = (size_t)L.nv * L.nfp * E, npv = (size_t)L.nv * L.np * E;
+        TRY(dalloc_t(C, &M.qf, nfv)); TRY(dalloc_t(C, &M.dq, nfv)); TRY(dalloc_t(C, &M.fn, nfv));
+        TRY(dalloc_t(C, &M.Ftf, nfv)); TRY(dalloc_t(C, &M.Q, L.d * npv)); TRY(dalloc_t(C, &M.Ft, L.d * npv));
+        TRY(dalloc_t(C, &M.Qf, L.d * nfv));
+    }
+    long long n0 = C->L[0].ndof;
+    TRY(dalloc_t(C, &C->x32, n0)); TRY(dalloc_t(C, &C->q32, n0)); TRY(dalloc_t(C, &C->Rq32, n0));
+    TRY(dalloc_t(C, &C->y32, n0)); TRY(dalloc_t(C, &C->xmax, 1));
+    CK(cudaDeviceSynchronize());
+    CKLAUNCH();
+    C->have32 = 1;
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------- element blocks
+template <typename T>
+static int ensure_blk_tmp(fr_ctx *C) {
+    PmgBuf<T> &P = pbuf<T>(C);
+    if (P.blk_R0) return FR_OK;
+    long long n0 = C->L[0].ndof;
+    TRY(dalloc_t(C, &P.blk_R0, n0));
+    TRY(dalloc_t(C, &P.blk_Rp, n0));
+    TRY(dalloc_t(C, &P.blk_qp, n0));
+    return FR_OK;
+}
+
+static int ensure_levelsAD(fr_ctx *C) {
+    if (C->haveAD) return FR_OK;
+    for (int l = 0; l < C->nlev; ++l) {
+        FrLevel32 &F = C->L32[l];
+        FrLevelAD &A = C->LA[l];
+        A.d = F.d; A.p = F.p; A.n = F.n; A.np = F.np; A.nf1 = F.nf1; A.nfp = F.nfp; A.nv = F.nv; A.E = F.E;
+        A.ndof = F.ndof; A.nd = F.nd; A.npairs = F.npairs; A.pairs = F.pairs; A.bc = F.bc;
+        A.etagL = F.etagL; A.etagR = F.etagR;
+        A.S = F.S; A.G = F.G; A.invJ = F.invJ; A.Sf = F.Sf; A.Gf = F.Gf;
+        size_t E = F.E, nfv = (size_t)F.nv * F.nfp * E, npv = (size_t)F.nv * F.np * E;
+        TRY(dalloc_t(C, &A.qf, nfv)); TRY(dalloc_t(C, &A.dq, nfv)); TRY(dalloc_t(C, &A.fn, nfv));
+        TRY(dalloc_t(C, &A.Ftf, nfv)); TRY(dalloc_t(C, &A.Q, F.d * npv)); TRY(dalloc_t(C, &A.Ft, F.d * npv));
+        TRY(dalloc_t(C, &A.Qf, F.d * nfv));
+    }
+    TRY(dalloc_t(C, &C->qd, C->L[0].ndof));
+    TRY(dalloc_t(C, &C->Rd, C->L[0].ndof));
+    C->haveAD = 1;
+    return FR_OK;
+}
+
+// FP32 blocks of level l: one forward-mode residual per (colour, column), seed 1 in
+// degree of freedom j of the colour's elements
+static int elem_blocks_ad(fr_ctx *C, int l, const float *q, double shift, float *M, cudaStream_t s) {
+    TRY(ensure_levelsAD(C));
+    FrLevelAD &A = C->LA[l];
+    frkad_init(A.ndof, q, C->qd, s);
+    for (int col = 0; col < C->ncolor; ++col)
+        for (int j = 0; j < A.nd; ++j) {
+            frkad_seed(A, C->color, col, j, C->qd, 1.f, s);
+            if (frkad_residual(A, C->ph, C->qd, C->Rd, s) != 0)
+                return fail(FR_ERR_UNIMPLEMENTED, "no kernel for d=%d p=%d", C->d, A.p);
+            frkad_block_column(A, C->color, col, j, C->Rd, shift, M, s);
+            frkad_seed(A, C->color, col, j, C->qd, 0.f, s);
+        }
+    CKLAUNCH();
+    return FR_OK;
+}
+
+// blocks of level l by colours: one residual per (colour, column); in FP32 the columns
+// come from forward-mode differentiation instead of differences
+template <typename T>
+static int elem_blocks_t(fr_ctx *C, int l, const T *q, double shift, T *M, cudaStream_t s);
+template <>
+int elem_blocks_t<float>(fr_ctx *C, int l, const float *q, double shift, float *M, cudaStream_t s) {
+    return elem_blocks_ad(C, l, q, shift, M, s);
+}
+template <>
+int elem_blocks_t<double>(fr_ctx *C, int l, const double *q, double shift, double *M, cudaStream_t s) {
+    typedef double T;
+    TRY(ensure_blk_tmp<T>(C));
+    PmgBuf<T> &P = pbuf<T>(C);
+    FrLevelT<T> &L = levels<T>(C)[l];
+    TRY(residual_t<T>(C, l, q, P.blk_R0, s));
+    Kn<T>::copy(L.ndof, q, P.blk_qp, s);
     for (int col = 0; col < C->ncolor; ++col)
         for (int j = 0; j < L.nd; ++j) {
-            frk64_perturb_color(L, C->color, col, j, q, C->blk_qp, s);
-            TRY(residual(C, l, C->blk_qp, C->blk_Rp, s));
-            frk64_block_column(L, C->color, col, j, q, C->blk_R0, C->blk_Rp, shift, M, s);
-            frk64_restore_color(L, C->color, col, j, q, C->blk_qp, s);
+            Kn<T>::perturb(L, C->color, col, j, q, P.blk_qp, Kn<T>::epsrel, s);
+            TRY(residual_t<T>(C, l, P.blk_qp, P.blk_Rp, s));
+            Kn<T>::column(L, C->color, col, j, q, P.blk_R0, P.blk_Rp, shift, Kn<T>::epsrel, M, s);
+            Kn<T>::restore(L, C->color, col, j, q, P.blk_qp, s);
         }
     CKLAUNCH();
     return FR_OK;
@@ -304,12 +459,13 @@ static int elem_blocks(fr_ctx *C, int l, const double *q, double shift, double *
 
 extern "C" int fr_elem_blocks(fr_ctx *C, int l, const double *q, double shift, double *M, void *stream) {
     if (!C || l < 0 || l >= C->nlev || !q || !M) return fail(FR_ERR_INVALID_ARG, "bad argument");
-    return elem_blocks(C, l, q, shift, M, S_(stream));
+    return elem_blocks_t<double>(C, l, q, shift, M, S_(stream));
 }
 
-static int block_factor(fr_ctx *C, int l, double *M, int *perm, cudaStream_t s) {
+template <typename T>
+static int block_factor_t(fr_ctx *C, int l, T *M, int *perm, cudaStream_t s) {
     CK(cudaMemsetAsync(C->info, 0, sizeof(int), s));
-    frk64_lu_factor(C->L[l], M, perm, C->info, s);
+    Kn<T>::factor(levels<T>(C)[l], M, perm, C->info, s);
     CKLAUNCH();
     return FR_OK;
 }
@@ -317,7 +473,7 @@ static int block_factor(fr_ctx *C, int l, double *M, int *perm, cudaStream_t s) 
 extern "C" int fr_block_factor(fr_ctx *C, int l, double *M, int *perm, void *stream) {
     if (!C || l < 0 || l >= C->nlev || !M || !perm) return fail(FR_ERR_INVALID_ARG, "bad argument");
     cudaStream_t s = S_(stream);
-    TRY(block_factor(C, l, M, perm, s));
+    TRY(block_factor_t<double>(C, l, M, perm, s));
     int info = 0;
     CK(cudaMemcpyAsync(&info, C->info, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -332,65 +488,87 @@ extern "C" int fr_block_solve(fr_ctx *C, int l, const double *M, const int *perm
     return FR_OK;
 }
 
-static int transfer(fr_ctx *C, int l, bool r, const double *x, double *y, cudaStream_t s) {
-    if (frk64_transfer(C->L[l], C->L[l + 1], r, x, y, s) != 0)
+template <typename T>
+static int transfer_t(fr_ctx *C, int l, bool r, const T *x, T *y, cudaStream_t s) {
+    if (Kn<T>::transfer(levels<T>(C)[l], levels<T>(C)[l + 1], r, x, y, s) != 0)
         return fail(FR_ERR_UNIMPLEMENTED, "no transfer kernel p%d <-> p%d", C->L[l].p, C->L[l + 1].p);
     CKLAUNCH();
     return FR_OK;
 }
 extern "C" int fr_restrict(fr_ctx *C, int l, const double *xf, double *xc, void *stream) {
     if (!C || l < 0 || l + 1 >= C->nlev || !xf || !xc) return fail(FR_ERR_INVALID_ARG, "bad argument");
-    return transfer(C, l, true, xf, xc, S_(stream));
+    return transfer_t<double>(C, l, true, xf, xc, S_(stream));
 }
 extern "C" int fr_prolong(fr_ctx *C, int l, const double *xc, double *xf, void *stream) {
     if (!C || l < 0 || l + 1 >= C->nlev || !xf || !xc) return fail(FR_ERR_INVALID_ARG, "bad argument");
-    return transfer(C, l, false, xc, xf, S_(stream));
+    return transfer_t<double>(C, l, false, xc, xf, S_(stream));
 }
 
 // ------------------------------------------------------------------------- pMG
-static int pmg_alloc(fr_ctx *C, int nlev) {
+template <typename T>
+static int pmg_alloc_t(fr_ctx *C, int nlev) {
+    PmgBuf<T> &P = pbuf<T>(C);
     for (int l = 0; l < nlev; ++l) {
         FrLevel &L = C->L[l];
         size_t need = (size_t)L.E * L.nd * L.nd;
-        if (C->M_cap[l] < need) {
-            dfree(C, C->M[l]);
-            dfree(C, C->perm[l]);
-            C->M[l] = nullptr; C->perm[l] = nullptr; C->M_cap[l] = 0;
-            TRY(dalloc_t(C, &C->M[l], need));
-            TRY(dalloc_t(C, &C->perm[l], (size_t)L.E * L.nd));
-            C->M_cap[l] = need;
+        if (P.M_cap[l] < need) {
+            dfree(C, P.M[l]);
+            dfree(C, P.perm[l]);
+            P.M[l] = nullptr; P.perm[l] = nullptr; P.M_cap[l] = 0;
+            TRY(dalloc_t(C, &P.M[l], need));
+            TRY(dalloc_t(C, &P.perm[l], (size_t)L.E * L.nd));
+            P.M_cap[l] = need;
         }
-        if (!C->pqh[l]) {
+        if (!P.qh[l]) {
             long long n = L.ndof;
-            if (l > 0) { TRY(dalloc_t(C, &C->pb[l], n)); TRY(dalloc_t(C, &C->pRb[l], n)); TRY(dalloc_t(C, &C->pd[l], n)); }
-            TRY(dalloc_t(C, &C->pqh[l], n)); TRY(dalloc_t(C, &C->pRqh[l], n));
-            TRY(dalloc_t(C, &C->prhs[l], n)); TRY(dalloc_t(C, &C->pC[l], n));
+            if (l > 0) { TRY(dalloc_t(C, &P.b[l], n)); TRY(dalloc_t(C, &P.Rb[l], n)); TRY(dalloc_t(C, &P.d[l], n)); }
+            TRY(dalloc_t(C, &P.qh[l], n)); TRY(dalloc_t(C, &P.Rqh[l], n));
+            TRY(dalloc_t(C, &P.rhs[l], n)); TRY(dalloc_t(C, &P.C[l], n));
         }
+    }
+    return FR_OK;
+}
+
+// blocks (1/dtau* + c) I - J_ee at q_ref restricted level by level, and their LU factors
+template <typename T>
+static int pmg_factor_levels(fr_ctx *C, const T *q_ref, const fr_pmg_opts *o, cudaStream_t s) {
+    PmgBuf<T> &P = pbuf<T>(C);
+    double shift = o->inv_dtau_star + o->c;
+    const T *qr = q_ref;
+    for (int l = 0; l < o->nlevels; ++l) {
+        if (l > 0) {
+            TRY(transfer_t<T>(C, l - 1, true, qr, P.b[l], s));   // P.b[l] is free until the first cycle
+            qr = P.b[l];
+        }
+        TRY(elem_blocks_t<T>(C, l, qr, shift, P.M[l], s));
+        TRY(block_factor_t<T>(C, l, P.M[l], P.perm[l], s));
     }
     return FR_OK;
 }
 
 static int pmg_setup_(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, cudaStream_t s) {
     C->pmg_ready = 0;
-    TRY(pmg_alloc(C, o->nlevels));
     C->pmg_nlev = o->nlevels;
     for (int l = 0; l < o->nlevels; ++l) C->nsmooth[l] = o->nsmooth[l];
     C->pmg_c = o->c;
     C->pmg_ids = o->inv_dtau_star;
-    double shift = o->inv_dtau_star + o->c;
-    const double *qr = q_ref;
-    for (int l = 0; l < o->nlevels; ++l) {
-        if (l > 0) {
-            // reference state restricted level by level (kept in pb[l] as scratch)
-            TRY(transfer(C, l - 1, true, qr, C->pb[l], s));
-            qr = C->pb[l];
-        }
-        TRY(elem_blocks(C, l, qr, shift, C->M[l], s));
-        TRY(block_factor(C, l, C->M[l], C->perm[l], s));
+    C->pmg_prec = o->precision;
+    if (o->precision == 0) {
+        TRY(pmg_alloc_t<double>(C, o->nlevels));
+        TRY(pmg_factor_levels<double>(C, q_ref, o, s));
+    } else {
+        TRY(ensure_levels32(C));
+        TRY(pmg_alloc_t<float>(C, o->nlevels));
+        long long n = C->L[0].ndof;
+        if (frk32_absmax(n, q_ref, C->xmax, s) != 0) return fail(FR_ERR_CUDA, "absmax");
+        CK(cudaMemcpyAsync(&C->pmg_qmax, C->xmax, sizeof(double), cudaMemcpyDeviceToHost, s));
+        frk32_d2f(n, q_ref, C->q32, s);
+        TRY(pmg_factor_levels<float>(C, C->q32, o, s));
     }
     int info = 0;
     CK(cudaMemcpyAsync(&info, C->info, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    CKLAUNCH();
     if (info) return fail(FR_ERR_BREAKDOWN, "zero pivot in an element block");
     C->pmg_ready = 1;
     return FR_OK;
@@ -399,57 +577,82 @@ static int pmg_setup_(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, cuda
 extern "C" int pmg_setup(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, void *stream) {
     if (!C || !q_ref || !o) return fail(FR_ERR_INVALID_ARG, "NULL argument");
     if (o->nlevels < 1 || o->nlevels > C->nlev) return fail(FR_ERR_INVALID_ARG, "nlevels %d outside 1..%d", o->nlevels, C->nlev);
+    if (o->precision != 0 && o->precision != 1) return fail(FR_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (FP32)");
     for (int l = 0; l < o->nlevels; ++l)
         if (o->nsmooth[l] < 0) return fail(FR_ERR_INVALID_ARG, "negative smoothing count");
     return pmg_setup_(C, q_ref, o, S_(stream));
 }
 
 // smoothing steps on level l: qh <- qh + M^{-1} (d - (c (qh - b) - (R(qh) - Rb)))
-static int smooth(fr_ctx *C, int l, int nsteps, const double *b, const double *Rb, const double *d, double *qh,
-                  bool first_is_base, cudaStream_t s) {
-    FrLevel &L = C->L[l];
+template <typename T>
+static int smooth_t(fr_ctx *C, int l, int nsteps, const T *b, const T *Rb, const T *d, T *qh, bool first_is_base,
+                    cudaStream_t s) {
+    PmgBuf<T> &P = pbuf<T>(C);
+    FrLevelT<T> &L = levels<T>(C)[l];
     for (int k = 0; k < nsteps; ++k) {
-        if (k == 0 && first_is_base) frk64_copy(L.ndof, d, C->prhs[l], s);
+        if (k == 0 && first_is_base) Kn<T>::copy(L.ndof, d, P.rhs[l], s);
         else {
-            TRY(residual(C, l, qh, C->pRqh[l], s));
-            frk64_pmg_rhs(L.ndof, C->pmg_c, d, qh, b, C->pRqh[l], Rb, C->prhs[l], s);
+            TRY(residual_t<T>(C, l, qh, P.Rqh[l], s));
+            Kn<T>::pmg_rhs(L.ndof, C->pmg_c, d, qh, b, P.Rqh[l], Rb, P.rhs[l], s);
         }
-        frk64_lu_solve(L, C->M[l], C->perm[l], C->prhs[l], s);
-        frk64_add(L.ndof, qh, C->prhs[l], qh, s);
+        Kn<T>::solve(L, P.M[l], P.perm[l], P.rhs[l], s);
+        Kn<T>::add(L.ndof, qh, P.rhs[l], qh, s);
     }
     CKLAUNCH();
     return FR_OK;
 }
 
-static int vcycle(fr_ctx *C, int l, const double *b, const double *Rb, const double *d, double *qh, cudaStream_t s) {
+template <typename T>
+static int vcycle_t(fr_ctx *C, int l, const T *b, const T *Rb, const T *d, T *qh, cudaStream_t s) {
+    PmgBuf<T> &P = pbuf<T>(C);
     int n = C->nsmooth[l];
-    TRY(smooth(C, l, n, b, Rb, d, qh, true, s));
+    TRY(smooth_t<T>(C, l, n, b, Rb, d, qh, true, s));
     if (l + 1 >= C->pmg_nlev) return FR_OK;
-    FrLevel &L = C->L[l];
-    double *r = C->prhs[l];
-    if (n == 0) frk64_copy(L.ndof, d, r, s);
+    FrLevelT<T> &L = levels<T>(C)[l];
+    FrLevelT<T> &L1 = levels<T>(C)[l + 1];
+    T *r = P.rhs[l];
+    if (n == 0) Kn<T>::copy(L.ndof, d, r, s);
     else {
-        TRY(residual(C, l, qh, C->pRqh[l], s));
-        frk64_pmg_rhs(L.ndof, C->pmg_c, d, qh, b, C->pRqh[l], Rb, r, s);
+        TRY(residual_t<T>(C, l, qh, P.Rqh[l], s));
+        Kn<T>::pmg_rhs(L.ndof, C->pmg_c, d, qh, b, P.Rqh[l], Rb, r, s);
     }
-    double *b1 = C->pb[l + 1], *Rb1 = C->pRb[l + 1], *d1 = C->pd[l + 1], *qh1 = C->pqh[l + 1];
-    TRY(transfer(C, l, true, qh, b1, s));
-    TRY(transfer(C, l, true, r, d1, s));
-    TRY(residual(C, l + 1, b1, Rb1, s));
-    frk64_copy(C->L[l + 1].ndof, b1, qh1, s);
-    TRY(vcycle(C, l + 1, b1, Rb1, d1, qh1, s));
-    frk64_sub(C->L[l + 1].ndof, qh1, b1, qh1, s);
-    TRY(transfer(C, l, false, qh1, C->pC[l], s));
-    frk64_add(L.ndof, qh, C->pC[l], qh, s);
-    TRY(smooth(C, l, n, b, Rb, d, qh, false, s));
+    T *b1 = P.b[l + 1], *Rb1 = P.Rb[l + 1], *d1 = P.d[l + 1], *qh1 = P.qh[l + 1];
+    TRY(transfer_t<T>(C, l, true, qh, b1, s));
+    TRY(transfer_t<T>(C, l, true, r, d1, s));
+    TRY(residual_t<T>(C, l + 1, b1, Rb1, s));
+    Kn<T>::copy(L1.ndof, b1, qh1, s);
+    TRY(vcycle_t<T>(C, l + 1, b1, Rb1, d1, qh1, s));
+    Kn<T>::sub(L1.ndof, qh1, b1, qh1, s);
+    TRY(transfer_t<T>(C, l, false, qh1, P.C[l], s));
+    Kn<T>::add(L.ndof, qh, P.C[l], qh, s);
+    TRY(smooth_t<T>(C, l, n, b, Rb, d, qh, false, s));
     return FR_OK;
 }
 
+// alpha: the FP32 cycle is driven with X scaled so that ||Y||_inf ~ alpha ||q||_inf, which keeps
+// R(qh) - R(q) far above FP32 rounding of R while the cycle's nonlinearity stays O(alpha)
+static const double kMixedAlpha = 1e-3;
+
 static int pmg_apply(fr_ctx *C, const double *q, const double *Rq, const double *X, double *Y, cudaStream_t s) {
     long long n = C->L[0].ndof;
-    frk64_copy(n, q, C->pqh[0], s);
-    TRY(vcycle(C, 0, q, Rq, X, C->pqh[0], s));
-    frk64_sub(n, C->pqh[0], q, Y, s);
+    if (C->pmg_prec == 0) {
+        PmgBuf<double> &P = C->p64;
+        frk64_copy(n, q, P.qh[0], s);
+        TRY(vcycle_t<double>(C, 0, q, Rq, X, P.qh[0], s));
+        frk64_sub(n, P.qh[0], q, Y, s);
+        CKLAUNCH();
+        return FR_OK;
+    }
+    PmgBuf<float> &P = C->p32;
+    double target = kMixedAlpha * C->pmg_qmax * (C->pmg_c + C->pmg_ids);
+    if (frk32_absmax(n, X, C->xmax, s) != 0) return fail(FR_ERR_CUDA, "absmax");
+    frk32_d2f_scaled(n, X, C->xmax, target, C->x32, s);
+    frk32_d2f(n, q, C->q32, s);
+    TRY(residual_t<float>(C, 0, C->q32, C->Rq32, s));
+    frk32_copy(n, C->q32, P.qh[0], s);
+    TRY(vcycle_t<float>(C, 0, C->q32, C->Rq32, C->x32, P.qh[0], s));
+    frk32_sub(n, P.qh[0], C->q32, C->y32, s);
+    frk32_f2d_unscale(n, C->y32, C->xmax, target, Y, s);
     CKLAUNCH();
     return FR_OK;
 }
@@ -616,6 +819,7 @@ static int check_solve_opts(const fr_ctx *C, const fr_solve_opts *o) {
         return fail(FR_ERR_INVALID_ARG, "bad solver options");
     if (o->use_pmg && (o->nlevels < 1 || o->nlevels > C->nlev))
         return fail(FR_ERR_INVALID_ARG, "nlevels outside 1..%d", C->nlev);
+    if (o->precision != 0 && o->precision != 1) return fail(FR_ERR_INVALID_ARG, "precision must be 0 or 1");
     return FR_OK;
 }
 
@@ -641,6 +845,7 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
         for (int l = 0; l < 4; ++l) po.nsmooth[l] = o->nsmooth[l];
         po.c = c;
         po.inv_dtau_star = o->inv_dtau_star;
+        po.precision = o->precision;
         TRY(pmg_setup_(C, qn, &po, s));
     }
     fr_gmres_opts go = gm_opts(o, c);
@@ -700,6 +905,7 @@ extern "C" int row_step(fr_ctx *C, const fr_row_tableau *tab, double dt, double 
         for (int l = 0; l < 4; ++l) po.nsmooth[l] = o->nsmooth[l];
         po.c = c;
         po.inv_dtau_star = o->inv_dtau_star;
+        po.precision = o->precision;
         TRY(pmg_setup_(C, qn, &po, s));
     }
     fr_gmres_opts go = gm_opts(o, c);
@@ -749,6 +955,7 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
             for (int l = 0; l < 4; ++l) po.nsmooth[l] = o->nsmooth[l];
             po.c = c;
             po.inv_dtau_star = o->inv_dtau_star < 0 ? c : o->inv_dtau_star;
+            po.precision = o->precision;
             TRY(pmg_setup_(C, q, &po, s));
         }
         fr_gmres_opts go = gm_opts(o, c);

@@ -222,3 +222,72 @@ def test_row_step_converged_state():
     api.row_step(G, gg, ag, cg, mg, dt, qg, go)
     assert relerr(qg, q_or) <= 1e-8
     assert relerr(qg, q0) > 1e-4
+
+
+# ----------------------------------------------------------------- mixed precision
+# The mixed preconditioner (FP32 cycle, FP32 FD blocks and LU) against the FP64 oracle.
+# Same input scaling on both sides (the library scales X so that ||Y||_inf ~ 1e-3
+# ||q||_inf, i.e. s = 1e-3 ||q||_inf (c + 1/dtau*) / ||X||_inf); the difference is then the
+# FP32 arithmetic: FD truncation of the FP32 blocks (step 3e-4 max(1,|q|), relative error
+# ~3e-4), FP32 rounding of R amplified by 1/1e-3 (~6e-5), through n{2-2} smoothing
+# steps: tolerance 5e-3 on the max-norm relative error.
+def test_pmg_precondition_mixed_vs_fp64_oracle(case):
+    O, G, q = case["O"], case["G"], case["q"]
+    if case["mesh"]["E"] > 128:
+        pytest.skip("oracle pMG on the small meshes only")
+    nl = len(case["levels"])
+    nsm = [2, 2, 5][:nl]
+    dt = 0.3
+    c = 1.0 / dt + 1.0 / (0.4358665215084590 * dt)
+    Rq = O.residual(q)
+    X = np.random.default_rng(12).standard_normal(q.shape)
+    X /= np.linalg.norm(X)
+    s = 1e-3 * np.abs(q).max() * (c + 1.0 / dt) / np.abs(X).max()
+    O.pmg_setup(q, nsm, c, 1.0 / dt)
+    Y_or = O.pmg_apply(q, Rq, s * X) / s
+    api.pmg_setup(G, dev(q), nsm, c, 1.0 / dt, precision="mixed")
+    Y_gpu = api.pmg_precondition(G, dev(q), dev(Rq), dev(X))
+    assert relerr(Y_gpu, Y_or) <= 5e-3
+
+
+def test_esdirk_step_mixed_converged_state():
+    """The converged implicit step does not depend on the preconditioner's precision."""
+    mesh = w.box2d(4, 4, 10, 10, qg=2, warp=0.1)
+    ph = w.Physics(mu=0.01, qinf=w.freestream(2, 0.5))
+    X = w.solution_point_coords(mesh, 2)
+    q0 = np.ascontiguousarray(w.isentropic_vortex(X, 5, 5, 5.0, 0.5, 10, 10))
+    dt = 10.0 * w.explicit_dt(mesh, 2, q0)
+    O = oracle.Oracle(mesh, ph, [2, 1])
+    G = api.fr_create(mesh, ph, [2, 1])
+    A, b, _ = OT.esdirk3()
+    oo = O.opts(kdim=30, maxit_gmres=300, max_ptc=40, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-12, dtau=dt,
+                inv_dtau_star=1.0 / dt)
+    q_or, st_or = O.esdirk_step(A, b, dt, q0, oo)
+    from paper_2202_09733_gb300 import tableaux as GT
+    Ag, bg = GT.esdirk3()
+    go = api.solve_opts(kdim=30, maxit_gmres=300, max_ptc=40, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-12,
+                        dtau=dt, inv_dtau_star=1.0 / dt, precision="mixed")
+    qg = dev(q0)
+    st = api.esdirk_step(G, Ag, bg, dt, qg, go)
+    assert st_or["converged"] and st["converged"]
+    assert relerr(qg, q_or) <= 1e-10
+
+
+def test_row_step_mixed_vs_fp64_oracle():
+    mesh = w.box2d(4, 4, 10, 10, qg=2, warp=0.1)
+    ph = w.Physics(mu=0.01, qinf=w.freestream(2, 0.5))
+    X = w.solution_point_coords(mesh, 2)
+    q0 = np.ascontiguousarray(w.isentropic_vortex(X, 5, 5, 5.0, 0.5, 10, 10))
+    dt = 10.0 * w.explicit_dt(mesh, 2, q0)
+    O = oracle.Oracle(mesh, ph, [2, 1])
+    G = api.fr_create(mesh, ph, [2, 1])
+    g, a, c, m = OT.ros34pw2()
+    oo = O.opts(kdim=40, maxit_gmres=400, nsmooth=(2, 2), tol_gmres=1e-9, inv_dtau_star=1.0 / dt)
+    q_or, _ = O.row_step(g, a, c, m, dt, q0, oo)
+    from paper_2202_09733_gb300 import tableaux as GT
+    gg, ag, cg, mg = GT.ros34pw2()
+    go = api.solve_opts(kdim=40, maxit_gmres=400, nsmooth=(2, 2), tol_gmres=1e-9, inv_dtau_star=1.0 / dt,
+                        precision="mixed")
+    qg = dev(q0)
+    api.row_step(G, gg, ag, cg, mg, dt, qg, go)
+    assert relerr(qg, q_or) <= 1e-8
