@@ -236,6 +236,127 @@ __global__ void __launch_bounds__(256) k_lu_factor(FRT *M, int *perm, int nd, in
         for (int t = tid; t < nd * nd; t += nt) Ag[t] = A[t];
 }
 
+// Blocked variant for blocks larger than shared memory: panels of LU_PB columns are
+// factored in shared memory, their row swaps are then applied to the other columns, the
+// panel rows of the trailing columns are forward-substituted (U12) and the trailing
+// matrix receives its rank-LU_PB update in place.  Every entry still receives its updates
+// a_ij = fma(-l_ik, u_kj, a_ij) one k at a time in ascending k, with the same multipliers
+// and pivots as the unblocked elimination, so the factors are identical bit for bit.
+#define LU_PB 32
+__global__ void __launch_bounds__(256) k_lu_factor_blocked(FRT *M, int *perm, int nd, int *info) {
+    extern __shared__ __align__(16) unsigned char dsm_raw[];
+    FRT *Pn = reinterpret_cast<FRT *>(dsm_raw);              // [LU_PB][nd] panel, column-major
+    FRT *U12 = Pn + (size_t)LU_PB * nd;                         // [nd][LU_PB] panel rows of trailing columns
+    __shared__ FRT s_best[8];
+    __shared__ int s_idx[8];
+    __shared__ int s_p;
+    __shared__ int s_piv[LU_PB];
+    int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    FRT *A = M + (size_t)e * nd * nd;
+    int *pv = perm + (size_t)e * nd;
+    for (int t = tid; t < nd; t += nt) pv[t] = t;
+    __syncthreads();
+    for (int k0 = 0; k0 < nd; k0 += LU_PB) {
+        int kb = min(LU_PB, nd - k0);
+        // 1. panel to shared memory (rows k0..nd-1)
+        for (int t = tid; t < kb * nd; t += nt) {
+            int c = t / nd, i = t - c * nd;
+            if (i >= k0) Pn[(size_t)c * nd + i] = A[(size_t)(k0 + c) * nd + i];
+        }
+        __syncthreads();
+        // 2. unblocked elimination of the panel
+        for (int c = 0; c < kb; ++c) {
+            int k = k0 + c;
+            FRT best = -1;
+            int bi = nd;
+            for (int i = k + tid; i < nd; i += nt) {
+                FRT a = fabs(Pn[(size_t)c * nd + i]);
+                if (a > best) { best = a; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                FRT ob = __shfl_down_sync(0xffffffffu, best, o);
+                int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) { s_best[wid] = best; s_idx[wid] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                FRT b = s_best[0];
+                int ix = s_idx[0];
+                for (int w = 1; w < nt / 32; ++w)
+                    if (s_best[w] > b || (s_best[w] == b && s_idx[w] < ix)) { b = s_best[w]; ix = s_idx[w]; }
+                if (ix >= nd) ix = k;
+                s_p = ix;
+                s_piv[c] = ix;
+                if (b == (FRT)0) atomicExch(info, 1);
+                if (ix != k) { int t = pv[k]; pv[k] = pv[ix]; pv[ix] = t; }
+            }
+            __syncthreads();
+            int p = s_p;
+            if (p != k)
+                for (int cc = tid; cc < kb; cc += nt) {
+                    FRT t = Pn[(size_t)cc * nd + k];
+                    Pn[(size_t)cc * nd + k] = Pn[(size_t)cc * nd + p];
+                    Pn[(size_t)cc * nd + p] = t;
+                }
+            __syncthreads();
+            FRT piv = Pn[(size_t)c * nd + k];
+            for (int i = k + 1 + tid; i < nd; i += nt) Pn[(size_t)c * nd + i] = Pn[(size_t)c * nd + i] / piv;
+            __syncthreads();
+            int m = nd - k - 1, w = kb - c - 1;
+            for (int t = tid; t < m * w; t += nt) {
+                int cc = c + 1 + t / m, i = k + 1 + t % m;
+                Pn[(size_t)cc * nd + i] = fma(-Pn[(size_t)c * nd + i], Pn[(size_t)cc * nd + k], Pn[(size_t)cc * nd + i]);
+            }
+            __syncthreads();
+        }
+        // 3. panel back to global memory
+        for (int t = tid; t < kb * nd; t += nt) {
+            int c = t / nd, i = t - c * nd;
+            if (i >= k0) A[(size_t)(k0 + c) * nd + i] = Pn[(size_t)c * nd + i];
+        }
+        // 4. the panel's row swaps, in order, on every other column
+        for (int j = tid; j < nd; j += nt) {
+            if (j >= k0 && j < k0 + kb) continue;
+            FRT *col = A + (size_t)j * nd;
+            for (int c = 0; c < kb; ++c) {
+                int p = s_piv[c], k = k0 + c;
+                if (p != k) { FRT t = col[k]; col[k] = col[p]; col[p] = t; }
+            }
+        }
+        __syncthreads();
+        int r0 = k0 + kb, mt = nd - r0;
+        if (mt > 0) {
+            // 5. U12: forward substitution of the panel rows of every trailing column
+            for (int j = r0 + tid; j < nd; j += nt) {
+                FRT u[LU_PB];
+                FRT *col = A + (size_t)j * nd + k0;
+#pragma unroll
+                for (int c = 0; c < LU_PB; ++c) u[c] = c < kb ? col[c] : (FRT)0;
+#pragma unroll
+                for (int cp = 0; cp < LU_PB; ++cp)
+#pragma unroll
+                    for (int c = cp + 1; c < LU_PB; ++c)
+                        if (c < kb) u[c] = fma(-Pn[(size_t)cp * nd + k0 + c], u[cp], u[c]);
+#pragma unroll
+                for (int c = 0; c < LU_PB; ++c)
+                    if (c < kb) { col[c] = u[c]; U12[(size_t)(j - r0) * LU_PB + c] = u[c]; }
+            }
+            __syncthreads();
+            // 6. trailing update in place, one k at a time
+            for (int t = tid; t < mt * mt; t += nt) {
+                int jj = t / mt, i = r0 + (t - jj * mt);
+                FRT *pa = A + (size_t)(r0 + jj) * nd + i;
+                FRT a = *pa;
+                const FRT *uj = U12 + (size_t)jj * LU_PB;
+                for (int c = 0; c < kb; ++c) a = fma(-Pn[(size_t)c * nd + i], uj[c], a);
+                *pa = a;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 int FRK(lu_factor)(const FrLevelT<FRT> &L, FRT *M, int *perm, int *info, cudaStream_t s) {
     size_t sm = sizeof(FRT) * (size_t)L.nd * L.nd;
     if (sm <= 200 * 1024) {
@@ -245,9 +366,19 @@ int FRK(lu_factor)(const FrLevelT<FRT> &L, FRT *M, int *perm, int *info, cudaStr
             attr = true;
         }
         CNT(); k_lu_factor<true><<<L.E, 256, sm, s>>>(M, perm, L.nd, info);
-    } else {
-        CNT(); k_lu_factor<false><<<L.E, 256, 0, s>>>(M, perm, L.nd, info);
+        return 0;
     }
+    size_t smb = sizeof(FRT) * (size_t)2 * LU_PB * L.nd;
+    if (smb <= 200 * 1024) {
+        static bool attrb = false;
+        if (!attrb) {
+            cudaFuncSetAttribute(k_lu_factor_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attrb = true;
+        }
+        CNT(); k_lu_factor_blocked<<<L.E, 256, smb, s>>>(M, perm, L.nd, info);
+        return 0;
+    }
+    CNT(); k_lu_factor<false><<<L.E, 256, 0, s>>>(M, perm, L.nd, info);
     return 0;
 }
 
@@ -350,7 +481,12 @@ int FRK(lu_solve)(const FrLevelT<FRT> &L, const FRT *M, const int *perm, FRT *x,
         case 6: { CNT(); k_lu_solve<6, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
         case 7: { CNT(); k_lu_solve<7, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
         case 8: { CNT(); k_lu_solve<8, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
-        case 10: { CNT(); k_lu_solve<10, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
+        case 10: {
+            CNT();
+            if (sizeof(FRT) == 4) k_lu_solve<10, 4><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E);
+            else k_lu_solve<10, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E);
+            break;
+        }
         default: return -1;
     }
     return 0;
