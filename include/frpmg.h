@@ -145,8 +145,12 @@ int fr_prolong(fr_ctx *ctx, int level, const double *x_coarse, double *x_fine, v
  * the cycle, its residuals on every level, the element blocks and their LU factors and
  * solves run in FP32, the blocks' columns by forward-mode differentiation of the FP32
  * residual (exact derivatives, no finite-difference noise); X is scaled on the
- * device so that ||Y||_inf ~ 1e-3 ||q_ref||_inf inside the cycle (keeping R(qh) - R(q)
- * clear of FP32 rounding) and Y is scaled back and returned in FP64. */
+ * device so that max_v ||Y_v||_inf / max|q_ref,v| ~ 1e-2 inside the cycle (keeping
+ * R(qh) - R(q) clear of FP32 rounding; the scale starts from the gain 1/((c + 1/dtau*)
+ * min_v max|q_ref,v|) and follows the gain measured by the previous call, and a call
+ * that lands more than 30x off repeats its cycle once at the measured gain), and Y is
+ * scaled back and returned in FP64.  Each mixed call reads nv maxima back to the host
+ * (one stream synchronisation). */
 typedef struct {
     int nlevels;
     int nsmooth[4];
@@ -184,10 +188,27 @@ typedef struct {
     int kdim, maxit_gmres, max_ptc, nlevels, nsmooth[4], use_pmg;
     double tol_gmres, tol_newton, eps, dtau, inv_dtau_star;
     int precision;   /* preconditioner precision, as fr_pmg_opts.precision */
+    /* Newton initial guess of the ESDIRK stages (esdirk_step only; the paper uses q^n):
+     * 0: q^n; 1: the better (smaller FP64 stage residual RMS(a_ii dt F)) of q^n and the
+     * quadratic extrapolation in time of the last three converged steps to t_n + c_i dt;
+     * 2: as 1 plus the extrapolation corrected by the attached network (fr_set_mlp): the
+ *    network's correction d enters scaled by the beta in [-1, 2] that minimises the
+ *    linearised ||F(qex + beta d)|| (one extra residual), or unscaled if that is better.
+     * train_iters > 0: after the step, the converged stages join a training ring (the
+     * last six steps) and the network takes train_iters Adam steps of train_batch
+     * samples at learning rate lr. */
+    int guess, train_iters, train_batch;
+    double lr;
 } fr_solve_opts;
 typedef struct {
     int n_ptc, n_gmres, converged;
     double final_res;
+    double guess_rms[3];   /* mean over stages of RMS(a_ii dt F) of q^n, extrapolation, network guess */
+    int guess_pick[3];     /* how many stages started from each candidate */
+    double guess_beta;     /* mean step along the network's correction (guess 2) */
+    double train_loss;     /* loss of the last training step (train_iters > 0) */
+    int prec_switch_it;    /* ptc_steady: pseudo step after which the FP32 preconditioner
+                              stalled and the FP64 one took over (-1: never) */
 } fr_step_stats;
 
 /* ESDIRK step, Eq. (2): stages solved by PTC/Newton (Eqs. 5-7) with FGMRES, the
@@ -202,6 +223,37 @@ typedef struct {
 } fr_esdirk_tableau;
 int esdirk_step(fr_ctx *ctx, const fr_esdirk_tableau *tab, double dt, double *q,
                 const fr_solve_opts *opts, fr_step_stats *stats, void *stream);
+
+/* Per-element network for the Newton initial guess (not in the paper; see fr_solve_opts.guess):
+ *   h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = W3 h2 + b3,
+ * bfloat16 operands and FP32 accumulation on the tensor cores, FP32 master weights and
+ * Adam moments.  params (host float): W1[hidden][in], b1[hidden], W2[hidden][hidden],
+ * b2[hidden], W3[out][hidden], b3[out]; the caller draws the initial values.  Features of
+ * element e: (q^n - q^{n-1})/s_v, (q^{n-1} - q^{n-2})/s_v, (q^n - qinf_v)/sig_v,
+ * dt R(q^n)/s_v, log J / 10, the stage abscissa c_i, zero padding (s_v, sig_v: per-variable
+ * RMS of q^n - q^{n-1} and q^n - qinf over the mesh);
+ * output: the stage state's correction of the extrapolation, in units of s_v. */
+typedef struct fr_mlp fr_mlp;
+int mlp_create(fr_mlp **out, int in_dim, int hidden, int out_dim, const float *params);
+int mlp_destroy(fr_mlp *mlp);
+int mlp_get_params(const fr_mlp *mlp, float *params /* host */);
+/* X: device bfloat16 [B][in] (as unsigned short), Y: device float [B][out] */
+int mlp_forward(fr_mlp *mlp, int B, const unsigned short *X, float *Y, void *stream);
+/* one step: forward, mean-squared loss against T (device float [B][out]), backward, Adam.
+ * loss (host, may be NULL) synchronises the stream; grads (device float, parameter
+ * layout, may be NULL) receives the gradients before the update. */
+int mlp_train_step(fr_mlp *mlp, int B, const unsigned short *X, const float *T, float lr, float *loss, float *grads,
+                   void *stream);
+/* network sizes the context expects (in = 4 nd + Np + 1 rounded up to 16, out = nd) */
+int fr_mlp_dims(const fr_ctx *ctx, int *in_dim, int *out_dim);
+int fr_set_mlp(fr_ctx *ctx, fr_mlp *mlp);
+/* the network's inputs for states q^n, q^{n-1}, q^{n-2} (device, level-0 layout), R(q^n),
+ * dt and stage abscissa c: X device bfloat16 [E][in]; scales (host double[10], may be
+ * NULL) receives s_0..s_4 and sig_0..sig_4 (entries past nv unused). */
+int fr_guess_features(fr_ctx *ctx, const double *qn, const double *q1, const double *q2, const double *Rn, double dt,
+                      double c, unsigned short *X, double *scales, void *stream);
+/* forget the converged-state history and the training ring (start of a new trajectory) */
+int fr_reset_history(fr_ctx *ctx);
 
 /* Rosenbrock-Wanner step in the variables of Eq. (3):
  * (I/(gamma dt) - dR/dq(q^n)) Y_i = R(q^n + sum_j a_ij Y_j) + (1/dt) sum_j c_ij Y_j,
@@ -219,7 +271,10 @@ int row_step(fr_ctx *ctx, const fr_row_tableau *tab, double dt, double *q, const
 /* Steady PTC (Eq. 7 without the dt terms) with the SER pseudo-step of Eq. (10), read as
  * dtau <- min(dtau ||R^k|| / ||R^{k+1}||, dtau_max); preconditioner re-set at every
  * iteration with c = 1/dtau (inv_dtau_star < 0 selects 1/dtau* = c).  Stops at
- * ||R|| <= tol_rel ||R_0||.  hist: host [max_it+1] residual norms (may be NULL). */
+ * ||R|| <= tol_rel ||R_0||.  hist: host [max_it+1] residual norms (may be NULL).
+ * precision = 1: the FP32 cycle until a pseudo step where FGMRES used all maxit_gmres
+ * iterations and ||R|| fell by less than half; from then on the FP64 cycle
+ * (stats->prec_switch_it records the step). */
 int ptc_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
                const fr_solve_opts *opts, fr_step_stats *stats, double *hist, void *stream);
 

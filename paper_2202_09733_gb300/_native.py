@@ -9,7 +9,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfrpmg.so")
 
-PD, PI = C.POINTER(C.c_double), C.POINTER(C.c_int)
+PD, PI, PF = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_float)
 VP = C.c_void_p
 
 FR_OK = 0
@@ -20,7 +20,9 @@ ERRORS = {-1: "FR_ERR_INVALID_ARG", -2: "FR_ERR_CUDA", -3: "FR_ERR_OOM", -4: "FR
 EXPORTS = ["fr_create", "fr_destroy", "fr_last_error", "fr_kernel_launches", "fr_level_info", "fr_num_colors", "fr_residual",
            "fr_residual_noalloc", "fr_jvp",
            "fr_elem_blocks", "fr_block_factor", "fr_block_solve", "fr_restrict", "fr_prolong", "pmg_setup",
-           "pmg_precondition", "gmres_solve", "esdirk_step", "row_step", "ptc_steady"]
+           "pmg_precondition", "gmres_solve", "esdirk_step", "row_step", "ptc_steady",
+           "mlp_create", "mlp_destroy", "mlp_get_params", "mlp_forward", "mlp_train_step", "fr_mlp_dims",
+           "fr_set_mlp", "fr_reset_history", "fr_guess_features"]
 
 
 class MeshDesc(C.Structure):
@@ -51,11 +53,14 @@ class SolveOpts(C.Structure):
     _fields_ = [("kdim", C.c_int), ("maxit_gmres", C.c_int), ("max_ptc", C.c_int), ("nlevels", C.c_int),
                 ("nsmooth", C.c_int * 4), ("use_pmg", C.c_int), ("tol_gmres", C.c_double),
                 ("tol_newton", C.c_double), ("eps", C.c_double), ("dtau", C.c_double),
-                ("inv_dtau_star", C.c_double), ("precision", C.c_int)]
+                ("inv_dtau_star", C.c_double), ("precision", C.c_int), ("guess", C.c_int),
+                ("train_iters", C.c_int), ("train_batch", C.c_int), ("lr", C.c_double)]
 
 
 class StepStats(C.Structure):
-    _fields_ = [("n_ptc", C.c_int), ("n_gmres", C.c_int), ("converged", C.c_int), ("final_res", C.c_double)]
+    _fields_ = [("n_ptc", C.c_int), ("n_gmres", C.c_int), ("converged", C.c_int), ("final_res", C.c_double),
+                ("guess_rms", C.c_double * 3), ("guess_pick", C.c_int * 3), ("guess_beta", C.c_double),
+                ("train_loss", C.c_double), ("prec_switch_it", C.c_int)]
 
 
 class EsdirkTableau(C.Structure):
@@ -102,6 +107,15 @@ def load(path: str = LIB_PATH):
                      C.c_int),
         "ptc_steady": ([VP, VP, C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(SolveOpts),
                         C.POINTER(StepStats), PD, VP], C.c_int),
+        "mlp_create": ([C.POINTER(VP), C.c_int, C.c_int, C.c_int, PF], C.c_int),
+        "mlp_destroy": ([VP], C.c_int),
+        "mlp_get_params": ([VP, PF], C.c_int),
+        "mlp_forward": ([VP, C.c_int, VP, VP, VP], C.c_int),
+        "mlp_train_step": ([VP, C.c_int, VP, VP, C.c_float, PF, VP, VP], C.c_int),
+        "fr_mlp_dims": ([VP, PI, PI], C.c_int),
+        "fr_set_mlp": ([VP, VP], C.c_int),
+        "fr_reset_history": ([VP], C.c_int),
+        "fr_guess_features": ([VP, VP, VP, VP, VP, C.c_double, C.c_double, VP, PD, VP], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

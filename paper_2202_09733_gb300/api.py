@@ -167,7 +167,11 @@ def _prec(p):
 
 
 def solve_opts(kdim=30, maxit_gmres=300, max_ptc=100, nsmooth=(2, 2), use_pmg=True, tol_gmres=1e-1,
-               tol_newton=1e-8, eps=1e-6, dtau=1.0, inv_dtau_star=0.0, precision="fp64"):
+               tol_newton=1e-8, eps=1e-6, dtau=1.0, inv_dtau_star=0.0, precision="fp64", guess="qn",
+               train_iters=0, train_batch=4096, lr=1e-3):
+    """guess: "qn" (the paper's q^n), "extrap" (best of q^n and the quadratic extrapolation
+    in time) or "mlp" (also the network-corrected extrapolation); train_iters > 0 trains
+    the attached network after every ESDIRK step."""
     o = N.SolveOpts()
     o.kdim, o.maxit_gmres, o.max_ptc, o.nlevels = int(kdim), int(maxit_gmres), int(max_ptc), len(nsmooth)
     for i, n in enumerate(nsmooth):
@@ -175,11 +179,17 @@ def solve_opts(kdim=30, maxit_gmres=300, max_ptc=100, nsmooth=(2, 2), use_pmg=Tr
     o.use_pmg, o.tol_gmres, o.tol_newton, o.eps = int(bool(use_pmg)), float(tol_gmres), float(tol_newton), float(eps)
     o.dtau, o.inv_dtau_star = float(dtau), float(inv_dtau_star)
     o.precision = _prec(precision)
+    guesses = {"qn": 0, "extrap": 1, "mlp": 2}
+    if guess not in guesses:
+        raise ValueError(f"guess must be one of {sorted(guesses)}")
+    o.guess, o.train_iters, o.train_batch, o.lr = guesses[guess], int(train_iters), int(train_batch), float(lr)
     return o
 
 
 def _stats(st):
-    return dict(n_ptc=st.n_ptc, n_gmres=st.n_gmres, converged=st.converged, final_res=st.final_res)
+    return dict(n_ptc=st.n_ptc, n_gmres=st.n_gmres, converged=st.converged, final_res=st.final_res,
+                guess_rms=list(st.guess_rms), guess_pick=list(st.guess_pick), guess_beta=st.guess_beta,
+                train_loss=st.train_loss, prec_switch_it=st.prec_switch_it)
 
 
 def esdirk_step(ctx, A, b, dt, q, opts, stream=None, allow_not_converged=True):
@@ -222,3 +232,77 @@ def ptc_steady(ctx, q, dtau_init, dtau_max, tol_rel, max_it, opts, stream=None):
     out = _stats(st)
     out["hist"] = hist[:st.n_ptc + 1]
     return out
+
+
+class MLP:
+    """Per-element BF16 network of the Newton initial guess (libfrpmg mlp_*)."""
+
+    def __init__(self, in_dim, hidden, out_dim, params: np.ndarray):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        self.in_dim, self.hidden, self.out_dim = int(in_dim), int(hidden), int(out_dim)
+        self.nparams = hidden * in_dim + hidden + hidden * hidden + hidden + out_dim * hidden + out_dim
+        if params.size != self.nparams:
+            raise ValueError(f"expected {self.nparams} parameters, got {params.size}")
+        h = C.c_void_p()
+        N.check(N.load().mlp_create(C.byref(h), self.in_dim, self.hidden, self.out_dim,
+                                    params.ctypes.data_as(N.PF)), "mlp_create")
+        self.handle = h
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.nparams, dtype=np.float32)
+        N.check(N.load().mlp_get_params(self.handle, out.ctypes.data_as(N.PF)), "mlp_get_params")
+        return out
+
+    def forward(self, X: torch.Tensor, Y: torch.Tensor | None = None, stream=None):
+        """X: CUDA bfloat16 [B, in]; returns float32 [B, out]."""
+        B = X.shape[0]
+        if Y is None:
+            Y = torch.empty((B, self.out_dim), dtype=torch.float32, device=X.device)
+        N.check(N.load().mlp_forward(self.handle, B, _dev(X, torch.bfloat16, "X"), _dev(Y, torch.float32, "Y"),
+                                     _stream(stream)), "mlp_forward")
+        return Y
+
+    def train_step(self, X: torch.Tensor, T: torch.Tensor, lr=1e-3, grads: torch.Tensor | None = None,
+                   want_loss=True, stream=None):
+        loss = C.c_float()
+        N.check(N.load().mlp_train_step(self.handle, X.shape[0], _dev(X, torch.bfloat16, "X"),
+                                        _dev(T, torch.float32, "T"), float(lr),
+                                        C.byref(loss) if want_loss else None,
+                                        _dev(grads, torch.float32, "grads") if grads is not None else None,
+                                        _stream(stream)), "mlp_train_step")
+        return loss.value if want_loss else None
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                N.load().mlp_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def fr_mlp_dims(ctx):
+    i, o = C.c_int(), C.c_int()
+    N.check(N.load().fr_mlp_dims(ctx.handle, C.byref(i), C.byref(o)), "fr_mlp_dims")
+    return i.value, o.value
+
+
+def fr_set_mlp(ctx, mlp: MLP | None):
+    N.check(N.load().fr_set_mlp(ctx.handle, mlp.handle if mlp is not None else None), "fr_set_mlp")
+    ctx._mlp = mlp   # keep the network alive while attached
+
+
+def fr_guess_features(ctx, qn, q1, q2, Rn, dt, c, stream=None):
+    """Network inputs (CUDA bfloat16 [E, in]) and the per-variable scales (s, sig)."""
+    K0, _ = fr_mlp_dims(ctx)
+    X = torch.empty((ctx.E, K0), dtype=torch.bfloat16, device="cuda")
+    sc = np.zeros(10)
+    N.check(N.load().fr_guess_features(ctx.handle, _dev(qn), _dev(q1), _dev(q2), _dev(Rn), float(dt), float(c),
+                                       _dev(X, torch.bfloat16, "X"), sc.ctypes.data_as(N.PD), _stream(stream)),
+            "fr_guess_features")
+    return X, sc[:ctx.nv], sc[5:5 + ctx.nv]
+
+
+def fr_reset_history(ctx):
+    N.check(N.load().fr_reset_history(ctx.handle), "fr_reset_history")

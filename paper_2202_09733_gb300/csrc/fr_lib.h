@@ -78,6 +78,9 @@ void frk64_update_x(long long n, int m, const double *y_host, const double *cons
 void frk32_d2f(long long n, const double *x, float *y, cudaStream_t s);
 void frk32_f2d_scaled(long long n, const float *x, double inv_s, double *y, cudaStream_t s);
 void frk32_d2f_scaled(long long n, const double *x, const double *xmax_dev, double target, float *y, cudaStream_t s);
+// per-variable max |x| of a [nv][per] vector into out_dev[0..nv)
+int frk32_absmax_var(int nv, long long per, const double *x, double *out_dev, cudaStream_t s);
+int frk32_absmax_var_f(int nv, long long per, const float *x, double *out_dev, cudaStream_t s);
 int frk32_absmax(long long n, const double *x, double *out_dev, cudaStream_t s);
 void frk32_f2d_unscale(long long n, const float *x, const double *xmax_dev, double target, double *y, cudaStream_t s);
 
@@ -89,3 +92,20 @@ void frkad_init(long long n, const float *q, DualF *qd, cudaStream_t s);        
 void frkad_seed(const FrLevelAD &L, const int *color, int col, int j, DualF *qd, float seed, cudaStream_t s);
 void frkad_block_column(const FrLevelAD &L, const int *color, int col, int j, const DualF *Rd, double shift,
                         float *M, cudaStream_t s);
+
+// learned initial guess (mlp.cu)
+struct fr_mlp;
+unsigned long long frkmlp_launch_count();
+void frkmlp_features(int E, int nv, int Np, int K0, const double *qn, const double *q1, const double *q2,
+                     const double *Rn, double dt, const double *invJ, double c, const double *s_dev,
+                     const double *sig_dev, const double *qinf_dev, unsigned short *X, cudaStream_t st);
+void frkmlp_extrap(long long n, const double *qn, const double *q1, const double *q2, double c, double *qex,
+                   cudaStream_t st);
+void frkmlp_targets(int E, int nv, int Np, const double *qs, const double *qex, const double *s_dev, float *T,
+                    cudaStream_t st);
+void frkmlp_guess(int E, int nv, int Np, const double *qex, const double *s_dev, const float *Y, double *g,
+                  cudaStream_t st);
+int frkmlp_forward(fr_mlp *M, int B, const unsigned short *X, float *Y, cudaStream_t s);
+int frkmlp_dims(const fr_mlp *M, int *in, int *hid, int *out);
+int frkmlp_var_stats(int nv, long long per, const double *a, const double *b, const double *qinf_dev, double *part,
+                     double *out_dev, cudaStream_t s);

@@ -1,3 +1,4 @@
+#include <algorithm>
 // FP32 kernels of the mixed-precision preconditioner (residuals on every p-level,
 // element blocks, block LU and solves, transfers), plus the FP64 <-> FP32 conversions at
 // the preconditioner's boundary.  Contraction is allowed in this unit.
@@ -35,6 +36,29 @@ int frk32_absmax(long long n, const double *x, double *out_dev, cudaStream_t s) 
     if (cudaMemsetAsync(out_dev, 0, sizeof(double), s) != cudaSuccess) return -1;
     CNT(); k_absmax<<<nblk(n), 256, 0, s>>>(n, x, (unsigned long long *)out_dev);
     return 0;
+}
+// per-variable max |x| of a [nv][per] vector: blockIdx.y = variable
+template <typename S>
+__global__ void k_absmax_var(long long per, const S *x, unsigned long long *out) {
+    const S *xv = x + (size_t)blockIdx.y * per;
+    double m = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per; i += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, fabs((double)xv[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, (unsigned long long)__double_as_longlong(m));
+}
+template <typename S>
+static int absmax_var(int nv, long long per, const S *x, double *out_dev, cudaStream_t s) {
+    if (cudaMemsetAsync(out_dev, 0, sizeof(double) * nv, s) != cudaSuccess) return -1;
+    int gx = (int)std::min<long long>((per + 255) / 256, 152LL * 4);
+    CNT(); k_absmax_var<S><<<dim3(gx, nv), 256, 0, s>>>(per, x, (unsigned long long *)out_dev);
+    return 0;
+}
+int frk32_absmax_var(int nv, long long per, const double *x, double *out_dev, cudaStream_t s) {
+    return absmax_var<double>(nv, per, x, out_dev, s);
+}
+int frk32_absmax_var_f(int nv, long long per, const float *x, double *out_dev, cudaStream_t s) {
+    return absmax_var<float>(nv, per, x, out_dev, s);
 }
 // y = double(x) * (max / target): undoes the input scaling of the FP32 cycle
 __global__ void k_f2d_unscale(long long n, const float *x, const double *xmax, double target, double *y) {

@@ -9,6 +9,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <algorithm>
 #include <vector>
 #include "../../include/frpmg.h"
 #include "fr_lib.h"
@@ -71,7 +72,9 @@ struct fr_ctx {
     double *dots;                 // device scratch for inner products (64)
     // pMG
     int pmg_ready, pmg_nlev, pmg_prec, nsmooth[FRL_MAXLEV];
-    double pmg_c, pmg_ids, pmg_qmax;
+    double pmg_c, pmg_ids, pmg_qref[5];
+    double pmg_gain;   // mixed cycle: last measured max_v ||Y_v||_inf / qref_v per ||X||_inf
+    double *ymax;
     PmgBuf<double> p64;
     PmgBuf<float> p32;
     float *x32, *q32, *Rq32, *y32;
@@ -81,6 +84,15 @@ struct fr_ctx {
     double *gw, *gr, *gtmp;
     // steppers
     std::vector<double *> stv;
+    // initial guess: last three converged states, extrapolation, learned correction
+    double *hist[3];              // q^{n-2}, q^{n-1}, q^n
+    int nhist;
+    fr_mlp *mlp;
+    int K0, O, mlp_steps;
+    double *qex, *qcand, *Rtmp, *Ftmp, *Fex, *sdev, *qinf_dev, *vpart;
+    unsigned short *Xf, *ringX;
+    float *Yf, *Tf, *ringT;
+    int ring_cap, ring_n, ring_head, train_cursor;
 };
 
 static int dalloc(fr_ctx *C, void **p, size_t bytes) {
@@ -110,7 +122,7 @@ static cudaStream_t S_(void *s) { return (cudaStream_t)s; }
 extern "C" const char *fr_last_error(void) { return g_err; }
 
 extern "C" unsigned long long fr_kernel_launches(void) {
-    return frk64_launch_count() + frk32_launch_count() + frkad_launch_count();
+    return frk64_launch_count() + frk32_launch_count() + frkad_launch_count() + frkmlp_launch_count();
 }
 
 // ---------------------------------------------------------------- context set-up
@@ -553,6 +565,7 @@ static int pmg_setup_(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, cuda
     C->pmg_c = o->c;
     C->pmg_ids = o->inv_dtau_star;
     C->pmg_prec = o->precision;
+    C->pmg_gain = o->c + o->inv_dtau_star > 0.0 ? 1.0 / (o->c + o->inv_dtau_star) : 1.0;
     if (o->precision == 0) {
         TRY(pmg_alloc_t<double>(C, o->nlevels));
         TRY(pmg_factor_levels<double>(C, q_ref, o, s));
@@ -560,8 +573,20 @@ static int pmg_setup_(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, cuda
         TRY(ensure_levels32(C));
         TRY(pmg_alloc_t<float>(C, o->nlevels));
         long long n = C->L[0].ndof;
-        if (frk32_absmax(n, q_ref, C->xmax, s) != 0) return fail(FR_ERR_CUDA, "absmax");
-        CK(cudaMemcpyAsync(&C->pmg_qmax, C->xmax, sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (!C->ymax) TRY(dalloc_t(C, &C->ymax, 5));
+        if (frk32_absmax_var(C->nv, n / C->nv, q_ref, C->ymax, s) != 0) return fail(FR_ERR_CUDA, "absmax");
+        CK(cudaMemcpyAsync(C->pmg_qref, C->ymax, sizeof(double) * C->nv, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        // per-variable magnitudes of the reference state, floored at 1e-3 of the largest
+        // (a momentum component of a flow at rest); the cycle's first gain guess
+        double qbig = 0.0, qsmall = INFINITY;
+        for (int v = 0; v < C->nv; ++v) qbig = fmax(qbig, C->pmg_qref[v]);
+        for (int v = 0; v < C->nv; ++v) {
+            C->pmg_qref[v] = fmax(C->pmg_qref[v], 1e-3 * qbig);
+            qsmall = fmin(qsmall, C->pmg_qref[v]);
+        }
+        if (!(qsmall > 0.0)) return fail(FR_ERR_INVALID_ARG, "reference state is zero");
+        C->pmg_gain /= qsmall;
         frk32_d2f(n, q_ref, C->q32, s);
         TRY(pmg_factor_levels<float>(C, C->q32, o, s));
     }
@@ -629,9 +654,18 @@ static int vcycle_t(fr_ctx *C, int l, const T *b, const T *Rb, const T *d, T *qh
     return FR_OK;
 }
 
-// alpha: the FP32 cycle is driven with X scaled so that ||Y||_inf ~ alpha ||q||_inf, which keeps
-// R(qh) - R(q) far above FP32 rounding of R while the cycle's nonlinearity stays O(alpha)
-static const double kMixedAlpha = 1e-3;
+// alpha: the FP32 cycle is driven with X scaled so that max_v ||Y_v||_inf / qref_v ~ alpha
+// (qref_v: magnitude of variable v in the reference state).  FP32 rounding of R(qh) - R(q)
+// perturbs the result by ~2.5e-5 / alpha relative (measured against the FP64 cycle at the
+// same scale on stretched curved meshes); the cycle's own nonlinearity grows with alpha but
+// leaves it a preconditioner (FGMRES takes a varying one).
+// The scale needs the cycle's gain (relative ||Y|| per ||X||_inf): 1 / ((c + 1/dtau*) min_v
+// qref_v) to start with (exact for a diagonally dominant operator), then the gain measured
+// by the previous application.  If an application lands more than kMixedSlack away from
+// the target (a small c, where the Jacobian and not c sets the gain), it is repeated once
+// at the measured gain.
+static const double kMixedAlpha = 1e-2;
+static const double kMixedSlack = 30.0;
 
 static int pmg_apply(fr_ctx *C, const double *q, const double *Rq, const double *X, double *Y, cudaStream_t s) {
     long long n = C->L[0].ndof;
@@ -644,14 +678,25 @@ static int pmg_apply(fr_ctx *C, const double *q, const double *Rq, const double 
         return FR_OK;
     }
     PmgBuf<float> &P = C->p32;
-    double target = kMixedAlpha * C->pmg_qmax * (C->pmg_c + C->pmg_ids);
     if (frk32_absmax(n, X, C->xmax, s) != 0) return fail(FR_ERR_CUDA, "absmax");
-    frk32_d2f_scaled(n, X, C->xmax, target, C->x32, s);
     frk32_d2f(n, q, C->q32, s);
     TRY(residual_t<float>(C, 0, C->q32, C->Rq32, s));
-    frk32_copy(n, C->q32, P.qh[0], s);
-    TRY(vcycle_t<float>(C, 0, C->q32, C->Rq32, C->x32, P.qh[0], s));
-    frk32_sub(n, P.qh[0], C->q32, C->y32, s);
+    double want = kMixedAlpha, target = want / C->pmg_gain;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (attempt) target = want / C->pmg_gain;
+        frk32_d2f_scaled(n, X, C->xmax, target, C->x32, s);
+        frk32_copy(n, C->q32, P.qh[0], s);
+        TRY(vcycle_t<float>(C, 0, C->q32, C->Rq32, C->x32, P.qh[0], s));
+        frk32_sub(n, P.qh[0], C->q32, C->y32, s);
+        if (frk32_absmax_var_f(C->nv, n / C->nv, C->y32, C->ymax, s) != 0) return fail(FR_ERR_CUDA, "absmax");
+        double yv[5], ym = 0.0;
+        CK(cudaMemcpyAsync(yv, C->ymax, sizeof(double) * C->nv, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int v = 0; v < C->nv; ++v) ym = fmax(ym, yv[v] / C->pmg_qref[v]);
+        if (!(ym > 0.0) || !isfinite(ym)) break;
+        C->pmg_gain = ym / target;
+        if (ym <= want * kMixedSlack && ym >= want / kMixedSlack) break;
+    }
     frk32_f2d_unscale(n, C->y32, C->xmax, target, Y, s);
     CKLAUNCH();
     return FR_OK;
@@ -823,18 +868,158 @@ static int check_solve_opts(const fr_ctx *C, const fr_solve_opts *o) {
     return FR_OK;
 }
 
+// --------------------------------------------------------------- initial guess
+extern "C" int mlp_train_step(fr_mlp *M, int B, const unsigned short *X, const float *T, float lr, float *loss,
+                              float *grads, void *stream);
+
+static int mlp_sizes(const fr_ctx *C, int *K0, int *O) {
+    const FrLevel &L = C->L[0];
+    *O = L.nd;
+    *K0 = ((4 * L.nd + L.np + 1) + 15) / 16 * 16;
+    return FR_OK;
+}
+
+extern "C" int fr_mlp_dims(const fr_ctx *C, int *in_dim, int *out_dim) {
+    if (!C || !in_dim || !out_dim) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    return mlp_sizes(C, in_dim, out_dim);
+}
+
+extern "C" int fr_set_mlp(fr_ctx *C, fr_mlp *M) {
+    if (!C) return fail(FR_ERR_INVALID_ARG, "NULL context");
+    if (M) {
+        int in, hid, out, K0, O;
+        frkmlp_dims(M, &in, &hid, &out);
+        mlp_sizes(C, &K0, &O);
+        if (in != K0 || out != O) return fail(FR_ERR_INVALID_ARG, "network is %d -> %d, the context needs %d -> %d", in, out, K0, O);
+    }
+    C->mlp = M;
+    C->mlp_steps = 0;
+    return FR_OK;
+}
+
+extern "C" int fr_reset_history(fr_ctx *C) {
+    if (!C) return fail(FR_ERR_INVALID_ARG, "NULL context");
+    C->nhist = 0;
+    C->ring_n = 0;
+    C->ring_head = 0;
+    C->train_cursor = 0;
+    return FR_OK;
+}
+
+static int ensure_guess_buffers(fr_ctx *C, int stages);
+
+extern "C" int fr_guess_features(fr_ctx *C, const double *qn, const double *q1, const double *q2, const double *Rn,
+                                 double dt, double c, unsigned short *X, double *scales, void *stream) {
+    if (!C || !qn || !q1 || !q2 || !Rn || !X) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    TRY(ensure_guess_buffers(C, 4));
+    cudaStream_t s = S_(stream);
+    const FrLevel &L0 = C->L[0];
+    frkmlp_var_stats(L0.nv, (long long)L0.np * L0.E, qn, q1, C->qinf_dev, C->vpart, C->sdev, s);
+    frkmlp_features(L0.E, L0.nv, L0.np, C->K0, qn, q1, q2, Rn, dt, L0.invJ, c, C->sdev, C->sdev + 5, C->qinf_dev, X,
+                    s);
+    CKLAUNCH();
+    if (scales) CK(cudaMemcpyAsync(scales, C->sdev, sizeof(double) * 10, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return FR_OK;
+}
+
+static const int kRingSteps = 6;   // training ring: samples of the last six steps
+
+static int ensure_guess_buffers(fr_ctx *C, int stages) {
+    if (C->qex) return FR_OK;
+    const FrLevel &L = C->L[0];
+    long long n = L.ndof;
+    mlp_sizes(C, &C->K0, &C->O);
+    for (int k = 0; k < 3; ++k) TRY(dalloc_t(C, &C->hist[k], n));
+    TRY(dalloc_t(C, &C->qex, n)); TRY(dalloc_t(C, &C->qcand, n));
+    TRY(dalloc_t(C, &C->Rtmp, n)); TRY(dalloc_t(C, &C->Ftmp, n)); TRY(dalloc_t(C, &C->Fex, n));
+    TRY(dalloc_t(C, &C->sdev, 16)); TRY(dalloc_t(C, &C->qinf_dev, 5)); TRY(dalloc_t(C, &C->vpart, 5 * 64 * 2));
+    CK(cudaMemcpy(C->qinf_dev, C->ph.qinf, sizeof(double) * 5, cudaMemcpyHostToDevice));
+    TRY(dalloc_t(C, &C->Xf, (size_t)L.E * C->K0));
+    TRY(dalloc_t(C, &C->Yf, (size_t)L.E * C->O));
+    TRY(dalloc_t(C, &C->Tf, (size_t)L.E * C->O));
+    C->ring_cap = kRingSteps * (stages - 1) * L.E;
+    TRY(dalloc_t(C, &C->ringX, (size_t)C->ring_cap * C->K0));
+    TRY(dalloc_t(C, &C->ringT, (size_t)C->ring_cap * C->O));
+    return FR_OK;
+}
+
+static void push_history(fr_ctx *C, const double *q, cudaStream_t s) {
+    double *t = C->hist[0];
+    C->hist[0] = C->hist[1];
+    C->hist[1] = C->hist[2];
+    C->hist[2] = t;
+    frk64_copy(C->L[0].ndof, q, C->hist[2], s);
+    if (C->nhist < 3) ++C->nhist;
+}
+
+// RMS(a_ii dt F(qc)) of a candidate stage state
+static int stage_rms(fr_ctx *C, const double *qc, const double *sv, double adt, double *rms, cudaStream_t s) {
+    long long n = C->L[0].ndof;
+    TRY(residual(C, 0, qc, C->Rtmp, s));
+    frk64_stage_F(n, qc, sv, adt, C->Rtmp, C->Ftmp, s);
+    double fn;
+    TRY(norm2(C, n, C->Ftmp, &fn, s));
+    *rms = fabs(adt) * fn / sqrt((double)n);
+    if (!isfinite(*rms)) *rms = INFINITY;
+    return FR_OK;
+}
+
+static void ring_append(fr_ctx *C, cudaStream_t s) {
+    int E = C->L[0].E;
+    for (int e0 = 0; e0 < E;) {
+        int cnt = std::min(E - e0, C->ring_cap - C->ring_head);
+        cudaMemcpyAsync(C->ringX + (size_t)C->ring_head * C->K0, C->Xf + (size_t)e0 * C->K0,
+                        sizeof(unsigned short) * (size_t)cnt * C->K0, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(C->ringT + (size_t)C->ring_head * C->O, C->Tf + (size_t)e0 * C->O,
+                        sizeof(float) * (size_t)cnt * C->O, cudaMemcpyDeviceToDevice, s);
+        C->ring_head = (C->ring_head + cnt) % C->ring_cap;
+        C->ring_n = std::min(C->ring_n + cnt, C->ring_cap);
+        e0 += cnt;
+    }
+}
+
+static int train_from_ring(fr_ctx *C, const fr_solve_opts *o, fr_step_stats *st, cudaStream_t s) {
+    if (!C->mlp || C->ring_n == 0 || o->train_iters <= 0) return FR_OK;
+    int B = std::min(o->train_batch > 0 ? o->train_batch : 4096, C->ring_n);
+    float loss = 0.f;
+    for (int it = 0; it < o->train_iters; ++it) {
+        if (C->train_cursor + B > C->ring_n) C->train_cursor = 0;
+        int rc = mlp_train_step(C->mlp, B, C->ringX + (size_t)C->train_cursor * C->K0,
+                                C->ringT + (size_t)C->train_cursor * C->O, (float)o->lr,
+                                it + 1 == o->train_iters ? &loss : nullptr, nullptr, s);
+        if (rc != FR_OK) return rc;
+        C->train_cursor += B;
+    }
+    C->mlp_steps += o->train_iters;
+    if (st) st->train_loss = loss;
+    return FR_OK;
+}
+
 extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, double *q, const fr_solve_opts *o,
                            fr_step_stats *st, void *stream) {
     if (!C || !tab || !q || !o) return fail(FR_ERR_INVALID_ARG, "NULL argument");
     if (tab->stages < 2 || tab->stages > 6 || !(dt > 0.0)) return fail(FR_ERR_INVALID_ARG, "bad tableau or dt");
     TRY(check_solve_opts(C, o));
+    if (o->guess < 0 || o->guess > 2) return fail(FR_ERR_INVALID_ARG, "guess must be 0, 1 or 2");
+    if ((o->guess == 2 || o->train_iters > 0) && !C->mlp) return fail(FR_ERR_NOT_READY, "no network attached (fr_set_mlp)");
     cudaStream_t s = S_(stream);
     int ns = tab->stages;
     TRY(stepper_alloc(C, ns + 5));
     long long n = C->L[0].ndof;
+    const FrLevel &L0 = C->L[0];
     double *qn = C->stv[0], *sv = C->stv[1], *F = C->stv[2], *Rk = C->stv[3], *dq = C->stv[4];
     double **Rs = &C->stv[5];
-    fr_step_stats loc = {0, 0, 1, 0.0};
+    fr_step_stats loc;
+    memset(&loc, 0, sizeof loc);
+    loc.converged = 1;
+    bool learn = o->guess > 0 || o->train_iters > 0;
+    if (learn) {
+        TRY(ensure_guess_buffers(C, ns));
+        if (C->nhist == 0) push_history(C, q, s);
+    }
+    bool have3 = learn && C->nhist >= 3;
+    if (have3) frkmlp_var_stats(L0.nv, (long long)L0.np * L0.E, C->hist[2], C->hist[1], C->qinf_dev, C->vpart, C->sdev, s);
     frk64_copy(n, q, qn, s);
     TRY(residual(C, 0, qn, Rs[0], s));
     double aii = tab->A[1 * ns + 1];
@@ -849,12 +1034,57 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
         TRY(pmg_setup_(C, qn, &po, s));
     }
     fr_gmres_opts go = gm_opts(o, c);
+    int nguess_stages = 0;
     for (int i = 1; i < ns; ++i) {
         double adt = tab->A[i * ns + i] * dt;
-        double coef[6];
+        double coef[6], ci = 0.0;
         for (int j = 0; j < i; ++j) coef[j] = tab->A[i * ns + j];
+        for (int j = 0; j <= i; ++j) ci += tab->A[i * ns + j];
         frk64_lincomb(n, i, coef, (const double *const *)Rs, qn, dt, sv, s);
         frk64_copy(n, qn, q, s);
+        if (have3) {
+            // candidates judged by the FP64 stage residual: q^n (the paper's guess),
+            // quadratic extrapolation in time, and the network's correction of it
+            frkmlp_extrap(n, C->hist[2], C->hist[1], C->hist[0], ci, C->qex, s);
+            frkmlp_features(L0.E, L0.nv, L0.np, C->K0, C->hist[2], C->hist[1], C->hist[0], Rs[0], dt, L0.invJ, ci,
+                            C->sdev, C->sdev + 5, C->qinf_dev, C->Xf, s);
+            if (o->guess >= 1) {
+                double r[3] = {INFINITY, INFINITY, INFINITY};
+                TRY(stage_rms(C, qn, sv, adt, &r[0], s));
+                TRY(stage_rms(C, C->qex, sv, adt, &r[1], s));
+                int best = r[1] < r[0] ? 1 : 0;
+                if (o->guess == 2 && C->mlp_steps > 0) {
+                    // the network's correction d = qnet - qex, scaled by the step beta that
+                    // minimises the linearised ||F(qex + beta d)||: F(qnet) - F(qex) = J d
+                    frk64_copy(n, C->Ftmp, C->Fex, s);
+                    if (frkmlp_forward(C->mlp, L0.E, C->Xf, C->Yf, s) != 0) return fail(FR_ERR_OOM, "network activations");
+                    frkmlp_guess(L0.E, L0.nv, L0.np, C->qex, C->sdev, C->Yf, C->qcand, s);
+                    double rnet;
+                    TRY(stage_rms(C, C->qcand, sv, adt, &rnet, s));
+                    frk64_sub(n, C->Ftmp, C->Fex, C->Ftmp, s);
+                    const double *V2[2] = {C->Fex, C->Ftmp};
+                    double ab[2];
+                    TRY(dots(C, n, 2, C->Ftmp, V2, ab, s));
+                    double beta = ab[1] > 0.0 ? -ab[0] / ab[1] : 0.0;
+                    beta = isfinite(beta) ? fmin(fmax(beta, -1.0), 2.0) : 0.0;
+                    loc.guess_beta += beta;
+                    double cf[2] = {1.0 - beta, beta};
+                    const double *Xs[2] = {C->qex, C->qcand};
+                    frk64_lincomb(n, 2, cf, Xs, nullptr, 1.0, C->qcand, s);
+                    TRY(stage_rms(C, C->qcand, sv, adt, &r[2], s));
+                    if (rnet < r[2]) {   // the linear model misjudged: keep the raw network guess
+                        frkmlp_guess(L0.E, L0.nv, L0.np, C->qex, C->sdev, C->Yf, C->qcand, s);
+                        r[2] = rnet;
+                    }
+                    if (r[2] < r[best]) best = 2;
+                }
+                for (int k = 0; k < 3; ++k) loc.guess_rms[k] += isfinite(r[k]) ? r[k] : 0.0;
+                loc.guess_pick[best]++;
+                ++nguess_stages;
+                if (best == 1) frk64_copy(n, C->qex, q, s);
+                else if (best == 2) frk64_copy(n, C->qcand, q, s);
+            }
+        }
         int conv = 0;
         double res = 0.0;
         for (int k = 0; k <= o->max_ptc; ++k) {
@@ -876,8 +1106,16 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
         if (!conv) loc.converged = 0;
         loc.final_res = res;
         frk64_copy(n, Rk, Rs[i], s);
+        if (have3 && o->train_iters > 0 && conv) {
+            frkmlp_targets(L0.E, L0.nv, L0.np, q, C->qex, C->sdev, C->Tf, s);
+            ring_append(C, s);
+        }
     }
+    for (int k = 0; k < 3 && nguess_stages; ++k) loc.guess_rms[k] /= nguess_stages;
+    if (nguess_stages) loc.guess_beta /= nguess_stages;
     frk64_lincomb(n, ns, tab->b, (const double *const *)Rs, qn, dt, q, s);
+    if (learn) push_history(C, q, s);
+    if (o->train_iters > 0) TRY(train_from_ring(C, o, &loc, s));
     CKLAUNCH();
     CK(cudaStreamSynchronize(s));
     if (st) *st = loc;
@@ -895,7 +1133,9 @@ extern "C" int row_step(fr_ctx *C, const fr_row_tableau *tab, double dt, double 
     long long n = C->L[0].ndof;
     double *qn = C->stv[0], *Rn = C->stv[1], *qi = C->stv[2], *rhs = C->stv[3], *Ri = C->stv[4];
     double **Y = &C->stv[5];
-    fr_step_stats loc = {0, 0, 1, 0.0};
+    fr_step_stats loc;
+    memset(&loc, 0, sizeof loc);
+    loc.converged = 1;
     frk64_copy(n, q, qn, s);
     TRY(residual(C, 0, qn, Rn, s));
     double c = 1.0 / (tab->gamma * dt);
@@ -940,7 +1180,10 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
     TRY(stepper_alloc(C, 2));
     long long n = C->L[0].ndof;
     double *R = C->stv[0], *dq = C->stv[1];
-    fr_step_stats loc = {0, 0, 0, 0.0};
+    fr_step_stats loc;
+    memset(&loc, 0, sizeof loc);
+    loc.prec_switch_it = -1;
+    int prec = o->precision;
     TRY(residual(C, 0, q, R, s));
     double r0, rk, dtau = dtau_init;
     TRY(norm2(C, n, R, &r0, s));
@@ -955,7 +1198,7 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
             for (int l = 0; l < 4; ++l) po.nsmooth[l] = o->nsmooth[l];
             po.c = c;
             po.inv_dtau_star = o->inv_dtau_star < 0 ? c : o->inv_dtau_star;
-            po.precision = o->precision;
+            po.precision = prec;
             TRY(pmg_setup_(C, q, &po, s));
         }
         fr_gmres_opts go = gm_opts(o, c);
@@ -967,6 +1210,13 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
         double rn;
         TRY(norm2(C, n, R, &rn, s));
         if (!isfinite(rn)) return fail(FR_ERR_NONFINITE, "non-finite residual at pseudo step %d", k);
+        // FP32 preconditioner stalled (FGMRES used every iteration, residual barely moved):
+        // with 1/dtau -> 0 the element blocks grow too ill-conditioned for FP32 LU, so
+        // the rest of the pseudo-time march takes the FP64 cycle
+        if (prec == 1 && o->use_pmg && gs.iters >= o->maxit_gmres && rn > 0.5 * rk) {
+            prec = 0;
+            loc.prec_switch_it = k + 1;
+        }
         dtau = fmin(dtau * (rk / rn), dtau_max);
         rk = rn;
         loc.n_ptc++;
