@@ -278,6 +278,36 @@ int row_step(fr_ctx *ctx, const fr_row_tableau *tab, double dt, double *q, const
 int ptc_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
                const fr_solve_opts *opts, fr_step_stats *stats, double *hist, void *stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent problems advanced together (not in the paper: a throughput mode).
+ * Problems sharing the dimension, geometry degree and p-levels are solved on one merged
+ * mesh per group, so each kernel of the step runs once per group; Newton and FGMRES stay
+ * per problem (segmented norms and inner products, own Hessenberg matrix, stopping test
+ * and restarts; a converged problem is masked out).  Every problem of a batch takes the
+ * same dt, solver options and physics (an ensemble advancing in lockstep); a group with
+ * fewer p-levels than opts->nlevels uses all it has.  The Arnoldi
+ * step of a group runs as a CUDA graph captured once per Krylov index and operator
+ * parameters (fr_batch_set_graphs(b, 0) launches the kernels one by one instead).  With
+ * precision 1 the FP32 cycle keeps its scale on the device: each call's measured gain
+ * sets the next call's input scale (no repeat of a call).  The work runs on the batch's
+ * own stream, ordered after and before the caller's stream. */
+typedef struct fr_batch fr_batch;
+/* meshes: host array of nprob descriptions (copied); physics shared by all problems */
+int fr_batch_create(fr_batch **out, int nprob, const fr_mesh_desc *meshes, const fr_physics *phys);
+int fr_batch_destroy(fr_batch *batch);
+/* host outs (any may be NULL): number of groups, group of each problem [nprob], first
+ * element of each problem in its group's merged mesh [nprob] */
+int fr_batch_info(const fr_batch *batch, int *ngroups, int *group_of, int *elem_offset);
+int fr_batch_set_graphs(fr_batch *batch, int on);
+/* R(q_k) for every problem: q, R host arrays of nprob device pointers ([nv][Np][E_k] each) */
+int fr_batch_residual(fr_batch *batch, double *const *q, double *const *R, void *stream);
+/* one ESDIRK step (as esdirk_step, guess 0, kdim <= 62) of every problem: q host array of
+ * nprob device pointers, updated in place; stats host [nprob] (may be NULL).  Returns
+ * FR_ERR_NOT_CONVERGED if any problem missed the Newton tolerance (all states are still
+ * advanced). */
+int fr_batch_esdirk_step(fr_batch *batch, const fr_esdirk_tableau *tab, double dt, double *const *q,
+                         const fr_solve_opts *opts, fr_step_stats *stats, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,8 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_last_error", "fr_kernel_launches", "fr
            "fr_elem_blocks", "fr_block_factor", "fr_block_solve", "fr_restrict", "fr_prolong", "pmg_setup",
            "pmg_precondition", "gmres_solve", "esdirk_step", "row_step", "ptc_steady",
            "mlp_create", "mlp_destroy", "mlp_get_params", "mlp_forward", "mlp_train_step", "fr_mlp_dims",
-           "fr_set_mlp", "fr_reset_history", "fr_guess_features"]
+           "fr_set_mlp", "fr_reset_history", "fr_guess_features", "fr_batch_create", "fr_batch_destroy",
+           "fr_batch_info", "fr_batch_set_graphs", "fr_batch_residual", "fr_batch_esdirk_step"]
 
 
 class MeshDesc(C.Structure):
@@ -116,6 +117,13 @@ def load(path: str = LIB_PATH):
         "fr_set_mlp": ([VP, VP], C.c_int),
         "fr_reset_history": ([VP], C.c_int),
         "fr_guess_features": ([VP, VP, VP, VP, VP, C.c_double, C.c_double, VP, PD, VP], C.c_int),
+        "fr_batch_create": ([C.POINTER(VP), C.c_int, C.POINTER(MeshDesc), C.POINTER(Physics)], C.c_int),
+        "fr_batch_destroy": ([VP], C.c_int),
+        "fr_batch_info": ([VP, PI, PI, PI], C.c_int),
+        "fr_batch_set_graphs": ([VP, C.c_int], C.c_int),
+        "fr_batch_residual": ([VP, C.POINTER(VP), C.POINTER(VP), VP], C.c_int),
+        "fr_batch_esdirk_step": ([VP, C.POINTER(EsdirkTableau), C.c_double, C.POINTER(VP), C.POINTER(SolveOpts),
+                                  C.POINTER(StepStats), VP], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

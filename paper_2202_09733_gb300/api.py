@@ -306,3 +306,84 @@ def fr_guess_features(ctx, qn, q1, q2, Rn, dt, c, stream=None):
 
 def fr_reset_history(ctx):
     N.check(N.load().fr_reset_history(ctx.handle), "fr_reset_history")
+
+
+class Batch:
+    """Many independent problems advanced together (libfrpmg fr_batch_*).  problems: list of
+    (mesh dict, levels); physics shared."""
+
+    def __init__(self, problems, phys):
+        lib = N.load()
+        torch.cuda.init()
+        self._keep = []
+        descs = (N.MeshDesc * len(problems))()
+        self.shapes = []
+        for k, (mesh, levels) in enumerate(problems):
+            g = np.ascontiguousarray(mesh["gnodes"], dtype=np.float64)
+            f = np.ascontiguousarray(mesh["faces"], dtype=np.int32)
+            pl = np.ascontiguousarray(levels, dtype=np.int32)
+            self._keep += [g, f, pl]
+            descs[k] = N.MeshDesc(mesh["d"], mesh["E"], mesh["qg"], g.ctypes.data_as(N.PD), len(f),
+                                  f.ctypes.data_as(N.PI), len(pl), pl.ctypes.data_as(N.PI))
+            np_ = (levels[0] + 1) ** mesh["d"]
+            self.shapes.append((mesh["d"] + 2, np_, mesh["E"]))
+        ph = N.Physics()
+        ph.gamma, ph.prandtl, ph.mu, ph.eta = phys.gamma, phys.Pr, phys.mu, phys.eta
+        for v, x in enumerate(phys.qinf):
+            ph.qinf[v] = float(x)
+        h = C.c_void_p()
+        N.check(lib.fr_batch_create(C.byref(h), len(problems), descs, C.byref(ph)), "fr_batch_create")
+        self.handle = h
+        self.nprob = len(problems)
+
+    def info(self):
+        ng = C.c_int()
+        grp = np.zeros(self.nprob, dtype=np.int32)
+        off = np.zeros(self.nprob, dtype=np.int32)
+        N.check(N.load().fr_batch_info(self.handle, C.byref(ng), grp.ctypes.data_as(N.PI), off.ctypes.data_as(N.PI)),
+                "fr_batch_info")
+        return ng.value, grp, off
+
+    def set_graphs(self, on: bool):
+        N.check(N.load().fr_batch_set_graphs(self.handle, int(bool(on))), "fr_batch_set_graphs")
+
+    def _ptrs(self, qs):
+        if len(qs) != self.nprob:
+            raise ValueError(f"expected {self.nprob} states")
+        arr = (C.c_void_p * self.nprob)()
+        for k, (t, shp) in enumerate(zip(qs, self.shapes)):
+            if tuple(t.shape) != shp:
+                raise ValueError(f"state {k} has shape {tuple(t.shape)}, expected {shp}")
+            arr[k] = _dev(t).value
+        return arr
+
+    def residual(self, qs, Rs=None, stream=None):
+        if Rs is None:
+            Rs = [torch.empty_like(q) for q in qs]
+        N.check(N.load().fr_batch_residual(self.handle, self._ptrs(qs), self._ptrs(Rs), _stream(stream)),
+                "fr_batch_residual")
+        return Rs
+
+    def esdirk_step(self, A, b, dt, qs, opts, stream=None, allow_not_converged=True):
+        A = np.asarray(A, dtype=np.float64)
+        s = len(b)
+        tab = N.EsdirkTableau()
+        tab.stages = s
+        for i in range(s):
+            tab.b[i] = float(b[i])
+            for j in range(s):
+                tab.A[i * s + j] = float(A[i, j])
+        st = (N.StepStats * self.nprob)()
+        rc = N.load().fr_batch_esdirk_step(self.handle, C.byref(tab), float(dt), self._ptrs(qs), C.byref(opts), st,
+                                           _stream(stream))
+        N.check(rc, "fr_batch_esdirk_step", allow=(-4,) if allow_not_converged else ())
+        return [_stats(x) for x in st]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                N.load().fr_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = None

@@ -84,6 +84,28 @@ int frk32_absmax_var_f(int nv, long long per, const float *x, double *out_dev, c
 int frk32_absmax(long long n, const double *x, double *out_dev, cudaStream_t s);
 void frk32_f2d_unscale(long long n, const float *x, const double *xmax_dev, double target, double *y, cudaStream_t s);
 
+void frk32_d2f_scaled_dev(long long n, const double *x, const double *xmax_dev, const double *target_dev, float *y,
+                          cudaStream_t s);
+void frk32_f2d_unscale_dev(long long n, const float *x, const double *xmax_dev, const double *target_dev, double *y,
+                           cudaStream_t s);
+void frk32_next_target(int nv, const double *ymax_dev, const double *qref_dev, double want, double *target_dev,
+                       cudaStream_t s);
+
+// segmented vector kernels of the batched solver (batch_kernels.cu)
+unsigned long long frkb_launch_count();
+void frkb_add_launches(long long k);
+int frkb_segdots(int rows, int E, int nitems, const int4 *items, int nprob, const int *item_off, const double *w,
+                 int m, const double *const *V, double *partial, double *out, int ld, cudaStream_t s);
+void frkb_seg_invnorm(int nprob, const double *sq, int ld, const double *mask, double *nrm, double *inv,
+                      cudaStream_t s);
+void frkb_seg_scale(long long n, int E, const int *ep, const double *f, const double *x, double *y, cudaStream_t s);
+void frkb_seg_multi_axpy(long long n, int E, const int *ep, int m, const double *h, int ld, const double *const *V,
+                         double *w, cudaStream_t s);
+void frkb_seg_update_x(long long n, int E, const int *ep, int m, const double *y, int ld, const double *const *Z,
+                       double *x, cudaStream_t s);
+void frkb_gather(int rows, int Ei, const double *qi, double *Q, int E, int off, cudaStream_t s);
+void frkb_scatter(int rows, int Ei, const double *Q, int E, int off, double *qi, cudaStream_t s);
+
 // FP32 element blocks by forward-mode differentiation of the residual (kernelsad.cu)
 unsigned long long frkad_launch_count();
 int frkad_upload_tables(const FrTabH *tabs);

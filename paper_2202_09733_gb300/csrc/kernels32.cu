@@ -69,3 +69,36 @@ __global__ void k_f2d_unscale(long long n, const float *x, const double *xmax, d
 void frk32_f2d_unscale(long long n, const float *x, const double *xmax_dev, double target, double *y, cudaStream_t s) {
     CNT(); k_f2d_unscale<<<nblk(n), 256, 0, s>>>(n, x, xmax_dev, target, y);
 }
+
+// Scaling of the FP32 cycle with the target held on the device (no host round trip):
+// x32 = X * target / max|X|, Y = y32 * max|X| / target, and after the cycle the target of
+// the next application from the measured gain: ym = max_v max|y32_v| / qref_v,
+// target' = want * target / ym (unchanged if ym is 0 or not finite).
+__global__ void k_d2f_scaled_dev(long long n, const double *x, const double *xmax, const double *target, float *y) {
+    double m = *xmax;
+    double s = m > 0.0 ? *target / m : 1.0;
+    GRID_STRIDE(i, n) y[i] = (float)(x[i] * s);
+}
+__global__ void k_f2d_unscale_dev(long long n, const float *x, const double *xmax, const double *target, double *y) {
+    double m = *xmax;
+    double inv_s = m > 0.0 ? m / *target : 1.0;
+    GRID_STRIDE(i, n) y[i] = (double)x[i] * inv_s;
+}
+__global__ void k_next_target(int nv, const double *ymax, const double *qref, double want, double *target) {
+    if (threadIdx.x != 0) return;
+    double ym = 0.0;
+    for (int v = 0; v < nv; ++v) ym = fmax(ym, ymax[v] / qref[v]);
+    if (ym > 0.0 && ym < INFINITY) *target = want * *target / ym;
+}
+void frk32_d2f_scaled_dev(long long n, const double *x, const double *xmax_dev, const double *target_dev, float *y,
+                          cudaStream_t s) {
+    CNT(); k_d2f_scaled_dev<<<nblk(n), 256, 0, s>>>(n, x, xmax_dev, target_dev, y);
+}
+void frk32_f2d_unscale_dev(long long n, const float *x, const double *xmax_dev, const double *target_dev, double *y,
+                           cudaStream_t s) {
+    CNT(); k_f2d_unscale_dev<<<nblk(n), 256, 0, s>>>(n, x, xmax_dev, target_dev, y);
+}
+void frk32_next_target(int nv, const double *ymax_dev, const double *qref_dev, double want, double *target_dev,
+                       cudaStream_t s) {
+    CNT(); k_next_target<<<1, 32, 0, s>>>(nv, ymax_dev, qref_dev, want, target_dev);
+}

@@ -121,8 +121,12 @@ static cudaStream_t S_(void *s) { return (cudaStream_t)s; }
 
 extern "C" const char *fr_last_error(void) { return g_err; }
 
+static unsigned long long g_graph_kernels = 0;    // kernels run by CUDA graph replays
+static unsigned long long g_capture_kernels = 0;  // launch-counter increments made while capturing graphs
+
 extern "C" unsigned long long fr_kernel_launches(void) {
-    return frk64_launch_count() + frk32_launch_count() + frkad_launch_count() + frkmlp_launch_count();
+    return frk64_launch_count() + frk32_launch_count() + frkad_launch_count() + frkmlp_launch_count() +
+           frkb_launch_count() - g_capture_kernels + g_graph_kernels;
 }
 
 // ---------------------------------------------------------------- context set-up
@@ -1227,3 +1231,5 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
     if (st) *st = loc;
     return loc.converged ? FR_OK : fail(FR_ERR_NOT_CONVERGED, "steady PTC stopped at %g relative residual", loc.final_res);
 }
+
+#include "batch_impl.h"

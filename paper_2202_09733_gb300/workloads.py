@@ -367,3 +367,27 @@ def cylinder_unsteady(nr: int = 96, nt: int = 192, p: int = 3, levels=None, mach
     phys = Physics(mu=1.0 / re, qinf=qinf)
     lv = levels if levels is not None else [p, p - 1]
     return Workload("cylinder_unsteady", mesh, phys, lv, q0, dt=cfl * explicit_dt(mesh, p, q0))
+
+
+def vortex_batch(nprob: int = 256, nmin: int = 4, nmax: int = 48, pmin: int = 1, pmax: int = 4, seed: int = 3,
+                 re: float = 100.0, mach: float = 0.5, L: float = 10.0, cfl: float = 20.0):
+    """Independent periodic [0, L]^2 isentropic-vortex problems of uneven size and degree:
+    problem k has n_k x n_k quads with n_k ~ U{nmin..nmax}, p_k ~ U{pmin..pmax}, levels
+    p{p-(p-1)} (a single level at p = 1), vortex centre (L/2, L/2) + U(-1, 1)^2 and strength
+    U(4, 6), all seeded.  One dt for the whole batch: cfl x the smallest explicit limit.
+    Returns (problems [(mesh, levels)], states, physics, dt)."""
+    rng = np.random.default_rng(seed)
+    problems, states, dts = [], [], []
+    for _ in range(nprob):
+        n = int(rng.integers(nmin, nmax + 1))
+        p = int(rng.integers(pmin, pmax + 1))
+        xc, yc = L / 2 + rng.uniform(-1, 1, size=2)
+        beta = rng.uniform(4.0, 6.0)
+        mesh = box2d(n, n, L, L, qg=2)
+        X = solution_point_coords(mesh, p)
+        q0 = to_state(isentropic_vortex(X, xc, yc, beta, mach, L, L))
+        problems.append((mesh, [p, p - 1] if p > 1 else [1]))
+        states.append(q0)
+        dts.append(explicit_dt(mesh, p, q0))
+    phys = Physics(mu=1.0 / re if re else 0.0, qinf=freestream(2, mach))
+    return problems, states, phys, cfl * min(dts)
