@@ -278,6 +278,27 @@ int row_step(fr_ctx *ctx, const fr_row_tableau *tab, double dt, double *q, const
 int ptc_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
                const fr_solve_opts *opts, fr_step_stats *stats, double *hist, void *stream);
 
+/* ---------------------------------------------------------------- autotuner
+ * Launch shapes (not in the paper; no result bit depends on them): the CTA size (elements
+ * per CTA tile, 64/128/256) of each of the 8 kernels of the residual, per level and
+ * precision, and the columns in flight G (2/4/8) of the block solve.  fr_autotune times
+ * the candidates with CUDA events on the context's own levels (reps launches each after
+ * a warm-up; a coordinate-descent pass over the residual kernels, then G on the level's
+ * factored blocks if pmg_setup has run in that precision) and keeps the fastest.  flags:
+ * bit 0 FP64 levels, bit 1 FP32 levels, bit 2 re-tune even if cached.  Results are kept
+ * in a process-wide cache keyed by (device name, d, p, precision, floor(log2 E)); new
+ * contexts pick cached shapes up.  report (host, may be NULL): one line per level.
+ * Uses the legacy default stream and synchronises the device. */
+int fr_autotune(fr_ctx *ctx, int flags, int reps, char *report, int report_len);
+/* tiles[9]: the 8 CTA sizes (0 = default 128; else a multiple of 32 in 32..256) and G
+ * (0 = default, 2, 4 or 8) of level `level` in precision 0 (FP64) or 1 (FP32) */
+int fr_get_tiles(const fr_ctx *ctx, int level, int precision, int *tiles);
+int fr_set_tiles(fr_ctx *ctx, int level, int precision, const int *tiles);
+/* the cache as a text file: one line "device d p precision log2E tile0..tile7 G" per key
+ * (load skips malformed lines and out-of-range values) */
+int fr_autotune_save(const char *path);
+int fr_autotune_load(const char *path);
+
 /* ------------------------------------------------------------------ batches
  * Many independent problems advanced together (not in the paper: a throughput mode).
  * Problems sharing the dimension, geometry degree and p-levels are solved on one merged
@@ -307,6 +328,8 @@ int fr_batch_residual(fr_batch *batch, double *const *q, double *const *R, void 
  * advanced). */
 int fr_batch_esdirk_step(fr_batch *batch, const fr_esdirk_tableau *tab, double dt, double *const *q,
                          const fr_solve_opts *opts, fr_step_stats *stats, void *stream);
+/* fr_autotune on every group of the batch (drops the captured graphs) */
+int fr_batch_autotune(fr_batch *batch, int flags, int reps, char *report, int report_len);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,8 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_last_error", "fr_kernel_launches", "fr
            "pmg_precondition", "gmres_solve", "esdirk_step", "row_step", "ptc_steady",
            "mlp_create", "mlp_destroy", "mlp_get_params", "mlp_forward", "mlp_train_step", "fr_mlp_dims",
            "fr_set_mlp", "fr_reset_history", "fr_guess_features", "fr_batch_create", "fr_batch_destroy",
-           "fr_batch_info", "fr_batch_set_graphs", "fr_batch_residual", "fr_batch_esdirk_step"]
+           "fr_batch_info", "fr_batch_set_graphs", "fr_batch_residual", "fr_batch_esdirk_step", "fr_autotune",
+           "fr_get_tiles", "fr_set_tiles", "fr_autotune_save", "fr_autotune_load", "fr_batch_autotune"]
 
 
 class MeshDesc(C.Structure):
@@ -124,6 +125,12 @@ def load(path: str = LIB_PATH):
         "fr_batch_residual": ([VP, C.POINTER(VP), C.POINTER(VP), VP], C.c_int),
         "fr_batch_esdirk_step": ([VP, C.POINTER(EsdirkTableau), C.c_double, C.POINTER(VP), C.POINTER(SolveOpts),
                                   C.POINTER(StepStats), VP], C.c_int),
+        "fr_autotune": ([VP, C.c_int, C.c_int, C.c_char_p, C.c_int], C.c_int),
+        "fr_get_tiles": ([VP, C.c_int, C.c_int, PI], C.c_int),
+        "fr_set_tiles": ([VP, C.c_int, C.c_int, PI], C.c_int),
+        "fr_autotune_save": ([C.c_char_p], C.c_int),
+        "fr_autotune_load": ([C.c_char_p], C.c_int),
+        "fr_batch_autotune": ([VP, C.c_int, C.c_int, C.c_char_p, C.c_int], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -304,6 +304,35 @@ def fr_guess_features(ctx, qn, q1, q2, Rn, dt, c, stream=None):
     return X, sc[:ctx.nv], sc[5:5 + ctx.nv]
 
 
+def fr_autotune(ctx, fp64=True, fp32=False, retune=False, reps=5):
+    """Tune the launch shapes of the context's levels; returns the report lines."""
+    buf = C.create_string_buffer(8192)
+    flags = (1 if fp64 else 0) | (2 if fp32 else 0) | (4 if retune else 0)
+    N.check(N.load().fr_autotune(ctx.handle, flags, int(reps), buf, len(buf)), "fr_autotune")
+    return buf.value.decode().splitlines()
+
+
+def fr_get_tiles(ctx, level, precision=0):
+    t = np.zeros(9, dtype=np.int32)
+    N.check(N.load().fr_get_tiles(ctx.handle, int(level), int(precision), t.ctypes.data_as(N.PI)), "fr_get_tiles")
+    return [int(x) for x in t]
+
+
+def fr_set_tiles(ctx, level, tiles, precision=0):
+    t = np.ascontiguousarray(tiles, dtype=np.int32)
+    if t.size != 9:
+        raise ValueError("tiles: 8 CTA sizes and the solve's G")
+    N.check(N.load().fr_set_tiles(ctx.handle, int(level), int(precision), t.ctypes.data_as(N.PI)), "fr_set_tiles")
+
+
+def fr_autotune_save(path):
+    N.check(N.load().fr_autotune_save(str(path).encode()), "fr_autotune_save")
+
+
+def fr_autotune_load(path):
+    N.check(N.load().fr_autotune_load(str(path).encode()), "fr_autotune_load")
+
+
 def fr_reset_history(ctx):
     N.check(N.load().fr_reset_history(ctx.handle), "fr_reset_history")
 
@@ -343,6 +372,12 @@ class Batch:
         N.check(N.load().fr_batch_info(self.handle, C.byref(ng), grp.ctypes.data_as(N.PI), off.ctypes.data_as(N.PI)),
                 "fr_batch_info")
         return ng.value, grp, off
+
+    def autotune(self, fp64=True, fp32=False, retune=False, reps=5):
+        buf = C.create_string_buffer(16384)
+        flags = (1 if fp64 else 0) | (2 if fp32 else 0) | (4 if retune else 0)
+        N.check(N.load().fr_batch_autotune(self.handle, flags, int(reps), buf, len(buf)), "fr_batch_autotune")
+        return buf.value.decode().splitlines()
 
     def set_graphs(self, on: bool):
         N.check(N.load().fr_batch_set_graphs(self.handle, int(bool(on))), "fr_batch_set_graphs")

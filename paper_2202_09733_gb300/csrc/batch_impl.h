@@ -593,3 +593,14 @@ extern "C" int fr_batch_residual(fr_batch *B, double *const *q, double *const *R
     CK(cudaStreamWaitEvent(us, B->ev, 0));
     return FR_OK;
 }
+
+extern "C" int fr_batch_autotune(fr_batch *B, int flags, int reps, char *report, int report_len) {
+    if (!B) return fail(FR_ERR_INVALID_ARG, "NULL batch");
+    if (report && report_len > 0) report[0] = 0;
+    for (auto &g : B->G) {
+        size_t u = report ? strlen(report) : 0;
+        TRY(fr_autotune(g.C, flags, reps, report ? report + u : nullptr, report ? report_len - (int)u : 0));
+        batch_free_graphs(g);   // captured graphs hold the old launch shapes
+    }
+    return FR_OK;
+}

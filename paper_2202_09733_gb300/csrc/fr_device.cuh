@@ -211,7 +211,7 @@ __device__ const FrTab<T> &frtab(int p);
 
 // stage 1: qf[v][k][e] = sum_m l_side[m] q[v][line(k, m)][e]
 template <int D, int P, typename T>
-__global__ void __launch_bounds__(128) k_interp(const T *__restrict__ q, T *__restrict__ qf, int E) {
+__global__ void __launch_bounds__(256) k_interp(const T *__restrict__ q, T *__restrict__ qf, int E) {
     using S = Sh<D, P>;
     constexpr int N = S::n;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(128) k_interp(const T *__restrict__ q, T *__re
 
 // stage 2: common solution, jumps dq = qs - q_side on both sides
 template <int D, int P, typename T>
-__global__ void __launch_bounds__(128) k_pair_common(const int4 *__restrict__ pairs, const int *__restrict__ bcs,
+__global__ void __launch_bounds__(256) k_pair_common(const int4 *__restrict__ pairs, const int *__restrict__ bcs,
                                                      int npairs, const T *__restrict__ qf, T *__restrict__ dq, int E,
                                                      FrPhys<typename FrBase<T>::type> ph) {
     using S = Sh<D, P>;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(128) k_pair_common(const int4 *__restrict__ pa
 
 // stage 3a: corrected gradient at solution points
 template <int D, int P, typename T>
-__global__ void __launch_bounds__(128) k_grad_sp(const T *__restrict__ q, const T *__restrict__ dq,
+__global__ void __launch_bounds__(256) k_grad_sp(const T *__restrict__ q, const T *__restrict__ dq,
                                                  const typename FrBase<T>::type *__restrict__ G, T *__restrict__ Q,
                                                  int E) {
     using S = Sh<D, P>;
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(128) k_grad_sp(const T *__restrict__ q, const 
 
 // stage 3b: face gradient traces (uncorrected) with the BR2 lifting of the face's own jump
 template <int D, int P, typename T>
-__global__ void __launch_bounds__(128) k_grad_fp(const T *__restrict__ q, const T *__restrict__ qf,
+__global__ void __launch_bounds__(256) k_grad_fp(const T *__restrict__ q, const T *__restrict__ qf,
                                                  const T *__restrict__ dq, const typename FrBase<T>::type *__restrict__ Gf,
                                                  T *__restrict__ Qf, int E, typename FrBase<T>::type etagL,
                                                  typename FrBase<T>::type etagR) {
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(128) k_grad_fp(const T *__restrict__ q, const 
 
 // stage 4: common normal flux Rusanov(qL, qR, n) - f_v(qs, Qs) . n on both sides
 template <int D, int P, typename T>
-__global__ void __launch_bounds__(128) k_pair_flux(const int4 *__restrict__ pairs, const int *__restrict__ bcs,
+__global__ void __launch_bounds__(256) k_pair_flux(const int4 *__restrict__ pairs, const int *__restrict__ bcs,
                                                    int npairs, const T *__restrict__ qf, const T *__restrict__ Qf,
                                                    const typename FrBase<T>::type *__restrict__ Sf, T *__restrict__ fn,
                                                    int E, FrPhys<typename FrBase<T>::type> ph) {
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(128) k_pair_flux(const int4 *__restrict__ pair
 
 // stage 5a: transformed volume flux Ft[dd][v][i][e] = sum_c S[dd][c] (f_inv - f_visc)_c
 template <int D, int P, typename T>
-__global__ void __launch_bounds__(128) k_vflux(const T *__restrict__ q, const T *__restrict__ Q,
+__global__ void __launch_bounds__(256) k_vflux(const T *__restrict__ q, const T *__restrict__ Q,
                                                const typename FrBase<T>::type *__restrict__ Sm, T *__restrict__ Ft, int E,
                                                FrPhys<typename FrBase<T>::type> ph) {
     using S = Sh<D, P>;
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(128) k_vflux(const T *__restrict__ q, const T 
 
 // stage 5b: transformed discontinuous flux at the face points (normal component)
 template <int D, int P, typename T>
-__global__ void __launch_bounds__(128) k_face_ft(const T *__restrict__ Ft, T *__restrict__ Ftf, int E) {
+__global__ void __launch_bounds__(256) k_face_ft(const T *__restrict__ Ft, T *__restrict__ Ftf, int E) {
     using S = Sh<D, P>;
     constexpr int N = S::n;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(128) k_face_ft(const T *__restrict__ Ft, T *__
 
 // stage 5c: divergence with FR corrections, R = -(div * invJ)
 template <int D, int P, typename T>
-__global__ void __launch_bounds__(128) k_div(const T *__restrict__ Ft, const T *__restrict__ Ftf,
+__global__ void __launch_bounds__(256) k_div(const T *__restrict__ Ft, const T *__restrict__ Ftf,
                                              const T *__restrict__ fn, const typename FrBase<T>::type *__restrict__ invJ,
                                              T *__restrict__ R, int E) {
     using S = Sh<D, P>;

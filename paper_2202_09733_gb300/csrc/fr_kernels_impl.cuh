@@ -52,15 +52,19 @@ static FrPhys<FRT> to_phys(const FrPhysH &h, const FrLevelT<FRT> &L) {
 template <int D, int P>
 static void residual_t(const FrLevelT<FRT> &L, const FrPhys<FRT> &ph, const FRT *q, FRT *R, cudaStream_t s) {
     using S = Sh<D, P>;
-    const int E = L.E, gx = (E + 127) / 128, gp = (L.npairs + 127) / 128;
-    CNT(); k_interp<D, P, FRT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, E);
-    CNT(); k_pair_common<D, P, FRT><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.dq, E, ph);
-    CNT(); k_grad_sp<D, P, FRT><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(q, L.dq, L.G, L.Q, E);
-    CNT(); k_grad_fp<D, P, FRT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
-    CNT(); k_pair_flux<D, P, FRT><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.Qf, L.Sf, L.fn, E, ph);
-    CNT(); k_vflux<D, P, FRT><<<dim3(gx, S::np), 128, 0, s>>>(q, L.Q, L.S, L.Ft, E, ph);
-    CNT(); k_face_ft<D, P, FRT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(L.Ft, L.Ftf, E);
-    CNT(); k_div<D, P, FRT><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
+    const int E = L.E;
+    int b[8];
+    for (int k = 0; k < 8; ++k) b[k] = L.tile[k] > 0 ? L.tile[k] : 128;
+    auto gx = [&](int k) { return (E + b[k] - 1) / b[k]; };
+    auto gp = [&](int k) { return (L.npairs + b[k] - 1) / b[k]; };
+    CNT(); k_interp<D, P, FRT><<<dim3(gx(0), S::nv * S::nfp), b[0], 0, s>>>(q, L.qf, E);
+    CNT(); k_pair_common<D, P, FRT><<<gp(1), b[1], 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.dq, E, ph);
+    CNT(); k_grad_sp<D, P, FRT><<<dim3(gx(2), S::nv * S::np), b[2], 0, s>>>(q, L.dq, L.G, L.Q, E);
+    CNT(); k_grad_fp<D, P, FRT><<<dim3(gx(3), S::nv * S::nfp), b[3], 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
+    CNT(); k_pair_flux<D, P, FRT><<<gp(4), b[4], 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.Qf, L.Sf, L.fn, E, ph);
+    CNT(); k_vflux<D, P, FRT><<<dim3(gx(5), S::np), b[5], 0, s>>>(q, L.Q, L.S, L.Ft, E, ph);
+    CNT(); k_face_ft<D, P, FRT><<<dim3(gx(6), S::nv * S::nfp), b[6], 0, s>>>(L.Ft, L.Ftf, E);
+    CNT(); k_div<D, P, FRT><<<dim3(gx(7), S::nv * S::np), b[7], 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
 }
 
 int FRK(residual)(const FrLevelT<FRT> &L, const FrPhysH &h, const FRT *q, FRT *R, cudaStream_t s) {
@@ -469,24 +473,31 @@ __global__ void __launch_bounds__(128) k_lu_solve(const FRT *__restrict__ M, con
     }
 }
 
+// G (columns in flight) is a launch-shape choice: 2, 4 or 8 where G x NR <= 40 registers
+// of column data, else the largest allowed; every G gives the same result bits
+template <int NR>
+static int lu_solve_nr(int g, int grid, const FRT *M, const int *perm, FRT *x, int nd, int E, cudaStream_t s) {
+    if (g >= 8 && 8 * NR <= 40) { CNT(); k_lu_solve<NR, 8><<<grid, 128, 0, s>>>(M, perm, x, nd, E); return 8; }
+    if (g >= 4 && 4 * NR <= 40) { CNT(); k_lu_solve<NR, 4><<<grid, 128, 0, s>>>(M, perm, x, nd, E); return 4; }
+    CNT(); k_lu_solve<NR, 2><<<grid, 128, 0, s>>>(M, perm, x, nd, E);
+    return 2;
+}
+
 int FRK(lu_solve)(const FrLevelT<FRT> &L, const FRT *M, const int *perm, FRT *x, cudaStream_t s) {
     int nr = (L.nd + 31) / 32;
     int grid = (L.E * 32 + 127) / 128;
+    // default G: the choice measured best before tuning existed
+    int g = L.lu_g > 0 ? L.lu_g : (nr <= 2 ? 8 : nr <= 5 ? 4 : (nr == 10 && sizeof(FRT) == 4) ? 4 : 2);
     switch (nr) {
-        case 1: { CNT(); k_lu_solve<1, 8><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
-        case 2: { CNT(); k_lu_solve<2, 8><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
-        case 3: { CNT(); k_lu_solve<3, 4><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
-        case 4: { CNT(); k_lu_solve<4, 4><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
-        case 5: { CNT(); k_lu_solve<5, 4><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
-        case 6: { CNT(); k_lu_solve<6, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
-        case 7: { CNT(); k_lu_solve<7, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
-        case 8: { CNT(); k_lu_solve<8, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E); break; }
-        case 10: {
-            CNT();
-            if (sizeof(FRT) == 4) k_lu_solve<10, 4><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E);
-            else k_lu_solve<10, 2><<<grid, 128, 0, s>>>(M, perm, x, L.nd, L.E);
-            break;
-        }
+        case 1: lu_solve_nr<1>(g, grid, M, perm, x, L.nd, L.E, s); break;
+        case 2: lu_solve_nr<2>(g, grid, M, perm, x, L.nd, L.E, s); break;
+        case 3: lu_solve_nr<3>(g, grid, M, perm, x, L.nd, L.E, s); break;
+        case 4: lu_solve_nr<4>(g, grid, M, perm, x, L.nd, L.E, s); break;
+        case 5: lu_solve_nr<5>(g, grid, M, perm, x, L.nd, L.E, s); break;
+        case 6: lu_solve_nr<6>(g, grid, M, perm, x, L.nd, L.E, s); break;
+        case 7: lu_solve_nr<7>(g, grid, M, perm, x, L.nd, L.E, s); break;
+        case 8: lu_solve_nr<8>(g, grid, M, perm, x, L.nd, L.E, s); break;
+        case 10: lu_solve_nr<10>(g, grid, M, perm, x, L.nd, L.E, s); break;
         default: return -1;
     }
     return 0;

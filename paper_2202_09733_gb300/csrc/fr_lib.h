@@ -20,6 +20,10 @@ struct FrLevelT {
     // residual workspace
     T *qf, *dq, *Q, *Qf, *fn, *Ft, *Ftf;
     double etagL, etagR;
+    // launch shapes (0 = default): CTA size of the 8 residual kernels, columns in flight
+    // of the block solve
+    short tile[8];
+    short lu_g;
 };
 typedef FrLevelT<double> FrLevel;
 typedef FrLevelT<float> FrLevel32;

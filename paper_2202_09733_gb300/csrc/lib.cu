@@ -118,6 +118,7 @@ static void dfree(fr_ctx *C, void *p) {
 }
 
 static cudaStream_t S_(void *s) { return (cudaStream_t)s; }
+static void apply_cached_tiles(fr_ctx *C, int prec);
 
 extern "C" const char *fr_last_error(void) { return g_err; }
 
@@ -249,6 +250,7 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
     if (rc == FR_OK) rc = dalloc_t(C, &C->jv_qp, n0);
     if (rc == FR_OK) rc = dalloc_t(C, &C->jv_Rp, n0);
     if (rc != FR_OK) { fr_destroy(C); return rc; }
+    apply_cached_tiles(C, 0);
     *out = C;
     return FR_OK;
 }
@@ -393,6 +395,7 @@ static int ensure_levels32(fr_ctx *C) {
     CK(cudaDeviceSynchronize());
     CKLAUNCH();
     C->have32 = 1;
+    apply_cached_tiles(C, 1);
     return FR_OK;
 }
 
@@ -1230,6 +1233,243 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
     loc.converged = rk <= tol_rel * r0;
     if (st) *st = loc;
     return loc.converged ? FR_OK : fail(FR_ERR_NOT_CONVERGED, "steady PTC stopped at %g relative residual", loc.final_res);
+}
+
+// -------------------------------------------------------------------- autotuner
+// Launch shapes per (device, dimension, degree, precision, element count bucket): the CTA
+// size of each of the 8 residual kernels and the columns in flight of the block solve.
+// None of them changes a result bit; the autotuner times the candidates with CUDA events
+// on the context's own levels and keeps the fastest (one coordinate-descent pass over the
+// residual kernels, then G of the solve if that level's blocks are factored).
+struct TuneKey {
+    char dev[64];
+    int d, p, prec, ebucket;
+};
+struct TuneVal {
+    short tile[8];
+    short lu_g;
+};
+static std::vector<std::pair<TuneKey, TuneVal>> g_tune;
+
+static int ebucket(long long E) {
+    int b = 0;
+    while ((1LL << (b + 1)) <= E) ++b;
+    return b;
+}
+static TuneKey tune_key(const FrLevel &L, int prec) {
+    TuneKey k;
+    memset(&k, 0, sizeof k);
+    cudaDeviceProp pr;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaGetDeviceProperties(&pr, dev) == cudaSuccess) snprintf(k.dev, sizeof k.dev, "%s", pr.name);
+    for (char *c = k.dev; *c; ++c)
+        if (*c == ' ' || *c == '|') *c = '_';
+    k.d = L.d; k.p = L.p; k.prec = prec; k.ebucket = ebucket(L.E);
+    return k;
+}
+static TuneVal *tune_find(const TuneKey &k) {
+    for (auto &x : g_tune)
+        if (!strcmp(x.first.dev, k.dev) && x.first.d == k.d && x.first.p == k.p && x.first.prec == k.prec &&
+            x.first.ebucket == k.ebucket)
+            return &x.second;
+    return nullptr;
+}
+
+template <typename T>
+static int time_residual(fr_ctx *C, int l, const T *q, T *R, int reps, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+    TRY(residual_t<T>(C, l, q, R, 0));
+    CK(cudaEventRecord(e0, 0));
+    for (int r = 0; r < reps; ++r) TRY(residual_t<T>(C, l, q, R, 0));
+    CK(cudaEventRecord(e1, 0));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= reps;
+    return FR_OK;
+}
+
+template <typename T>
+static int tune_level(fr_ctx *C, int l, int prec, int reps, char *rep, size_t replen) {
+    FrLevelT<T> &L = levels<T>(C)[l];
+    const FrLevel &L64 = C->L[l];
+    long long n = L64.ndof;
+    // a state for timing: the free stream at every point
+    std::vector<T> h((size_t)n);
+    long long per = n / C->nv;
+    for (int v = 0; v < C->nv; ++v)
+        for (long long i = 0; i < per; ++i) h[(size_t)(v * per + i)] = (T)C->ph.qinf[v];
+    T *q = nullptr, *R = nullptr;
+    TRY(dalloc_t(C, &q, n));
+    TRY(dalloc_t(C, &R, n));
+    CK(cudaMemcpy(q, h.data(), sizeof(T) * n, cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    static const short cand[3] = {64, 128, 256};
+    float t0 = 0.f, best = 0.f;
+    int rc = time_residual<T>(C, l, q, R, reps, e0, e1, &t0);
+    best = t0;
+    for (int k = 0; rc == FR_OK && k < 8; ++k) {
+        short keep = L.tile[k];
+        for (short c : cand) {
+            L.tile[k] = c;
+            float t;
+            rc = time_residual<T>(C, l, q, R, reps, e0, e1, &t);
+            if (rc != FR_OK) break;
+            if (t < best) { best = t; keep = c; }
+        }
+        L.tile[k] = keep;
+    }
+    // G of the block solve, on the factored blocks of this level if there are any
+    float sb = -1.f, sg = -1.f;
+    PmgBuf<T> &P = pbuf<T>(C);
+    if (rc == FR_OK && C->pmg_ready && C->pmg_prec == prec && l < C->pmg_nlev && P.M[l]) {
+        static const short gc[3] = {2, 4, 8};
+        short keep = L.lu_g;
+        for (short g : gc) {
+            L.lu_g = g;
+            CK(cudaMemset(P.rhs[l], 0, sizeof(T) * n));
+            Kn<T>::solve(L, P.M[l], P.perm[l], P.rhs[l], 0);
+            CK(cudaEventRecord(e0, 0));
+            for (int r = 0; r < reps; ++r) Kn<T>::solve(L, P.M[l], P.perm[l], P.rhs[l], 0);
+            CK(cudaEventRecord(e1, 0));
+            CK(cudaEventSynchronize(e1));
+            float t;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            t /= reps;
+            if (sb < 0.f) sb = t;
+            if (sg < 0.f || t < sg) { sg = t; keep = g; }
+        }
+        L.lu_g = keep;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dfree(C, q);
+    dfree(C, R);
+    TRY(rc);
+    CKLAUNCH();
+    TuneKey key = tune_key(L64, prec);
+    TuneVal val;
+    memcpy(val.tile, L.tile, sizeof val.tile);
+    val.lu_g = L.lu_g;
+    if (TuneVal *v = tune_find(key)) *v = val;
+    else g_tune.push_back({key, val});
+    if (rep) {
+        size_t u = strlen(rep);
+        snprintf(rep + u, replen - u,
+                 "d=%d p=%d %s E=%d: tiles %d %d %d %d %d %d %d %d, residual %.4f -> %.4f ms; solve G %d%s\n", L.d, L.p,
+                 prec ? "fp32" : "fp64", L.E, L.tile[0], L.tile[1], L.tile[2], L.tile[3], L.tile[4], L.tile[5],
+                 L.tile[6], L.tile[7], t0, best, L.lu_g, sg >= 0.f ? "" : " (not tuned: no factored blocks)");
+    }
+    return FR_OK;
+}
+
+template <typename T>
+static void apply_tune(fr_ctx *C, int l, const TuneVal &v) {
+    FrLevelT<T> &L = levels<T>(C)[l];
+    memcpy(L.tile, v.tile, sizeof v.tile);
+    L.lu_g = v.lu_g;
+}
+
+// a new context (or its FP32 levels) takes the shapes already tuned for its key
+static void apply_cached_tiles(fr_ctx *C, int prec) {
+    for (int l = 0; l < C->nlev; ++l)
+        if (TuneVal *v = tune_find(tune_key(C->L[l], prec))) {
+            if (prec) apply_tune<float>(C, l, *v);
+            else apply_tune<double>(C, l, *v);
+        }
+}
+
+extern "C" int fr_autotune(fr_ctx *C, int flags, int reps, char *report, int report_len) {
+    if (!C || reps < 1) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    if (report && report_len > 0) report[0] = 0;
+    size_t rl = report && report_len > 0 ? (size_t)report_len : 0;
+    char *rp = rl ? report : nullptr;
+    for (int prec = 0; prec < 2; ++prec) {
+        if (!(flags & (1 << prec))) continue;
+        if (prec == 1) TRY(ensure_levels32(C));
+        for (int l = 0; l < C->nlev; ++l) {
+            TuneVal *v = (flags & 4) ? nullptr : tune_find(tune_key(C->L[l], prec));
+            if (v) {
+                if (prec) apply_tune<float>(C, l, *v);
+                else apply_tune<double>(C, l, *v);
+                if (rp) {
+                    size_t u = strlen(rp);
+                    snprintf(rp + u, rl - u, "d=%d p=%d %s E=%d: cached\n", C->L[l].d, C->L[l].p, prec ? "fp32" : "fp64",
+                             C->L[l].E);
+                }
+                continue;
+            }
+            if (prec) TRY(tune_level<float>(C, l, 1, reps, rp, rl));
+            else TRY(tune_level<double>(C, l, 0, reps, rp, rl));
+        }
+    }
+    return FR_OK;
+}
+
+extern "C" int fr_get_tiles(const fr_ctx *C, int l, int prec, int *tiles) {
+    if (!C || l < 0 || l >= C->nlev || !tiles || (prec != 0 && prec != 1)) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    const short *t = prec ? C->L32[l].tile : C->L[l].tile;
+    for (int k = 0; k < 8; ++k) tiles[k] = t[k] > 0 ? t[k] : 128;
+    tiles[8] = prec ? C->L32[l].lu_g : C->L[l].lu_g;
+    return FR_OK;
+}
+
+extern "C" int fr_set_tiles(fr_ctx *C, int l, int prec, const int *tiles) {
+    if (!C || l < 0 || l >= C->nlev || !tiles || (prec != 0 && prec != 1)) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    for (int k = 0; k < 8; ++k)
+        if (tiles[k] != 0 && (tiles[k] < 32 || tiles[k] > 256 || tiles[k] % 32))
+            return fail(FR_ERR_INVALID_ARG, "CTA size %d: a multiple of 32 in 32..256 (or 0)", tiles[k]);
+    if (tiles[8] != 0 && tiles[8] != 2 && tiles[8] != 4 && tiles[8] != 8)
+        return fail(FR_ERR_INVALID_ARG, "solve G must be 0, 2, 4 or 8");
+    if (prec == 1) TRY(ensure_levels32(C));
+    short *t = prec ? C->L32[l].tile : C->L[l].tile;
+    for (int k = 0; k < 8; ++k) t[k] = (short)tiles[k];
+    (prec ? C->L32[l].lu_g : C->L[l].lu_g) = (short)tiles[8];
+    return FR_OK;
+}
+
+extern "C" int fr_autotune_save(const char *path) {
+    if (!path) return fail(FR_ERR_INVALID_ARG, "NULL path");
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(FR_ERR_INVALID_ARG, "cannot write %s", path);
+    fprintf(f, "# frpmg launch shapes: device d p precision log2E tile0..tile7 solveG\n");
+    for (auto &x : g_tune) {
+        fprintf(f, "%s %d %d %d %d", x.first.dev, x.first.d, x.first.p, x.first.prec, x.first.ebucket);
+        for (int k = 0; k < 8; ++k) fprintf(f, " %d", x.second.tile[k]);
+        fprintf(f, " %d\n", x.second.lu_g);
+    }
+    fclose(f);
+    return FR_OK;
+}
+
+extern "C" int fr_autotune_load(const char *path) {
+    if (!path) return fail(FR_ERR_INVALID_ARG, "NULL path");
+    FILE *f = fopen(path, "r");
+    if (!f) return fail(FR_ERR_INVALID_ARG, "cannot read %s", path);
+    char line[512];
+    int n = 0;
+    while (fgets(line, sizeof line, f)) {
+        if (line[0] == '#') continue;
+        TuneKey k;
+        TuneVal v;
+        memset(&k, 0, sizeof k);
+        int t[9];
+        if (sscanf(line, "%63s %d %d %d %d %d %d %d %d %d %d %d %d %d", k.dev, &k.d, &k.p, &k.prec, &k.ebucket, &t[0],
+                   &t[1], &t[2], &t[3], &t[4], &t[5], &t[6], &t[7], &t[8]) != 14)
+            continue;
+        bool ok = true;
+        for (int i = 0; i < 8; ++i) ok &= t[i] == 0 || (t[i] >= 32 && t[i] <= 256 && t[i] % 32 == 0);
+        ok &= t[8] == 0 || t[8] == 2 || t[8] == 4 || t[8] == 8;
+        if (!ok) continue;
+        for (int i = 0; i < 8; ++i) v.tile[i] = (short)t[i];
+        v.lu_g = (short)t[8];
+        if (TuneVal *o = tune_find(k)) *o = v;
+        else g_tune.push_back({k, v});
+        ++n;
+    }
+    fclose(f);
+    return FR_OK;
 }
 
 #include "batch_impl.h"
