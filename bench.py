@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="preconditioner precision of the timed step (the FP64 step is timed alongside)")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ESDIRK3 initial-guess comparison (cylinder) and the batched step")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -143,6 +146,96 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def esdirk_guess_compare(api, w, T, np, torch, warm=6, timed=6):
+    """ESDIRK3 steps at the 1e-8 Newton tolerance on the unsteady low-Mach cylinder
+    (O-mesh 96 x 192, p = 3, Ma 0.05, Re 150, CFL 50, pMG p{3-2} n{2-2}, dtau = dt as in the
+    paper): the plain FP64 method (guess q^n, the paper's) against the mixed preconditioner
+    with the initial-guess candidates.  Each variant runs `warm` steps from the same state
+    (the history and the network's training data) and then `timed` steps, timed with CUDA
+    events."""
+    import math
+    wl = w.cylinder_unsteady()
+    A, b = T.esdirk3()
+    out = {"workload": "cylinder_unsteady 96x192 O-mesh quads p=3 (Ma 0.05, Re 150), ESDIRK3, dt = 50x explicit, "
+                       "Newton tol 1e-8 (RMS of a_ii dt F), pMG p{3-2} n{2-2}, FGMRES(30) tol 1e-2",
+           "warm_steps": warm, "timed_steps": timed, "variants": {}}
+    ref = None
+    for name, prec, guess, train in (("fp64_qn", "fp64", "qn", 0), ("mixed_qn", "mixed", "qn", 0),
+                                     ("mixed_extrap", "mixed", "extrap", 0), ("mixed_mlp", "mixed", "mlp", 10)):
+        G = api.fr_create(wl.mesh, wl.phys, wl.levels)
+        if guess == "mlp":
+            K0, O = api.fr_mlp_dims(G)
+            rng = np.random.default_rng(0)
+            H = 128
+            P = [rng.standard_normal((H, K0)) / math.sqrt(K0), np.zeros(H), rng.standard_normal((H, H)) / math.sqrt(H),
+                 np.zeros(H), rng.standard_normal((O, H)) / math.sqrt(H) * 0.1, np.zeros(O)]
+            net = api.MLP(K0, H, O, np.concatenate([x.reshape(-1) for x in P]).astype(np.float32))
+            api.fr_set_mlp(G, net)
+        o = api.solve_opts(kdim=30, maxit_gmres=300, max_ptc=40, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-8,
+                           dtau=wl.dt, inv_dtau_star=1.0 / wl.dt, precision=prec, guess=guess, train_iters=train,
+                           train_batch=4096, lr=1e-3)
+        q = torch.from_numpy(np.ascontiguousarray(wl.q0)).cuda()
+        for _ in range(warm):
+            api.esdirk_step(G, A, b, wl.dt, q, o)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sts = []
+        e0.record()
+        for _ in range(timed):
+            sts.append(api.esdirk_step(G, A, b, wl.dt, q, o))
+        e1.record()
+        torch.cuda.synchronize()
+        qf = q.cpu().numpy()
+        if ref is None:
+            ref = qf
+        out["variants"][name] = {
+            "s_per_step": e0.elapsed_time(e1) / 1e3 / timed,
+            "newton_per_step": float(np.mean([s_["n_ptc"] for s_ in sts])),
+            "gmres_per_step": float(np.mean([s_["n_gmres"] for s_ in sts])),
+            "picks_qn_extrap_mlp": [int(sum(s_["guess_pick"][k] for s_ in sts)) for k in range(3)],
+            "state_vs_fp64_qn_maxrel": float(np.abs(qf - ref).max() / np.abs(ref).max()),
+        }
+    v = out["variants"]
+    out["speedup_mixed_extrap_vs_fp64_qn"] = v["fp64_qn"]["s_per_step"] / v["mixed_extrap"]["s_per_step"]
+    out["speedup_mixed_mlp_vs_fp64_qn"] = v["fp64_qn"]["s_per_step"] / v["mixed_mlp"]["s_per_step"]
+    return out
+
+
+def batched_step(api, w, T, np, torch, N):
+    """One ESDIRK3 step of 256 independent periodic vortex problems (n x n quads, n in
+    4..48, p in 1..4, seeded), grouped by p-levels on merged meshes, Arnoldi steps under
+    CUDA graphs, autotuned launch shapes; one warm step then one timed step per precision."""
+    probs, states, phys, dt = w.vortex_batch()
+    A, b = T.esdirk3()
+    out = {"workload": f"{len(probs)} periodic vortex problems, n x n quads n~U{{4..48}}, p~U{{1..4}}, "
+                       f"levels p{{p-(p-1)}} (p=1: one level), ESDIRK3, common dt {dt:.4g}, Newton tol 1e-8",
+           "elements": int(sum(m["E"] for m, _ in probs)),
+           "dofs": int(sum(4 * (lv[0] + 1) ** 2 * m["E"] for m, lv in probs))}
+    for prec in ("fp64", "mixed"):
+        Bt = api.Batch(probs, phys)
+        go = api.solve_opts(kdim=30, maxit_gmres=300, max_ptc=40, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-8,
+                            dtau=dt, inv_dtau_star=1.0 / dt, precision=prec)
+        qs = [torch.from_numpy(np.ascontiguousarray(q)).cuda() for q in states]
+        Bt.esdirk_step(A, b, dt, [x.clone() for x in qs], go)
+        Bt.autotune(fp64=True, fp32=(prec == "mixed"), retune=False, reps=3)
+        Bt.esdirk_step(A, b, dt, [x.clone() for x in qs], go)     # graphs captured with the tuned shapes
+        torch.cuda.synchronize()
+        n0 = N.load().fr_kernel_launches()
+        # the batch runs on its own stream, ordered after and before the current stream,
+        # so events on the current stream bracket its work
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = Bt.esdirk_step(A, b, dt, qs, go)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        out[prec] = {"s_per_step": t, "problems_per_s": len(probs) / t,
+                     "converged": int(sum(s_["converged"] for s_ in st)),
+                     "gmres_total": int(sum(s_["n_gmres"] for s_ in st)),
+                     "kernel_launches": int(N.load().fr_kernel_launches() - n0)}
+    return out
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -176,6 +269,13 @@ def gpu_arm(args):
     def step(o=opts):
         q.copy_(q0)
         return api.row_step(ctx, g, a, c, m, W.dt, q, o)
+
+    tune = None
+    if not args.no_autotune:
+        # launch shapes of this GPU for the residual kernels; G of the block solves after
+        # one step has factored the blocks (no result bit depends on either)
+        step()
+        tune = api.fr_autotune(ctx, fp64=True, fp32=True, retune=True, reps=3)
 
     def barrier():
         if ws > 1:
@@ -252,6 +352,11 @@ def gpu_arm(args):
     t_e2e = (time.perf_counter() - t0) / args.steps
     barrier()
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["esdirk_cylinder"] = esdirk_guess_compare(api, w, T, np, torch)
+        extras["batched_vortex"] = batched_step(api, w, T, np, torch, N)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -292,7 +397,9 @@ def gpu_arm(args):
             "cpu_baseline": cpu,
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "autotune": tune,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
