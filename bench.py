@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "implicit step wall time @1e-8 tol: mixed/learned pMG vs FP64; residual GDOF/s"
 FP64_PEAK_NOMINAL = 1.25e12        # GB300 FP64 (vector = tensor), nominal
 SAMPLE_N = 4                       # oracle sample: 4^3 hexes, scaled by (32/4)^3
+RESIDUAL_TRAFFIC_BYTES = 6.371e9   # DRAM bytes of one FP64 residual launch on 32^3 p=3 (ncu)
 
 
 def parse():
@@ -146,7 +147,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def esdirk_guess_compare(api, w, T, np, torch, warm=6, timed=6):
+def esdirk_guess_compare(api, w, T, np, torch, warm=15, timed=6):
     """ESDIRK3 steps at the 1e-8 Newton tolerance on the unsteady low-Mach cylinder
     (O-mesh 96 x 192, p = 3, Ma 0.05, Re 150, CFL 50, pMG p{3-2} n{2-2}, dtau = dt as in the
     paper): the plain FP64 method (guess q^n, the paper's) against the mixed preconditioner
@@ -389,7 +390,10 @@ def gpu_arm(args):
             "gmres_iterations_per_step": statistics.mean(ng),
             "roofline": {"kernel": "fr_residual (FP64 FR residual, 8 kernels per launch)", "bound": "alu",
                          "achieved": flops / t_R / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
-                         "frac": (flops / t_R) / FP64_PEAK_NOMINAL, "traffic": None,
+                         "frac": (flops / t_R) / FP64_PEAK_NOMINAL, "traffic": RESIDUAL_TRAFFIC_BYTES,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 8 kernels of one "
+                                           "residual on this workload at the default launch shapes "
+                                           "(profiles/residual_tgv3d32_fp64_dram.md)",
                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 entry); "
                                         "a DFMA-chain probe measured 1.19"},
             "e2e": {"value": t_e2e, "unit": "s/step", "h2d_bytes_per_step": q_host.numel() * 8,
