@@ -120,10 +120,10 @@ int fr_jvp(fr_ctx *ctx, const double *q, const double *Rq, const double *v, doub
  * E * nd * nd doubles, column-major per element (see Layouts). */
 int fr_elem_blocks(fr_ctx *ctx, int level, const double *q, double shift, double *M, void *stream);
 
-/* In-place LU with partial pivoting of every block (first maximal |pivot|).  M as above;
- * perm: device int [E][nd], receives the row permutation (row i of LU is row perm[i] of
- * the input block).  Returns FR_ERR_BREAKDOWN (after the whole batch) if a zero pivot
- * was met. */
+/* In-place LU with partial pivoting of every block (first maximal |pivot|).  M as above,
+ * receives L (unit, below the diagonal), U (above) and 1/u_kk on the diagonal; perm:
+ * device int [E][nd], receives the row permutation (row i of LU is row perm[i] of the
+ * input block).  Returns FR_ERR_BREAKDOWN (after the whole batch) if a zero pivot was met. */
 int fr_block_factor(fr_ctx *ctx, int level, double *M, int *perm, void *stream);
 /* x <- M_e^{-1} x for every element using the factors of fr_block_factor.
  * x: device [nv][Np][E], overwritten. */
@@ -283,21 +283,32 @@ int ptc_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, double
  * per CTA tile, 64/128/256) of each of the 8 kernels of the residual, per level and
  * precision, and the columns in flight G (2/4/8) of the block solve.  fr_autotune times
  * the candidates with CUDA events on the context's own levels (reps launches each after
- * a warm-up; a coordinate-descent pass over the residual kernels, then G on the level's
- * factored blocks if pmg_setup has run in that precision) and keeps the fastest.  flags:
+ * a warm-up; a coordinate-descent pass over the residual kernels, then the solve variant
+ * on the level's factored blocks if pmg_setup has run in that precision) and keeps the
+ * fastest.  Solve variants: the register kernel with G = 2, 4 or 8 columns in flight, or
+ * (G = 1) the kernel that streams the factor through shared memory with bulk async
+ * copies (rows of a column that the pass needs only; nd * sizeof(scalar) % 16 == 0).  flags:
  * bit 0 FP64 levels, bit 1 FP32 levels, bit 2 re-tune even if cached.  Results are kept
  * in a process-wide cache keyed by (device name, d, p, precision, floor(log2 E)); new
  * contexts pick cached shapes up.  report (host, may be NULL): one line per level.
  * Uses the legacy default stream and synchronises the device. */
 int fr_autotune(fr_ctx *ctx, int flags, int reps, char *report, int report_len);
 /* tiles[9]: the 8 CTA sizes (0 = default 128; else a multiple of 32 in 32..256) and G
- * (0 = default, 2, 4 or 8) of level `level` in precision 0 (FP64) or 1 (FP32) */
+ * (0 = default, 1 = bulk-copy kernel, 2, 4 or 8) of level `level` in precision 0 (FP64)
+ * or 1 (FP32) */
 int fr_get_tiles(const fr_ctx *ctx, int level, int precision, int *tiles);
 int fr_set_tiles(fr_ctx *ctx, int level, int precision, const int *tiles);
 /* the cache as a text file: one line "device d p precision log2E tile0..tile7 G" per key
  * (load skips malformed lines and out-of-range values) */
 int fr_autotune_save(const char *path);
 int fr_autotune_load(const char *path);
+/* bounded device-side waits that ran out since the last clear (bit 0: block-solve stage
+ * barriers); such a kernel records the failure and returns instead of hanging */
+int fr_kernel_timeouts(int clear);
+/* runs the time-out path of those waits on purpose (a barrier that nothing completes,
+ * 4096 polls) so that callers can check that it reports through fr_kernel_timeouts and
+ * leaves the context usable; synchronises the device */
+int fr_selftest_wait_timeout(void);
 
 /* ------------------------------------------------------------------ batches
  * Many independent problems advanced together (not in the paper: a throughput mode).

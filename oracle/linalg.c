@@ -11,8 +11,10 @@
  *
  * Dense LU: Gaussian elimination with partial pivoting (first maximal |pivot|, rows
  * swapped), multipliers l = a/u, trailing updates a = fma(-l, u, a) in ascending
- * elimination order; triangular solves as fma chains in the order the unknowns become
- * known (ascending column index forward, descending column index backward).
+ * elimination order; the factor keeps the reciprocal 1/u_kk in place of each pivot
+ * (the paper leaves the LU arithmetic open; one division per pivot instead of one per
+ * solve).  Triangular solves as fma chains in the order the unknowns become known
+ * (ascending column index forward, descending column index backward), x_k = s_k (1/u_kk).
  *
  * Transfers (Eqs. 17-18): the 1-D Gamma / Pi applied along direction 0, then 1, then 2.
  */
@@ -69,6 +71,7 @@ void or_lu_factor(int n, double *A, int *piv) {
                 A[(size_t)i * n + j] = fma(-li, A[(size_t)k * n + j], A[(size_t)i * n + j]);
         }
     }
+    for (int k = 0; k < n; ++k) A[(size_t)k * n + k] = 1.0 / A[(size_t)k * n + k];
 }
 
 void or_lu_solve(int n, const double *A, const int *piv, double *b) {
@@ -82,7 +85,7 @@ void or_lu_solve(int n, const double *A, const int *piv, double *b) {
     for (int i = n - 1; i >= 0; --i) {
         double s = b[i];
         for (int k = n - 1; k > i; --k) s = fma(-A[(size_t)i * n + k], b[k], s);
-        b[i] = s / A[(size_t)i * n + i];
+        b[i] = s * A[(size_t)i * n + i];
     }
 }
 

@@ -24,7 +24,8 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_last_error", "fr_kernel_launches", "fr
            "mlp_create", "mlp_destroy", "mlp_get_params", "mlp_forward", "mlp_train_step", "fr_mlp_dims",
            "fr_set_mlp", "fr_reset_history", "fr_guess_features", "fr_batch_create", "fr_batch_destroy",
            "fr_batch_info", "fr_batch_set_graphs", "fr_batch_residual", "fr_batch_esdirk_step", "fr_autotune",
-           "fr_get_tiles", "fr_set_tiles", "fr_autotune_save", "fr_autotune_load", "fr_batch_autotune"]
+           "fr_get_tiles", "fr_set_tiles", "fr_autotune_save", "fr_autotune_load", "fr_batch_autotune", "fr_kernel_timeouts",
+           "fr_selftest_wait_timeout"]
 
 
 class MeshDesc(C.Structure):
@@ -131,6 +132,8 @@ def load(path: str = LIB_PATH):
         "fr_autotune_save": ([C.c_char_p], C.c_int),
         "fr_autotune_load": ([C.c_char_p], C.c_int),
         "fr_batch_autotune": ([VP, C.c_int, C.c_int, C.c_char_p, C.c_int], C.c_int),
+        "fr_kernel_timeouts": ([C.c_int], C.c_int),
+        "fr_selftest_wait_timeout": ([], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

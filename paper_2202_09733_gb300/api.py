@@ -325,6 +325,14 @@ def fr_set_tiles(ctx, level, tiles, precision=0):
     N.check(N.load().fr_set_tiles(ctx.handle, int(level), int(precision), t.ctypes.data_as(N.PI)), "fr_set_tiles")
 
 
+def fr_kernel_timeouts(clear=True):
+    return int(N.load().fr_kernel_timeouts(int(bool(clear))))
+
+
+def fr_selftest_wait_timeout():
+    N.check(N.load().fr_selftest_wait_timeout(), "fr_selftest_wait_timeout")
+
+
 def fr_autotune_save(path):
     N.check(N.load().fr_autotune_save(str(path).encode()), "fr_autotune_save")
 

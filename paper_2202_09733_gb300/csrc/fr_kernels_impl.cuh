@@ -236,6 +236,9 @@ __global__ void __launch_bounds__(256) k_lu_factor(FRT *M, int *perm, int nd, in
         }
         __syncthreads();
     }
+    // the factor keeps 1/u_kk in place of each pivot (the solve multiplies by it)
+    for (int k = tid; k < nd; k += nt) A[(size_t)k * nd + k] = (FRT)1 / A[(size_t)k * nd + k];
+    __syncthreads();
     if (SMEM)
         for (int t = tid; t < nd * nd; t += nt) Ag[t] = A[t];
 }
@@ -359,6 +362,8 @@ __global__ void __launch_bounds__(256) k_lu_factor_blocked(FRT *M, int *perm, in
         }
         __syncthreads();
     }
+    // the factor keeps 1/u_kk in place of each pivot (the solve multiplies by it)
+    for (int k = tid; k < nd; k += nt) A[(size_t)k * nd + k] = (FRT)1 / A[(size_t)k * nd + k];
 }
 
 int FRK(lu_factor)(const FrLevelT<FRT> &L, FRT *M, int *perm, int *info, cudaStream_t s) {
@@ -389,7 +394,7 @@ int FRK(lu_factor)(const FrLevelT<FRT> &L, FRT *M, int *perm, int *info, cudaStr
 // One warp per element: rows i = lane + 32 s held in registers.  Forward substitution
 // with the unit lower factor applies y_k to every later row in ascending k; backward
 // substitution applies x_k to every earlier row in descending k (the order the unknowns
-// become known), x_k = b_k / u_kk.  Columns are fetched G at a time ahead of the
+// become known), x_k = b_k (1/u_kk) with the reciprocal the factor stored.  Columns are fetched G at a time ahead of the
 // dependent fma chain so that G column loads are in flight per step.
 template <int NR>
 __device__ __forceinline__ FRT pick(const FRT (&b)[NR], int slot) {
@@ -413,55 +418,66 @@ __global__ void __launch_bounds__(128) k_lu_solve(const FRT *__restrict__ M, con
         int i = lane + 32 * s;
         b[s] = i < nd ? x[(size_t)pv[i] * E + e] : (FRT)0;
     }
-    for (int k0 = 0; k0 < nd; k0 += G) {
-        FRT cv[G][NR];
+    // forward: column k lives in register slot sk = k / 32 (compile-time in this unrolled
+    // loop), so y_k is one shuffle of b[sk] and only slots sk.. hold rows below k
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            int k = k0 + g;
-            const FRT *col = A + (size_t)(k < nd ? k : nd - 1) * nd;
+    for (int sk = 0; sk < NR; ++sk) {
+        const int kend = min(nd, 32 * sk + 32);
+        for (int k0 = 32 * sk; k0 < kend; k0 += G) {
+            FRT cv[G][NR];
 #pragma unroll
-            for (int s = 0; s < NR; ++s) {
-                int i = lane + 32 * s;
-                cv[g][s] = (k < nd && i > k && i < nd) ? col[i] : (FRT)0;
+            for (int g = 0; g < G; ++g) {
+                int k = k0 + g;
+                const FRT *col = A + (size_t)(k < kend ? k : kend - 1) * nd;
+#pragma unroll
+                for (int s = sk; s < NR; ++s) {
+                    int i = lane + 32 * s;
+                    bool need = k < kend && i < nd && (s > sk || lane > (k & 31));
+                    cv[g][s] = need ? col[i] : (FRT)0;
+                }
             }
-        }
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            int k = k0 + g;
-            if (k >= nd) break;
-            FRT yk = __shfl_sync(0xffffffffu, pick<NR>(b, k >> 5), k & 31);
+            for (int g = 0; g < G; ++g) {
+                int k = k0 + g;
+                if (k >= kend) break;
+                FRT yk = __shfl_sync(0xffffffffu, b[sk], k & 31);
 #pragma unroll
-            for (int s = 0; s < NR; ++s) {
-                int i = lane + 32 * s;
-                if (i > k && i < nd) b[s] = fma(-cv[g][s], yk, b[s]);
+                for (int s = sk; s < NR; ++s) {
+                    int i = lane + 32 * s;
+                    if (i < nd && (s > sk || lane > (k & 31))) b[s] = fma(-cv[g][s], yk, b[s]);
+                }
             }
         }
     }
-    for (int kt = nd - 1; kt >= 0; kt -= G) {
-        FRT cv[G][NR];
+    // backward: x_k = b_k / u_kk on the owner lane, then rows above k; slots 0..sk
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            int k = kt - g;
-            const FRT *col = A + (size_t)(k >= 0 ? k : 0) * nd;
+    for (int sk = NR - 1; sk >= 0; --sk) {
+        const int kbeg = min(nd, 32 * sk + 32) - 1;
+        for (int kt = kbeg; kt >= 32 * sk; kt -= G) {
+            FRT cv[G][NR];
 #pragma unroll
-            for (int s = 0; s < NR; ++s) {
-                int i = lane + 32 * s;
-                cv[g][s] = (k >= 0 && i <= k) ? col[i] : (FRT)0;
+            for (int g = 0; g < G; ++g) {
+                int k = kt - g;
+                const FRT *col = A + (size_t)(k >= 32 * sk ? k : 32 * sk) * nd;
+#pragma unroll
+                for (int s = 0; s <= sk; ++s) {
+                    int i = lane + 32 * s;
+                    bool need = k >= 32 * sk && (s < sk || lane <= (k & 31));
+                    cv[g][s] = need ? col[i] : (FRT)0;
+                }
             }
-        }
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            int k = kt - g;
-            if (k < 0) break;
-            int owner = k & 31, slot = k >> 5;
-            FRT xk = (FRT)0;
-            if (lane == owner) xk = pick<NR>(b, slot) / pick<NR>(cv[g], slot);
-            xk = __shfl_sync(0xffffffffu, xk, owner);
+            for (int g = 0; g < G; ++g) {
+                int k = kt - g;
+                if (k < 32 * sk) break;
+                int owner = k & 31;
+                FRT xk = (FRT)0;
+                if (lane == owner) xk = b[sk] * cv[g][sk];   // the factor holds 1/u_kk
+                xk = __shfl_sync(0xffffffffu, xk, owner);
 #pragma unroll
-            for (int s = 0; s < NR; ++s) {
-                int i = lane + 32 * s;
-                if (i == k) b[s] = xk;
-                else if (i < k) b[s] = fma(-cv[g][s], xk, b[s]);
+                for (int s = 0; s < sk; ++s) b[s] = fma(-cv[g][s], xk, b[s]);
+                if (lane == owner) b[sk] = xk;
+                else if (lane < owner) b[sk] = fma(-cv[g][sk], xk, b[sk]);
             }
         }
     }
@@ -471,6 +487,223 @@ __global__ void __launch_bounds__(128) k_lu_solve(const FRT *__restrict__ M, con
         int i = lane + 32 * s;
         if (i < nd) x[(size_t)i * E + e] = b[s];
     }
+}
+
+// Block solve with the factor streamed through shared memory by the bulk-copy (TMA)
+// engine.  One warp per element, LUB_W warps per CTA, each warp with its own ring of
+// LUB_NS stages of cg columns and one mbarrier per stage.  Lane 0 issues, per column,
+// one cp.async.bulk of exactly the rows the pass needs (forward: rows below the diagonal,
+// from the 16-byte boundary at or before k+1; backward: rows 0..k, to the 16-byte
+// boundary at or after k+1), so the factor is read about once per solve; the warp
+// computes on stage t while stages t+1, t+2 are in flight.  The arithmetic is the
+// register kernel's, fma for fma, so both give the same result bits.  Every wait is
+// bounded: on time-out the warp records the failure in g_lub_err, waits (bounded) for its
+// own copies in flight and returns.  Needs nd * sizeof(FRT) % 16 == 0.
+#define LUB_W 6
+#define LUB_NS 3
+#define LUB_STAGE_BYTES 12288
+static __device__ int g_lub_err;
+
+__device__ __forceinline__ unsigned lub_smem(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void lub_bar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(lub_smem(bar)));
+}
+__device__ __forceinline__ void lub_expect(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lub_smem(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void lub_copy(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(lub_smem(dst)), "l"(src), "r"(bytes), "r"(lub_smem(bar)) : "memory");
+}
+__device__ __forceinline__ bool lub_wait(unsigned long long *bar, unsigned parity, int limit = 1 << 22) {
+    for (int it = 0; it < limit; ++it) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(lub_smem(bar)), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// chunk t of the sequence: forward chunks (columns k0 .. k0+cg-1 ascending), then backward
+// chunks (columns kt, kt-1, ... descending); returns the number of columns
+__device__ __forceinline__ int lub_chunk(int t, int nf, int cg, int nd, bool *fwd, int *k0) {
+    if (t < nf) {
+        *fwd = true;
+        *k0 = t * cg;
+        return min(cg, nd - *k0);
+    }
+    *fwd = false;
+    *k0 = nd - 1 - (t - nf) * cg;
+    return min(cg, *k0 + 1);
+}
+
+// lane 0: stage the needed rows of the chunk's columns and arm the stage barrier
+__device__ __forceinline__ void lub_issue(const FRT *A, FRT *stage, unsigned long long *bar, int t, int nf, int cg,
+                                          int nd) {
+    const int AL = 16 / (int)sizeof(FRT);
+    bool fwd;
+    int k0;
+    int nc = lub_chunk(t, nf, cg, nd, &fwd, &k0);
+    unsigned total = 0;
+    for (int g = 0; g < nc; ++g) {
+        int k = fwd ? k0 + g : k0 - g;
+        int r0 = fwd ? ((k + 1) / AL) * AL : 0;
+        int r1 = fwd ? nd : min(nd, ((k + 1 + AL - 1) / AL) * AL);
+        total += (unsigned)((r1 - r0) * (int)sizeof(FRT));
+    }
+    lub_expect(bar, total);
+    for (int g = 0; g < nc; ++g) {
+        int k = fwd ? k0 + g : k0 - g;
+        int r0 = fwd ? ((k + 1) / AL) * AL : 0;
+        int r1 = fwd ? nd : min(nd, ((k + 1 + AL - 1) / AL) * AL);
+        if (r1 > r0)
+            lub_copy(stage + (size_t)g * nd + r0, A + (size_t)k * nd + r0, (unsigned)((r1 - r0) * (int)sizeof(FRT)), bar);
+    }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(32 * LUB_W) k_lu_solve_bulk(const FRT *__restrict__ M, const int *__restrict__ perm,
+                                                              FRT *__restrict__ x, int nd, int E, int cg) {
+    extern __shared__ __align__(16) unsigned char lub_raw[];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(lub_raw) + warp * LUB_NS;
+    FRT *ring = reinterpret_cast<FRT *>(lub_raw + 16 * ((LUB_W * LUB_NS * 8 + 15) / 16)) +
+                (size_t)warp * LUB_NS * cg * nd;
+    int e = blockIdx.x * LUB_W + warp;
+    if (e >= E) return;   // warp-uniform: this warp has no element
+    const FRT *A = M + (size_t)e * nd * nd;
+    const int *pv = perm + (size_t)e * nd;
+    if (lane == 0)
+        for (int st = 0; st < LUB_NS; ++st) lub_bar_init(&bars[st]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
+    int nf = (nd + cg - 1) / cg, nt = 2 * nf;
+    if (lane == 0)
+        for (int t = 0; t < LUB_NS && t < nt; ++t) lub_issue(A, ring + (size_t)t * cg * nd, &bars[t], t, nf, cg, nd);
+    FRT b[NR];
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+        int i = lane + 32 * s;
+        b[s] = i < nd ? x[(size_t)pv[i] * E + e] : (FRT)0;
+    }
+    unsigned phase = 0;   // bit st: parity of stage st's next completion
+    for (int t = 0; t < nt; ++t) {
+        int st = t % LUB_NS;
+        bool ok = lub_wait(&bars[st], (phase >> st) & 1u);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                atomicExch(&g_lub_err, 1);
+                // copies still in flight (issued for chunks t .. min(nt, t + LUB_NS) - 1)
+                for (int u = t; u < nt && u < t + LUB_NS; ++u) {
+                    int su = u % LUB_NS;
+                    lub_wait(&bars[su], (phase >> su) & 1u);
+                    phase ^= 1u << su;
+                }
+            }
+            __syncwarp();
+            return;
+        }
+        phase ^= 1u << st;
+        const FRT *stage = ring + (size_t)st * cg * nd;
+        bool fwd;
+        int k0;
+        int nc = lub_chunk(t, nf, cg, nd, &fwd, &k0);
+        if (fwd) {
+            for (int g = 0; g < nc; ++g) {
+                int k = k0 + g;
+                const FRT *col = stage + (size_t)g * nd;
+                FRT yk = __shfl_sync(0xffffffffu, pick<NR>(b, k >> 5), k & 31);
+#pragma unroll
+                for (int s = 0; s < NR; ++s) {
+                    int i = lane + 32 * s;
+                    if (i > k && i < nd) b[s] = fma(-col[i], yk, b[s]);
+                }
+            }
+        } else {
+            for (int g = 0; g < nc; ++g) {
+                int k = k0 - g;
+                const FRT *col = stage + (size_t)g * nd;
+                int owner = k & 31, slot = k >> 5;
+                FRT xk = (FRT)0;
+                if (lane == owner) xk = pick<NR>(b, slot) * col[k];   // the factor holds 1/u_kk
+                xk = __shfl_sync(0xffffffffu, xk, owner);
+#pragma unroll
+                for (int s = 0; s < NR; ++s) {
+                    int i = lane + 32 * s;
+                    if (i == k) b[s] = xk;
+                    else if (i < k) b[s] = fma(-col[i], xk, b[s]);
+                }
+            }
+        }
+        __syncwarp();   // every lane is done with this stage before it is refilled
+        if (lane == 0 && t + LUB_NS < nt) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads before the async writes
+            lub_issue(A, ring + (size_t)st * cg * nd, &bars[st], t + LUB_NS, nf, cg, nd);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+        int i = lane + 32 * s;
+        if (i < nd) x[(size_t)i * E + e] = b[s];
+    }
+}
+
+static int lub_cg(int nd) {
+    int cg = LUB_STAGE_BYTES / (nd * (int)sizeof(FRT));
+    return cg < 1 ? 1 : cg > 32 ? 32 : cg;
+}
+static size_t lub_smem_bytes(int nd) {
+    return 16 * (size_t)((LUB_W * LUB_NS * 8 + 15) / 16) + (size_t)LUB_W * LUB_NS * lub_cg(nd) * nd * sizeof(FRT);
+}
+
+// shared-memory limits of the bulk kernel, set before any launch (and before any stream
+// capture that may contain one)
+void FRK(lu_solve_prepare)() {
+    static bool done = false;
+    if (done) return;
+    int lim = 227 * 1024;
+    cudaFuncSetAttribute(k_lu_solve_bulk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu_solve_bulk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu_solve_bulk<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu_solve_bulk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu_solve_bulk<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_lu_solve_bulk<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    done = true;
+}
+// The time-out path of the bounded stage waits, exercised on purpose: one warp arms a
+// barrier for 16 bytes that no copy will deliver, waits `limit` polls, records the
+// failure and returns (nothing is in flight, so nothing is left behind).
+static __global__ void k_wait_selftest(int limit) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) lub_bar_init(&bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
+    if (threadIdx.x == 0) lub_expect(&bar, 16);
+    __syncwarp();
+    bool ok = lub_wait(&bar, 0, limit);
+    if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicExch(&g_lub_err, 1);
+}
+void FRK(wait_selftest)(int limit, cudaStream_t s) { CNT(); k_wait_selftest<<<1, 32, 0, s>>>(limit); }
+
+int FRK(lu_solve_error)(int clear) {
+    int h = 0;
+    cudaMemcpyFromSymbol(&h, g_lub_err, sizeof(int));
+    if (clear) {
+        int z = 0;
+        cudaMemcpyToSymbol(g_lub_err, &z, sizeof(int));
+    }
+    return h;
+}
+
+static bool lub_usable(int nd) {
+    return (nd * (int)sizeof(FRT)) % 16 == 0 && lub_smem_bytes(nd) <= 227 * 1024;
+}
+
+template <int NR>
+static void lub_launch(const FrLevelT<FRT> &L, const FRT *M, const int *perm, FRT *x, cudaStream_t s) {
+    int grid = (L.E + LUB_W - 1) / LUB_W;
+    CNT(); k_lu_solve_bulk<NR><<<grid, 32 * LUB_W, lub_smem_bytes(L.nd), s>>>(M, perm, x, L.nd, L.E, lub_cg(L.nd));
 }
 
 // G (columns in flight) is a launch-shape choice: 2, 4 or 8 where G x NR <= 40 registers
@@ -486,8 +719,20 @@ static int lu_solve_nr(int g, int grid, const FRT *M, const int *perm, FRT *x, i
 int FRK(lu_solve)(const FrLevelT<FRT> &L, const FRT *M, const int *perm, FRT *x, cudaStream_t s) {
     int nr = (L.nd + 31) / 32;
     int grid = (L.E * 32 + 127) / 128;
+    // lu_g 1 selects the bulk-copy (TMA) kernel where the layout allows it
+    if (L.lu_g == 1 && lub_usable(L.nd)) {
+        switch (nr) {
+            case 1: lub_launch<1>(L, M, perm, x, s); return 0;
+            case 2: lub_launch<2>(L, M, perm, x, s); return 0;
+            case 3: lub_launch<3>(L, M, perm, x, s); return 0;
+            case 4: lub_launch<4>(L, M, perm, x, s); return 0;
+            case 5: lub_launch<5>(L, M, perm, x, s); return 0;
+            case 10: lub_launch<10>(L, M, perm, x, s); return 0;
+            default: break;
+        }
+    }
     // default G: the choice measured best before tuning existed
-    int g = L.lu_g > 0 ? L.lu_g : (nr <= 2 ? 8 : nr <= 5 ? 4 : (nr == 10 && sizeof(FRT) == 4) ? 4 : 2);
+    int g = L.lu_g > 1 ? L.lu_g : (nr <= 2 ? 8 : nr <= 5 ? 4 : (nr == 10 && sizeof(FRT) == 4) ? 4 : 2);
     switch (nr) {
         case 1: lu_solve_nr<1>(g, grid, M, perm, x, L.nd, L.E, s); break;
         case 2: lu_solve_nr<2>(g, grid, M, perm, x, L.nd, L.E, s); break;

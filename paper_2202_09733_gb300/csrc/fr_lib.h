@@ -20,8 +20,8 @@ struct FrLevelT {
     // residual workspace
     T *qf, *dq, *Q, *Qf, *fn, *Ft, *Ftf;
     double etagL, etagR;
-    // launch shapes (0 = default): CTA size of the 8 residual kernels, columns in flight
-    // of the block solve
+    // launch shapes (0 = default): CTA size of the 8 residual kernels; block solve: columns
+    // in flight of the register kernel (2, 4, 8) or 1 = the bulk-copy (TMA) kernel
     short tile[8];
     short lu_g;
 };
@@ -55,6 +55,9 @@ struct FrTabH {
                           const T *Rp, double shift, double epsrel, T *M, cudaStream_t s);                  \
     int P##_lu_factor(const FrLevelT<T> &L, T *M, int *perm, int *info_dev, cudaStream_t s);               \
     int P##_lu_solve(const FrLevelT<T> &L, const T *M, const int *perm, T *x, cudaStream_t s);             \
+    void P##_lu_solve_prepare();                                                                            \
+    int P##_lu_solve_error(int clear);                                                                      \
+    void P##_wait_selftest(int limit, cudaStream_t s);                                                      \
     int P##_transfer(const FrLevelT<T> &Lf, const FrLevelT<T> &Lc, bool restrict_, const T *x, T *y,       \
                      cudaStream_t s);
 

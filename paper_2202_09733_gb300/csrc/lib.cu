@@ -10,6 +10,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <algorithm>
+#include <string>
 #include <vector>
 #include "../../include/frpmg.h"
 #include "fr_lib.h"
@@ -251,7 +252,20 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
     if (rc == FR_OK) rc = dalloc_t(C, &C->jv_Rp, n0);
     if (rc != FR_OK) { fr_destroy(C); return rc; }
     apply_cached_tiles(C, 0);
+    frk64_lu_solve_prepare();
+    frk32_lu_solve_prepare();
     *out = C;
+    return FR_OK;
+}
+
+extern "C" int fr_kernel_timeouts(int clear) {
+    return frk64_lu_solve_error(clear) | frk32_lu_solve_error(clear);
+}
+
+extern "C" int fr_selftest_wait_timeout(void) {
+    frk32_wait_selftest(1 << 12, 0);
+    CKLAUNCH();
+    CK(cudaDeviceSynchronize());
     return FR_OK;
 }
 
@@ -1321,10 +1335,11 @@ static int tune_level(fr_ctx *C, int l, int prec, int reps, char *rep, size_t re
         L.tile[k] = keep;
     }
     // G of the block solve, on the factored blocks of this level if there are any
-    float sb = -1.f, sg = -1.f;
+    float sg = -1.f;
+    char gtimes[160] = "";
     PmgBuf<T> &P = pbuf<T>(C);
     if (rc == FR_OK && C->pmg_ready && C->pmg_prec == prec && l < C->pmg_nlev && P.M[l]) {
-        static const short gc[3] = {2, 4, 8};
+        static const short gc[4] = {1, 2, 4, 8};
         short keep = L.lu_g;
         for (short g : gc) {
             L.lu_g = g;
@@ -1337,7 +1352,8 @@ static int tune_level(fr_ctx *C, int l, int prec, int reps, char *rep, size_t re
             float t;
             CK(cudaEventElapsedTime(&t, e0, e1));
             t /= reps;
-            if (sb < 0.f) sb = t;
+            size_t u = strlen(gtimes);
+            snprintf(gtimes + u, sizeof gtimes - u, " %d:%.3f", g, t);
             if (sg < 0.f || t < sg) { sg = t; keep = g; }
         }
         L.lu_g = keep;
@@ -1357,9 +1373,10 @@ static int tune_level(fr_ctx *C, int l, int prec, int reps, char *rep, size_t re
     if (rep) {
         size_t u = strlen(rep);
         snprintf(rep + u, replen - u,
-                 "d=%d p=%d %s E=%d: tiles %d %d %d %d %d %d %d %d, residual %.4f -> %.4f ms; solve G %d%s\n", L.d, L.p,
-                 prec ? "fp32" : "fp64", L.E, L.tile[0], L.tile[1], L.tile[2], L.tile[3], L.tile[4], L.tile[5],
-                 L.tile[6], L.tile[7], t0, best, L.lu_g, sg >= 0.f ? "" : " (not tuned: no factored blocks)");
+                 "d=%d p=%d %s E=%d: tiles %d %d %d %d %d %d %d %d, residual %.4f -> %.4f ms; solve G %d%s%s\n", L.d,
+                 L.p, prec ? "fp32" : "fp64", L.E, L.tile[0], L.tile[1], L.tile[2], L.tile[3], L.tile[4], L.tile[5],
+                 L.tile[6], L.tile[7], t0, best, L.lu_g, sg >= 0.f ? " (ms per G" : " (not tuned: no factored blocks)",
+                 sg >= 0.f ? (std::string(gtimes) + ")").c_str() : "");
     }
     return FR_OK;
 }
@@ -1420,8 +1437,8 @@ extern "C" int fr_set_tiles(fr_ctx *C, int l, int prec, const int *tiles) {
     for (int k = 0; k < 8; ++k)
         if (tiles[k] != 0 && (tiles[k] < 32 || tiles[k] > 256 || tiles[k] % 32))
             return fail(FR_ERR_INVALID_ARG, "CTA size %d: a multiple of 32 in 32..256 (or 0)", tiles[k]);
-    if (tiles[8] != 0 && tiles[8] != 2 && tiles[8] != 4 && tiles[8] != 8)
-        return fail(FR_ERR_INVALID_ARG, "solve G must be 0, 2, 4 or 8");
+    if (tiles[8] != 0 && tiles[8] != 1 && tiles[8] != 2 && tiles[8] != 4 && tiles[8] != 8)
+        return fail(FR_ERR_INVALID_ARG, "solve G must be 0, 1 (bulk-copy kernel), 2, 4 or 8");
     if (prec == 1) TRY(ensure_levels32(C));
     short *t = prec ? C->L32[l].tile : C->L[l].tile;
     for (int k = 0; k < 8; ++k) t[k] = (short)tiles[k];
@@ -1460,7 +1477,7 @@ extern "C" int fr_autotune_load(const char *path) {
             continue;
         bool ok = true;
         for (int i = 0; i < 8; ++i) ok &= t[i] == 0 || (t[i] >= 32 && t[i] <= 256 && t[i] % 32 == 0);
-        ok &= t[8] == 0 || t[8] == 2 || t[8] == 4 || t[8] == 8;
+        ok &= t[8] == 0 || t[8] == 1 || t[8] == 2 || t[8] == 4 || t[8] == 8;
         if (!ok) continue;
         for (int i = 0; i < 8; ++i) v.tile[i] = (short)t[i];
         v.lu_g = (short)t[8];

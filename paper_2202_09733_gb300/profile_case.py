@@ -4,7 +4,8 @@ external profilers (ncu):  python -m paper_2202_09733_gb300.profile_case --case 
 Operations: residual (FP64), residual32 (the FP32 residual of the mixed preconditioner:
 a cycle with no smoothing, one FP32 residual per level), jvp, pmg (one preconditioner
 application, --precision fp64|mixed; its block solves, transfers and residuals can be
-picked out with the profiler's kernel filter), row_step.  The setup (context, blocks and
+picked out with the profiler's kernel filter), row_step (from the same state every run),
+esdirk_step (ESDIRK3 at the 1e-8 Newton tolerance, successive steps).  The setup (context, blocks and
 factors where the operation needs them) runs first; then --reps runs of the operation,
 each followed by a device synchronisation.
 """
@@ -24,10 +25,13 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="tgv3d", choices=["tgv3d", "cylinder_unsteady", "vortex2d"])
     ap.add_argument("--n", type=int, default=32, help="tgv3d: elements per direction")
-    ap.add_argument("--op", default="residual", choices=["residual", "residual32", "jvp", "pmg", "row_step"])
+    ap.add_argument("--op", default="residual",
+                    choices=["residual", "residual32", "jvp", "pmg", "row_step", "esdirk_step"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--reps", type=int, default=4)
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--solve-g", type=int, default=0,
+                    help="block-solve variant on every level (0 default, 1 bulk-copy kernel, 2/4/8 columns in flight)")
     a = ap.parse_args(argv)
     B.build()
     if a.case == "tgv3d":
@@ -39,6 +43,10 @@ def main(argv=None):
     ctx = api.fr_create(W.mesh, W.phys, W.levels)
     if a.autotune:
         api.fr_autotune(ctx, fp64=True, fp32=True, reps=3)
+    if a.solve_g:
+        for l in range(len(W.levels)):
+            for prec in (0, 1):
+                api.fr_set_tiles(ctx, l, api.fr_get_tiles(ctx, l, prec)[:8] + [a.solve_g], precision=prec)
     q = torch.from_numpy(np.ascontiguousarray(W.q0)).cuda()
     R = api.fr_residual(ctx, 0, q)
     v = torch.from_numpy(np.random.default_rng(0).standard_normal(q.shape)).cuda()
@@ -60,6 +68,11 @@ def main(argv=None):
             api.fr_jvp(ctx, q, R, v, 1e-6, c)
         elif a.op == "pmg":
             api.pmg_precondition(ctx, q, R, v)
+        elif a.op == "esdirk_step":
+            A, bb = T.esdirk3()
+            o = api.solve_opts(kdim=30, maxit_gmres=300, max_ptc=40, nsmooth=(2,) * len(W.levels), tol_gmres=1e-2,
+                               tol_newton=1e-8, dtau=dt, inv_dtau_star=1.0 / dt, precision=a.precision)
+            api.esdirk_step(ctx, A, bb, dt, qs, o)
         elif a.op == "row_step":
             g, aa, cc, m = T.ros34pw2()
             o = api.solve_opts(kdim=30, maxit_gmres=300, nsmooth=(2,) * len(W.levels), tol_gmres=1e-6,
@@ -67,12 +80,19 @@ def main(argv=None):
             qq = q.clone()
             api.row_step(ctx, g, aa, cc, m, dt, qq, o)
 
+    qs = q.clone()   # esdirk_step: successive runs advance this state
     if a.op == "residual32":
         api.pmg_setup(ctx, q, (0,) * len(W.levels), c, 1.0 / dt, precision="mixed")
+    from . import _native as N
+    lib = N.load()
+    counts = []
     for _ in range(a.reps):
+        n0 = lib.fr_kernel_launches()
         once()
         torch.cuda.synchronize()
-    print(f"{a.case} {a.op} {a.precision}: {a.reps} runs done")
+        counts.append(int(lib.fr_kernel_launches() - n0))
+    print(f"{a.case} {a.op} {a.precision}: {a.reps} runs done; kernel launches before the runs "
+          f"{int(lib.fr_kernel_launches()) - sum(counts)}, per run {counts}")
     return 0
 
 

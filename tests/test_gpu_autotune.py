@@ -64,12 +64,41 @@ def test_fp32_preconditioner_bits_do_not_depend_on_solve_G():
     Rq = api.fr_residual(G, 0, qg)
     v = torch.from_numpy(np.random.default_rng(2).standard_normal(q.shape)).cuda()
     outs = []
-    for g in (2, 4, 8):
+    for g in (1, 2, 4, 8):
         for l in range(len(lv)):
             api.fr_set_tiles(G, l, [0] * 8 + [g], precision=1)
         api.pmg_setup(G, qg, [2, 2], 10.0, 3.0, precision="mixed")
         outs.append(api.pmg_precondition(G, qg, Rq, v))
-    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    for o in outs[1:]:
+        assert torch.equal(outs[0], o)
+    assert api.fr_kernel_timeouts() == 0
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_block_solve_variants_match_oracle_bitwise(name):
+    """The register kernels (G = 2, 4, 8) and the bulk-copy kernel (G = 1) apply the same
+    fma sequence to every row: the solves agree with each other and the oracle bit for bit."""
+    mesh, lv = CASES[name]
+    ph = w.Physics(mu=0.02, qinf=w.freestream(mesh["d"], 0.3))
+    O = oracle.Oracle(mesh, ph, lv)
+    G = api.fr_create(mesh, ph, lv)
+    X = w.solution_point_coords(mesh, lv[0])
+    q = np.ascontiguousarray(w.prim_to_cons(1 + 0.05 * np.sin(X[0]), [0.3 + 0.1 * np.cos(X[1])] +
+                                            [0.1 * np.sin(X[0] + X[1])] * (mesh["d"] - 1),
+                                            (1 / (1.4 * 0.09)) * np.ones_like(X[0])))
+    qg = torch.from_numpy(q).cuda()
+    M = api.fr_elem_blocks(G, 0, qg, 7.5)
+    perm = api.fr_block_factor(G, 0, M)
+    O.pmg_setup(q, [1], 7.5, 0.0)
+    rhs = np.random.default_rng(4).standard_normal(q.shape)
+    ref = O.block_solve(rhs)
+    outs = []
+    for g in (1, 2, 4, 8):
+        api.fr_set_tiles(G, 0, [0] * 8 + [g])
+        outs.append(api.fr_block_solve(G, 0, M, perm, torch.from_numpy(rhs.copy()).cuda()).cpu().numpy())
+    for o in outs:
+        assert np.array_equal(o, ref)
+    assert api.fr_kernel_timeouts() == 0
 
 
 def test_autotuned_batch_step_is_bit_identical():
@@ -90,3 +119,27 @@ def test_autotuned_batch_step_is_bit_identical():
         res.append(qs)
     for a, b_ in zip(*res):
         assert torch.equal(a, b_)
+
+
+def test_bounded_wait_times_out_and_leaves_the_context_usable():
+    """A stage barrier that nothing completes: the bounded wait gives up, the failure is
+    reported to the host, and the next solve still runs (and is exact)."""
+    mesh, lv = CASES["quad_p4"]
+    ph = w.Physics(mu=0.02, qinf=w.freestream(2, 0.3))
+    G = api.fr_create(mesh, ph, lv)
+    api.fr_kernel_timeouts(clear=True)
+    api.fr_selftest_wait_timeout()
+    assert api.fr_kernel_timeouts(clear=True) == 1
+    assert api.fr_kernel_timeouts() == 0
+    X = w.solution_point_coords(mesh, lv[0])
+    q = np.ascontiguousarray(w.prim_to_cons(1 + 0.05 * np.sin(X[0]), [0.3 + 0.1 * np.cos(X[1]), 0.1 * np.sin(X[0])],
+                                            (1 / (1.4 * 0.09)) * np.ones_like(X[0])))
+    qg = torch.from_numpy(q).cuda()
+    M = api.fr_elem_blocks(G, 0, qg, 7.5)
+    perm = api.fr_block_factor(G, 0, M)
+    rhs = torch.from_numpy(np.random.default_rng(6).standard_normal(q.shape)).cuda()
+    outs = []
+    for g in (1, 2):
+        api.fr_set_tiles(G, 0, [0] * 8 + [g])
+        outs.append(api.fr_block_solve(G, 0, M, perm, rhs.clone()))
+    assert torch.equal(outs[0], outs[1]) and api.fr_kernel_timeouts() == 0
