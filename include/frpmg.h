@@ -273,8 +273,9 @@ int row_step(fr_ctx *ctx, const fr_row_tableau *tab, double dt, double *q, const
  * iteration with c = 1/dtau (inv_dtau_star < 0 selects 1/dtau* = c).  Stops at
  * ||R|| <= tol_rel ||R_0||.  hist: host [max_it+1] residual norms (may be NULL).
  * precision = 1: the FP32 cycle until a pseudo step where FGMRES used all maxit_gmres
- * iterations and ||R|| fell by less than half; from then on the FP64 cycle
- * (stats->prec_switch_it records the step). */
+ * iterations and ||R|| fell by less than half, or the fifth pseudo step in a row that cut
+ * ||R|| by less than 10%; from then on the FP64 cycle (stats->prec_switch_it records the
+ * step). */
 int ptc_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
                const fr_solve_opts *opts, fr_step_stats *stats, double *hist, void *stream);
 

@@ -1204,7 +1204,7 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
     fr_step_stats loc;
     memset(&loc, 0, sizeof loc);
     loc.prec_switch_it = -1;
-    int prec = o->precision;
+    int prec = o->precision, stall = 0;
     TRY(residual(C, 0, q, R, s));
     double r0, rk, dtau = dtau_init;
     TRY(norm2(C, n, R, &r0, s));
@@ -1231,10 +1231,12 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
         double rn;
         TRY(norm2(C, n, R, &rn, s));
         if (!isfinite(rn)) return fail(FR_ERR_NONFINITE, "non-finite residual at pseudo step %d", k);
-        // FP32 preconditioner stalled (FGMRES used every iteration, residual barely moved):
-        // with 1/dtau -> 0 the element blocks grow too ill-conditioned for FP32 LU, so
-        // the rest of the pseudo-time march takes the FP64 cycle
-        if (prec == 1 && o->use_pmg && gs.iters >= o->maxit_gmres && rn > 0.5 * rk) {
+        // FP32 preconditioner stalled (FGMRES used every iteration and the residual fell by
+        // less than half, or five pseudo steps in a row each gained less than 10%): with
+        // 1/dtau -> 0 the element blocks grow too ill-conditioned for FP32 LU, so the rest of
+        // the pseudo-time march takes the FP64 cycle
+        stall = rn > 0.9 * rk ? stall + 1 : 0;
+        if (prec == 1 && o->use_pmg && ((gs.iters >= o->maxit_gmres && rn > 0.5 * rk) || stall >= 5)) {
             prec = 0;
             loc.prec_switch_it = k + 1;
         }
