@@ -195,6 +195,7 @@ def esdirk_guess_compare(api, w, T, np, torch, warm=15, timed=6):
             "gmres_per_step": float(np.mean([s_["n_gmres"] for s_ in sts])),
             "picks_qn_extrap_mlp": [int(sum(s_["guess_pick"][k] for s_ in sts)) for k in range(3)],
             "state_vs_fp64_qn_maxrel": dq,
+            "state_abs_sum": float(q.abs().sum().item()),
         }
     v = out["variants"]
     out["speedup_mixed_extrap_vs_fp64_qn"] = v["fp64_qn"]["s_per_step"] / v["mixed_extrap"]["s_per_step"]

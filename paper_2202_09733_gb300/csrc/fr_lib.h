@@ -27,7 +27,7 @@ struct FrLevelT {
 };
 typedef FrLevelT<double> FrLevel;
 typedef FrLevelT<float> FrLevel32;
-typedef FrLevelT<DualF> FrLevelAD;
+typedef FrLevelT<DualT> FrLevelAD;
 
 struct FrPhysH {
     double gamma, gm1, mu, kappa, c23, qinf[5];
@@ -113,13 +113,14 @@ void frkb_seg_update_x(long long n, int E, const int *ep, int m, const double *y
 void frkb_gather(int rows, int Ei, const double *qi, double *Q, int E, int off, cudaStream_t s);
 void frkb_scatter(int rows, int Ei, const double *Q, int E, int off, double *qi, cudaStream_t s);
 
-// FP32 element blocks by forward-mode differentiation of the residual (kernelsad.cu)
+// FP32 element blocks by forward-mode differentiation of the residual (kernelsad.cu),
+// FR_AD_K columns per residual evaluation
 unsigned long long frkad_launch_count();
 int frkad_upload_tables(const FrTabH *tabs);
-int frkad_residual(const FrLevelAD &L, const FrPhysH &ph, const DualF *q, DualF *R, cudaStream_t s);
-void frkad_init(long long n, const float *q, DualF *qd, cudaStream_t s);          // qd = (q, 0)
-void frkad_seed(const FrLevelAD &L, const int *color, int col, int j, DualF *qd, float seed, cudaStream_t s);
-void frkad_block_column(const FrLevelAD &L, const int *color, int col, int j, const DualF *Rd, double shift,
+int frkad_residual(const FrLevelAD &L, const FrPhysH &ph, const DualT *q, DualT *R, cudaStream_t s);
+void frkad_init(long long n, const float *q, DualT *qd, cudaStream_t s);          // qd = (q, 0)
+void frkad_seed(const FrLevelAD &L, const int *color, int col, int j0, DualT *qd, float seed, cudaStream_t s);
+void frkad_block_column(const FrLevelAD &L, const int *color, int col, int j0, const DualT *Rd, double shift,
                         float *M, cudaStream_t s);
 
 // learned initial guess (mlp.cu)

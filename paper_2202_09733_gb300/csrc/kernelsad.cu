@@ -1,7 +1,8 @@
 // FP32 element-diagonal Jacobian blocks by forward-mode differentiation: the residual
-// kernels run on DualF with derivative seed 1 in degree of freedom j of every element of
-// one colour (elements of a colour share no face), so R.d restricted to each of those
-// elements is column j of its block dR_e/dq_e, exact up to FP32 rounding of each term.
+// kernels run on DualT (FR_AD_K tangents) with tangent t seeded 1 in degree of freedom
+// j0 + t of every element of one colour (elements of a colour share no face), so R.d[t]
+// restricted to each of those elements is column j0 + t of its block dR_e/dq_e, exact up
+// to FP32 rounding of each term.  One residual evaluation gives FR_AD_K columns.
 #include <algorithm>
 #include "fr_device.cuh"
 #include "fr_lib.h"
@@ -29,20 +30,20 @@ int frkad_upload_tables(const FrTabH *tabs) {
 }
 
 template <int D, int P>
-static void residual_ad(const FrLevelAD &L, const FrPhys<float> &ph, const DualF *q, DualF *R, cudaStream_t s) {
+static void residual_ad(const FrLevelAD &L, const FrPhys<float> &ph, const DualT *q, DualT *R, cudaStream_t s) {
     using S = Sh<D, P>;
     const int E = L.E, gx = (E + 127) / 128, gp = (L.npairs + 127) / 128;
-    CNT(); k_interp<D, P, DualF><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, E);
-    CNT(); k_pair_common<D, P, DualF><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.dq, E, ph);
-    CNT(); k_grad_sp<D, P, DualF><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(q, L.dq, L.G, L.Q, E);
-    CNT(); k_grad_fp<D, P, DualF><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
-    CNT(); k_pair_flux<D, P, DualF><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.Qf, L.Sf, L.fn, E, ph);
-    CNT(); k_vflux<D, P, DualF><<<dim3(gx, S::np), 128, 0, s>>>(q, L.Q, L.S, L.Ft, E, ph);
-    CNT(); k_face_ft<D, P, DualF><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(L.Ft, L.Ftf, E);
-    CNT(); k_div<D, P, DualF><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
+    CNT(); k_interp<D, P, DualT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, E);
+    CNT(); k_pair_common<D, P, DualT><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.dq, E, ph);
+    CNT(); k_grad_sp<D, P, DualT><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(q, L.dq, L.G, L.Q, E);
+    CNT(); k_grad_fp<D, P, DualT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
+    CNT(); k_pair_flux<D, P, DualT><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.Qf, L.Sf, L.fn, E, ph);
+    CNT(); k_vflux<D, P, DualT><<<dim3(gx, S::np), 128, 0, s>>>(q, L.Q, L.S, L.Ft, E, ph);
+    CNT(); k_face_ft<D, P, DualT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(L.Ft, L.Ftf, E);
+    CNT(); k_div<D, P, DualT><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
 }
 
-int frkad_residual(const FrLevelAD &L, const FrPhysH &h, const DualF *q, DualF *R, cudaStream_t s) {
+int frkad_residual(const FrLevelAD &L, const FrPhysH &h, const DualT *q, DualT *R, cudaStream_t s) {
     FrPhys<float> ph;
     ph.gamma = (float)h.gamma; ph.gm1 = (float)h.gm1; ph.mu = (float)h.mu; ph.kappa = (float)h.kappa;
     ph.c23 = (float)h.c23;
@@ -65,24 +66,27 @@ int frkad_residual(const FrLevelAD &L, const FrPhysH &h, const DualF *q, DualF *
     return -1;
 }
 
-__global__ void k_ad_init(long long n, const float *q, DualF *qd) {
+__global__ void k_ad_init(long long n, const float *q, DualT *qd) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        qd[i] = DualF(q[i], 0.f);
+        qd[i] = DualT(q[i]);
 }
-void frkad_init(long long n, const float *q, DualF *qd, cudaStream_t s) {
+void frkad_init(long long n, const float *q, DualT *qd, cudaStream_t s) {
     int g = (int)std::min<long long>((n + 255) / 256, 152LL * 32);
     CNT(); k_ad_init<<<g, 256, 0, s>>>(n, q, qd);
 }
-__global__ void k_ad_seed(int E, const int *color, int col, int j, DualF *qd, float seed) {
+// tangent t of dof j0 + t (< nd) of every element of the colour: seed (1) or clear (0)
+__global__ void k_ad_seed(int E, int nd, const int *color, int col, int j0, DualT *qd, float seed) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E || color[e] != col) return;
-    qd[(size_t)j * E + e].d = seed;
+#pragma unroll
+    for (int t = 0; t < FR_AD_K; ++t)
+        if (j0 + t < nd) qd[(size_t)(j0 + t) * E + e].d[t] = seed;
 }
-void frkad_seed(const FrLevelAD &L, const int *color, int col, int j, DualF *qd, float seed, cudaStream_t s) {
-    CNT(); k_ad_seed<<<(L.E + 255) / 256, 256, 0, s>>>(L.E, color, col, j, qd, seed);
+void frkad_seed(const FrLevelAD &L, const int *color, int col, int j0, DualT *qd, float seed, cudaStream_t s) {
+    CNT(); k_ad_seed<<<(L.E + 255) / 256, 256, 0, s>>>(L.E, L.nd, color, col, j0, qd, seed);
 }
-// M[e][j][r] = (r == j ? shift : 0) - dR_r/dq_j for the elements of the colour (tiled)
-__global__ void __launch_bounds__(256) k_ad_column(int E, int nd, const int *color, int col, int j, const DualF *Rd,
+// M[e][j][r] = (r == j ? shift : 0) - dR_r/dq_j for j = j0 + t, t < FR_AD_K (tiled)
+__global__ void __launch_bounds__(256) k_ad_column(int E, int nd, const int *color, int col, int j0, const DualT *Rd,
                                                    float shift, float *M) {
     __shared__ float tile[32][33];
     __shared__ int s_col[32];
@@ -92,25 +96,29 @@ __global__ void __launch_bounds__(256) k_ad_column(int E, int nd, const int *col
         s_col[tx] = e < E && color[e] == col;
     }
     __syncthreads();
-    for (int r0 = 0; r0 < nd; r0 += 32) {
-        for (int rr = ty; rr < 32; rr += 8) {
-            int r = r0 + rr, e = e0 + tx;
-            float val = 0.f;
-            if (r < nd && e < E && s_col[tx]) {
-                float dr = Rd[(size_t)r * E + e].d;
-                val = (r == j) ? shift - dr : -dr;
+    for (int t = 0; t < FR_AD_K; ++t) {
+        int j = j0 + t;
+        if (j >= nd) break;
+        for (int r0 = 0; r0 < nd; r0 += 32) {
+            for (int rr = ty; rr < 32; rr += 8) {
+                int r = r0 + rr, e = e0 + tx;
+                float val = 0.f;
+                if (r < nd && e < E && s_col[tx]) {
+                    float dr = Rd[(size_t)r * E + e].d[t];
+                    val = (r == j) ? shift - dr : -dr;
+                }
+                tile[rr][tx] = val;
             }
-            tile[rr][tx] = val;
+            __syncthreads();
+            for (int ee = ty; ee < 32; ee += 8) {
+                int e = e0 + ee, r = r0 + tx;
+                if (e < E && s_col[ee] && r < nd) M[((size_t)e * nd + j) * nd + r] = tile[tx][ee];
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int ee = ty; ee < 32; ee += 8) {
-            int e = e0 + ee, r = r0 + tx;
-            if (e < E && s_col[ee] && r < nd) M[((size_t)e * nd + j) * nd + r] = tile[tx][ee];
-        }
-        __syncthreads();
     }
 }
-void frkad_block_column(const FrLevelAD &L, const int *color, int col, int j, const DualF *Rd, double shift, float *M,
-                        cudaStream_t s) {
-    CNT(); k_ad_column<<<(L.E + 31) / 32, 256, 0, s>>>(L.E, L.nd, color, col, j, Rd, (float)shift, M);
+void frkad_block_column(const FrLevelAD &L, const int *color, int col, int j0, const DualT *Rd, double shift,
+                        float *M, cudaStream_t s) {
+    CNT(); k_ad_column<<<(L.E + 31) / 32, 256, 0, s>>>(L.E, L.nd, color, col, j0, Rd, (float)shift, M);
 }

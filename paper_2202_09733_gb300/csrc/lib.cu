@@ -64,7 +64,7 @@ struct fr_ctx {
     FrLevel32 L32[FRL_MAXLEV];    // FP32 copies of the levels (mixed preconditioner)
     FrLevelAD LA[FRL_MAXLEV];     // forward-mode (FP32 dual) residual workspace for the FP32 blocks
     int have32, haveAD;
-    DualF *qd, *Rd;
+    DualT *qd, *Rd;
     int ncolor;
     int *color;
     int *info;
@@ -452,12 +452,12 @@ static int elem_blocks_ad(fr_ctx *C, int l, const float *q, double shift, float 
     FrLevelAD &A = C->LA[l];
     frkad_init(A.ndof, q, C->qd, s);
     for (int col = 0; col < C->ncolor; ++col)
-        for (int j = 0; j < A.nd; ++j) {
-            frkad_seed(A, C->color, col, j, C->qd, 1.f, s);
+        for (int j0 = 0; j0 < A.nd; j0 += FR_AD_K) {
+            frkad_seed(A, C->color, col, j0, C->qd, 1.f, s);
             if (frkad_residual(A, C->ph, C->qd, C->Rd, s) != 0)
                 return fail(FR_ERR_UNIMPLEMENTED, "no kernel for d=%d p=%d", C->d, A.p);
-            frkad_block_column(A, C->color, col, j, C->Rd, shift, M, s);
-            frkad_seed(A, C->color, col, j, C->qd, 0.f, s);
+            frkad_block_column(A, C->color, col, j0, C->Rd, shift, M, s);
+            frkad_seed(A, C->color, col, j0, C->qd, 0.f, s);
         }
     CKLAUNCH();
     return FR_OK;
