@@ -55,6 +55,18 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, ws, device):
+    """The largest of every rank's x (replica timings: the job takes as long as its
+    slowest rank); x itself on a single rank."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -303,10 +315,7 @@ def gpu_arm(args):
     launches = lib.fr_kernel_launches() - n0
     clocks = clk.stop()
     t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
-    if ws > 1:
-        tt = torch.tensor([t_step], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(t_step, ws, "cuda")
 
     q_mixed = q.clone()
 
