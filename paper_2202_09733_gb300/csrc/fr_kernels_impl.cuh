@@ -350,14 +350,50 @@ __global__ void __launch_bounds__(256) k_lu_factor_blocked(FRT *M, int *perm, in
                     if (c < kb) { col[c] = u[c]; U12[(size_t)(j - r0) * LU_PB + c] = u[c]; }
             }
             __syncthreads();
-            // 6. trailing update in place, one k at a time
-            for (int t = tid; t < mt * mt; t += nt) {
-                int jj = t / mt, i = r0 + (t - jj * mt);
-                FRT *pa = A + (size_t)(r0 + jj) * nd + i;
-                FRT a = *pa;
-                const FRT *uj = U12 + (size_t)jj * LU_PB;
-                for (int c = 0; c < kb; ++c) a = fma(-Pn[(size_t)c * nd + i], uj[c], a);
-                *pa = a;
+            // 6. trailing update in place, one k at a time.  Register tiles of 4 rows x 4
+            //    columns: consecutive threads take consecutive row tiles of one column
+            //    tile, so the multipliers come as one 4-wide shared load per k and the
+            //    U12 values are broadcasts; each entry still takes its fmas in ascending k.
+            if (mt % 4 == 0 && nd % 4 == 0 && r0 % 4 == 0) {
+                int ntr = mt / 4, ntile = ntr * ntr;
+                for (int t = tid; t < ntile; t += nt) {
+                    int tc = t / ntr, i0 = r0 + 4 * (t - tc * ntr), j0 = 4 * tc;
+                    FRT acc[4][4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) acc[q][r] = A[(size_t)(r0 + j0 + q) * nd + i0 + r];
+                    for (int c = 0; c < kb; ++c) {
+                        const FRT *lc = Pn + (size_t)c * nd + i0;
+                        FRT l[4], u[4];
+                        if (sizeof(FRT) == 4) {
+                            float4 v = *reinterpret_cast<const float4 *>(lc);
+                            l[0] = v.x; l[1] = v.y; l[2] = v.z; l[3] = v.w;
+                        } else {
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) l[r] = lc[r];
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) u[q] = U12[(size_t)(j0 + q) * LU_PB + c];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) acc[q][r] = fma(-l[r], u[q], acc[q][r]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) A[(size_t)(r0 + j0 + q) * nd + i0 + r] = acc[q][r];
+                }
+            } else {
+                for (int t = tid; t < mt * mt; t += nt) {
+                    int jj = t / mt, i = r0 + (t - jj * mt);
+                    FRT *pa = A + (size_t)(r0 + jj) * nd + i;
+                    FRT a = *pa;
+                    const FRT *uj = U12 + (size_t)jj * LU_PB;
+                    for (int c = 0; c < kb; ++c) a = fma(-Pn[(size_t)c * nd + i], uj[c], a);
+                    *pa = a;
+                }
             }
         }
         __syncthreads();
