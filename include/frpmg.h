@@ -279,6 +279,16 @@ int row_step(fr_ctx *ctx, const fr_row_tableau *tab, double dt, double *q, const
 int ptc_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
                const fr_solve_opts *opts, fr_step_stats *stats, double *hist, void *stream);
 
+/* The pMG nonlinear solver for steady problems (Sec. 3.1, Eqs. 11-16), the paper's
+ * comparison method: each iteration is one nonlinear V-cycle of pseudo-time marching on
+ * R(q) = 0 from the current state — the preconditioner's cycle with X = R(q), which turns
+ * its equation into the backward-Euler pseudo step R(qh) - c (qh - q) = 0, c = 1/dtau —
+ * then q <- qh; element blocks at every iteration's q; dtau by the SER rule of ptc_steady.
+ * Uses opts->nlevels, nsmooth, inv_dtau_star (< 0: = c); FP64 only (precision 0).
+ * q: device, updated in place; hist: host [max_it+1] residual norms (may be NULL). */
+int pmg_solve_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
+                     const fr_solve_opts *opts, fr_step_stats *stats, double *hist, void *stream);
+
 /* ---------------------------------------------------------------- autotuner
  * Launch shapes (not in the paper; no result bit depends on them): the CTA size (elements
  * per CTA tile, 64/128/256) of each of the 8 kernels of the residual, per level and

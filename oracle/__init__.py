@@ -69,6 +69,8 @@ def lib():
                                   C.c_void_p, C.c_void_p]
         L.or_ptc_steady.argtypes = [C.c_void_p, PD, C.c_double, C.c_double, C.c_double, C.c_int,
                                     C.c_void_p, C.c_void_p, PD]
+        L.or_pmg_steady.argtypes = [C.c_void_p, PD, C.c_double, C.c_double, C.c_double, C.c_int,
+                                    C.c_void_p, C.c_void_p, PD]
         L.or_table.argtypes = [C.c_int, C.c_int, PD]
         L.or_transfer.argtypes = [C.c_int, C.c_int, PD, PD]
         L.or_jacobian.argtypes = [C.c_void_p, C.c_int, PD]
@@ -245,6 +247,15 @@ class Oracle:
         st = StepStats()
         lib().or_row_step(self.h, len(m), gam, _d(a), _d(c), _d(m), dt, _d(q), C.byref(opts), C.byref(st))
         return q, dict(n_ptc=st.n_ptc, n_gmres=st.n_gmres, converged=st.converged, final_res=st.final_res)
+
+    def pmg_steady(self, q, dtau_init, dtau_max, tol_rel, max_it, opts):
+        """The pMG nonlinear solver (one nonlinear V-cycle per iteration, Sec. 3.1)."""
+        q = np.ascontiguousarray(q, dtype=np.float64).copy()
+        st = StepStats()
+        hist = np.zeros(max_it + 1)
+        lib().or_pmg_steady(self.h, _d(q), dtau_init, dtau_max, tol_rel, max_it, C.byref(opts), C.byref(st),
+                            _d(hist))
+        return q, dict(n_ptc=st.n_ptc, converged=st.converged, final_res=st.final_res, hist=hist[:st.n_ptc + 1])
 
     def ptc_steady(self, q, dtau_init, dtau_max, tol_rel, max_it, opts):
         q = np.ascontiguousarray(q, dtype=np.float64).copy()

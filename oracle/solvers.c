@@ -399,3 +399,36 @@ int or_ptc_steady(or_ctx *C, double *q, double dtau_init, double dtau_max, doubl
     free(R); free(dq);
     return st->converged ? 0 : 1;
 }
+
+/* The pMG nonlinear solver for steady problems (Sec. 3.1, Eqs. 11-16): every iteration is
+ * one nonlinear V-cycle of pseudo-time marching on R(q) = 0 started from the current
+ * state.  The preconditioner's cycle solves 0 = X + R(qh) - c (qh - q) - R(q); with
+ * X = R(q) that is the backward-Euler pseudo step R(qh) - c (qh - q) = 0, c = 1/dtau, so the
+ * iteration is q <- q + P(q, R(q), R(q)); dtau follows the same SER rule as the PTC
+ * driver.  Element blocks are formed at every iteration's q. */
+int or_pmg_steady(or_ctx *C, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
+                  const or_solve_opts *o, or_step_stats *st, double *hist) {
+    size_t N = vlen(C, 0);
+    double *R = malloc(sizeof(double) * N), *Y = malloc(sizeof(double) * N);
+    memset(st, 0, sizeof(*st));
+    or_residual(C, 0, q, R);
+    double r0 = sqrt(dot(N, R, R)), rk = r0, dtau = dtau_init;
+    if (hist) hist[0] = r0;
+    for (int k = 0; k < max_it; ++k) {
+        if (rk <= tol_rel * r0) break;
+        double c = 1.0 / dtau;
+        or_pmg_setup(C, q, o->nlev, o->nsmooth, c, o->inv_dtau_star < 0 ? c : o->inv_dtau_star);
+        or_pmg_apply(C, q, R, R, Y);
+        for (size_t t = 0; t < N; ++t) q[t] = q[t] + Y[t];
+        or_residual(C, 0, q, R);
+        double rn = sqrt(dot(N, R, R));
+        dtau = fmin(dtau * (rk / rn), dtau_max);
+        rk = rn;
+        st->n_ptc++;
+        if (hist) hist[k + 1] = rn;
+    }
+    st->final_res = rk / r0;
+    st->converged = rk <= tol_rel * r0;
+    free(R); free(Y);
+    return st->converged ? 0 : 1;
+}

@@ -25,7 +25,7 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_last_error", "fr_kernel_launches", "fr
            "fr_set_mlp", "fr_reset_history", "fr_guess_features", "fr_batch_create", "fr_batch_destroy",
            "fr_batch_info", "fr_batch_set_graphs", "fr_batch_residual", "fr_batch_esdirk_step", "fr_autotune",
            "fr_get_tiles", "fr_set_tiles", "fr_autotune_save", "fr_autotune_load", "fr_batch_autotune", "fr_kernel_timeouts",
-           "fr_selftest_wait_timeout"]
+           "fr_selftest_wait_timeout", "pmg_solve_steady"]
 
 
 class MeshDesc(C.Structure):
@@ -134,6 +134,8 @@ def load(path: str = LIB_PATH):
         "fr_batch_autotune": ([VP, C.c_int, C.c_int, C.c_char_p, C.c_int], C.c_int),
         "fr_kernel_timeouts": ([C.c_int], C.c_int),
         "fr_selftest_wait_timeout": ([], C.c_int),
+        "pmg_solve_steady": ([VP, VP, C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(SolveOpts),
+                              C.POINTER(StepStats), PD, VP], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

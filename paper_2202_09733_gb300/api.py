@@ -234,6 +234,19 @@ def ptc_steady(ctx, q, dtau_init, dtau_max, tol_rel, max_it, opts, stream=None):
     return out
 
 
+def pmg_solve_steady(ctx, q, dtau_init, dtau_max, tol_rel, max_it, opts, stream=None):
+    """The pMG nonlinear solver (one nonlinear V-cycle per iteration)."""
+    hist = np.zeros(max_it + 1)
+    st = N.StepStats()
+    rc = N.load().pmg_solve_steady(ctx.handle, _dev(q), float(dtau_init), float(dtau_max), float(tol_rel),
+                                   int(max_it), C.byref(opts), C.byref(st), hist.ctypes.data_as(N.PD),
+                                   _stream(stream))
+    N.check(rc, "pmg_solve_steady", allow=(-4,))
+    out = _stats(st)
+    out["hist"] = hist[:st.n_ptc + 1]
+    return out
+
+
 class MLP:
     """Per-element BF16 network of the Newton initial guess (libfrpmg mlp_*)."""
 

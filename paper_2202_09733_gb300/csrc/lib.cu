@@ -75,6 +75,8 @@ struct fr_ctx {
     int pmg_ready, pmg_nlev, pmg_prec, nsmooth[FRL_MAXLEV];
     double pmg_c, pmg_ids, pmg_qref[5];
     double pmg_gain;   // mixed cycle: last measured max_v ||Y_v||_inf / qref_v per ||X||_inf
+    const double *q32_of;   // q whose FP32 copy and residual q32/Rq32 hold (NULL: none); set
+                            // only while an FGMRES solve keeps q fixed
     double *ymax;
     PmgBuf<double> p64;
     PmgBuf<float> p32;
@@ -700,8 +702,10 @@ static int pmg_apply(fr_ctx *C, const double *q, const double *Rq, const double 
     }
     PmgBuf<float> &P = C->p32;
     if (frk32_absmax(n, X, C->xmax, s) != 0) return fail(FR_ERR_CUDA, "absmax");
-    frk32_d2f(n, q, C->q32, s);
-    TRY(residual_t<float>(C, 0, C->q32, C->Rq32, s));
+    if (C->q32_of != q) {
+        frk32_d2f(n, q, C->q32, s);
+        TRY(residual_t<float>(C, 0, C->q32, C->Rq32, s));
+    }
     double want = kMixedAlpha, target = want / C->pmg_gain;
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (attempt) target = want / C->pmg_gain;
@@ -761,8 +765,21 @@ static int gmres_alloc(fr_ctx *C, int kdim) {
     return FR_OK;
 }
 
+static int gmres_(fr_ctx *C, const double *q, const double *Rq, const double *b, double *x, const fr_gmres_opts *o,
+                  fr_gmres_stats *st, cudaStream_t s);
+
+// q stays fixed through one FGMRES solve, so the FP32 cycle's copy of q and its FP32
+// residual are formed by the first preconditioner application and reused by the rest
 static int gmres(fr_ctx *C, const double *q, const double *Rq, const double *b, double *x, const fr_gmres_opts *o,
                  fr_gmres_stats *st, cudaStream_t s) {
+    C->q32_of = nullptr;
+    int rc = gmres_(C, q, Rq, b, x, o, st, s);
+    C->q32_of = nullptr;
+    return rc;
+}
+
+static int gmres_(fr_ctx *C, const double *q, const double *Rq, const double *b, double *x, const fr_gmres_opts *o,
+                  fr_gmres_stats *st, cudaStream_t s) {
     int K = o->kdim;
     TRY(gmres_alloc(C, K));
     long long n = C->L[0].ndof;
@@ -788,6 +805,7 @@ static int gmres(fr_ctx *C, const double *q, const double *Rq, const double *b, 
             const double *zj;
             if (o->use_pmg) {
                 TRY(pmg_apply(C, q, Rq, C->V[j], C->Z[j], s));
+                if (C->pmg_prec == 1) C->q32_of = q;
                 double zn;
                 TRY(norm2(C, n, C->Z[j], &zn, s));
                 if (!(zn > 0.0) || !isfinite(zn)) return fail(FR_ERR_NONFINITE, "preconditioner output norm %g", zn);
@@ -1249,6 +1267,57 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
     loc.converged = rk <= tol_rel * r0;
     if (st) *st = loc;
     return loc.converged ? FR_OK : fail(FR_ERR_NOT_CONVERGED, "steady PTC stopped at %g relative residual", loc.final_res);
+}
+
+// The pMG nonlinear solver for steady problems (Sec. 3.1, Eqs. 11-16): one nonlinear
+// V-cycle per iteration.  The preconditioner's cycle solves 0 = X + R(qh) - c (qh - q) -
+// R(q); with X = R(q) that is the backward-Euler pseudo step R(qh) - c (qh - q) = 0, so an
+// iteration is q <- q + P(q, R(q), R(q)) with c = 1/dtau and the SER rule of ptc_steady.
+extern "C" int pmg_solve_steady(fr_ctx *C, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
+                                const fr_solve_opts *o, fr_step_stats *st, double *hist, void *stream) {
+    if (!C || !q || !o) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    if (!(dtau_init > 0.0) || !(dtau_max >= dtau_init) || max_it < 0) return fail(FR_ERR_INVALID_ARG, "bad pseudo-time parameters");
+    if (o->nlevels < 1 || o->nlevels > C->nlev) return fail(FR_ERR_INVALID_ARG, "nlevels outside 1..%d", C->nlev);
+    if (o->precision != 0)
+        return fail(FR_ERR_UNIMPLEMENTED, "the nonlinear pMG solver runs the FP64 cycle (the FP32 cycle is scaled for "
+                                          "preconditioning)");
+    cudaStream_t s = S_(stream);
+    TRY(stepper_alloc(C, 2));
+    long long n = C->L[0].ndof;
+    double *R = C->stv[0], *Y = C->stv[1];
+    fr_step_stats loc;
+    memset(&loc, 0, sizeof loc);
+    loc.prec_switch_it = -1;
+    TRY(residual(C, 0, q, R, s));
+    double r0, rk, dtau = dtau_init;
+    TRY(norm2(C, n, R, &r0, s));
+    rk = r0;
+    if (hist) hist[0] = r0;
+    for (int k = 0; k < max_it; ++k) {
+        if (rk <= tol_rel * r0) break;
+        double c = 1.0 / dtau;
+        fr_pmg_opts po;
+        po.nlevels = o->nlevels;
+        for (int l = 0; l < 4; ++l) po.nsmooth[l] = o->nsmooth[l];
+        po.c = c;
+        po.inv_dtau_star = o->inv_dtau_star < 0 ? c : o->inv_dtau_star;
+        po.precision = 0;
+        TRY(pmg_setup_(C, q, &po, s));
+        TRY(pmg_apply(C, q, R, R, Y, s));
+        frk64_add(n, q, Y, q, s);
+        TRY(residual(C, 0, q, R, s));
+        double rn;
+        TRY(norm2(C, n, R, &rn, s));
+        if (!isfinite(rn)) return fail(FR_ERR_NONFINITE, "non-finite residual at iteration %d", k);
+        dtau = fmin(dtau * (rk / rn), dtau_max);
+        rk = rn;
+        loc.n_ptc++;
+        if (hist) hist[k + 1] = rn;
+    }
+    loc.final_res = rk / r0;
+    loc.converged = rk <= tol_rel * r0;
+    if (st) *st = loc;
+    return loc.converged ? FR_OK : fail(FR_ERR_NOT_CONVERGED, "pMG solver stopped at %g relative residual", loc.final_res);
 }
 
 // -------------------------------------------------------------------- autotuner

@@ -340,3 +340,23 @@ def test_ptc_steady_converged_state():
             assert st["prec_switch_it"] > 0, st
         assert np.linalg.norm(O.residual(qg.cpu().numpy())) <= tol * r0, prec
         assert relerr(qg, q_or) <= state_tol, prec
+
+
+def test_pmg_solver_steady_matches_oracle():
+    """The pMG nonlinear solver (one FP64 V-cycle per iteration): the GPU iterates are the
+    oracle's (the cycle is bit for bit; the pseudo step follows norms that may differ in the
+    last bit, so the states are held to 1e-11), for one-level element-Jacobi steps and for
+    two-level cycles."""
+    W = w.cylinder_steady(nr=6, nt=12, p=2, levels=[2, 1], mach=0.2, re=40)
+    O = oracle.Oracle(W.mesh, W.phys, W.levels)
+    G = api.fr_create(W.mesh, W.phys, W.levels)
+    for nsm, ids, its in (((1,), 0.0, 3), ((2, 2), -1.0, 6)):
+        q_or, st_or = O.pmg_steady(W.q0, 1e-3, 1e-3, 0.0, its, O.opts(nsmooth=nsm, inv_dtau_star=ids))
+        go = api.solve_opts(nsmooth=nsm, inv_dtau_star=ids)
+        qg = dev(W.q0)
+        st = api.pmg_solve_steady(G, qg, 1e-3, 1e-3, 0.0, its, go)
+        assert st["n_ptc"] == st_or["n_ptc"] == its
+        assert relerr(qg, q_or) <= 1e-11, (nsm, relerr(qg, q_or))
+        assert np.allclose(st["hist"], st_or["hist"], rtol=1e-11)
+    with pytest.raises(Exception, match="FP64"):
+        api.pmg_solve_steady(G, dev(W.q0), 1e-3, 1e-3, 0.0, 1, api.solve_opts(nsmooth=(2, 2), precision="mixed"))
