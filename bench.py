@@ -165,7 +165,7 @@ def esdirk_guess_compare(api, w, T, np, torch, warm=15, timed=6):
     paper): the plain FP64 method (guess q^n, the paper's) against the mixed preconditioner
     with the initial-guess candidates.  Each variant runs `warm` steps from the same state
     (the history and the network's training data) and then `timed` steps, timed with CUDA
-    events."""
+    events.  fp64_ej_qn is the paper's JFNK-EJ baseline (element-Jacobi preconditioner)."""
     import math
     wl = w.cylinder_unsteady()
     A, b = T.esdirk3()
@@ -174,7 +174,8 @@ def esdirk_guess_compare(api, w, T, np, torch, warm=15, timed=6):
            "warm_steps": warm, "timed_steps": timed, "variants": {}}
     ref = None
     for name, prec, guess, train in (("fp64_qn", "fp64", "qn", 0), ("mixed_qn", "mixed", "qn", 0),
-                                     ("mixed_extrap", "mixed", "extrap", 0), ("mixed_mlp", "mixed", "mlp", 10)):
+                                     ("mixed_extrap", "mixed", "extrap", 0), ("mixed_mlp", "mixed", "mlp", 10),
+                                     ("fp64_ej_qn", "fp64", "qn", 0)):
         G = api.fr_create(wl.mesh, wl.phys, wl.levels)
         if guess == "mlp":
             K0, O = api.fr_mlp_dims(G)
@@ -184,9 +185,13 @@ def esdirk_guess_compare(api, w, T, np, torch, warm=15, timed=6):
                  np.zeros(H), rng.standard_normal((O, H)) / math.sqrt(H) * 0.1, np.zeros(O)]
             net = api.MLP(K0, H, O, np.concatenate([x.reshape(-1) for x in P]).astype(np.float32))
             api.fr_set_mlp(G, net)
-        o = api.solve_opts(kdim=30, maxit_gmres=300, max_ptc=40, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-8,
-                           dtau=wl.dt, inv_dtau_star=1.0 / wl.dt, precision=prec, guess=guess, train_iters=train,
-                           train_batch=4096, lr=1e-3)
+        # "_ej": the paper's JFNK-EJ baseline, the element-Jacobi preconditioner (one fine
+        # pseudo step with 1/dtau* = 0: the pMG cycle's special case)
+        ej = name.endswith("_ej_qn")
+        o = api.solve_opts(kdim=30, maxit_gmres=300 if not ej else 3000, max_ptc=40,
+                           nsmooth=(2, 2) if not ej else (1,), tol_gmres=1e-2, tol_newton=1e-8,
+                           dtau=wl.dt, inv_dtau_star=1.0 / wl.dt if not ej else 0.0, precision=prec, guess=guess,
+                           train_iters=train, train_batch=4096, lr=1e-3)
         q = torch.from_numpy(np.ascontiguousarray(wl.q0)).cuda()
         for _ in range(warm):
             api.esdirk_step(G, A, b, wl.dt, q, o)
@@ -212,6 +217,7 @@ def esdirk_guess_compare(api, w, T, np, torch, warm=15, timed=6):
     v = out["variants"]
     out["speedup_mixed_extrap_vs_fp64_qn"] = v["fp64_qn"]["s_per_step"] / v["mixed_extrap"]["s_per_step"]
     out["speedup_mixed_mlp_vs_fp64_qn"] = v["fp64_qn"]["s_per_step"] / v["mixed_mlp"]["s_per_step"]
+    out["speedup_fp64_pmg_vs_fp64_ej"] = v["fp64_ej_qn"]["s_per_step"] / v["fp64_qn"]["s_per_step"]
     return out
 
 
@@ -248,6 +254,22 @@ def batched_step(api, w, T, np, torch, N):
                      "gmres_total": int(sum(s_["n_gmres"] for s_ in st)),
                      "kernel_launches": int(N.load().fr_kernel_launches() - n0)}
     return out
+
+
+def run_extras_in_child():
+    """The ESDIRK guess comparison and the batched step, in a child process of their own
+    (a clean library state, and a failure there cannot take the main measurement down)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import numpy as np, torch, bench; "
+            "from paper_2202_09733_gb300 import api, workloads as w, tableaux as T, _native as N; "
+            "torch.cuda.set_device(0); "
+            "out = {'esdirk_cylinder': bench.esdirk_guess_compare(api, w, T, np, torch), "
+            "'batched_vortex': bench.batched_step(api, w, T, np, torch, N)}; "
+            "print('EXTRAS ' + json.dumps(out))") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    for line in r.stdout.splitlines():
+        if line.startswith("EXTRAS "):
+            return json.loads(line[len("EXTRAS "):])
+    return {"extras_error": (r.stderr or r.stdout)[-2000:]}
 
 
 def gpu_arm(args):
@@ -365,8 +387,7 @@ def gpu_arm(args):
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        extras["esdirk_cylinder"] = esdirk_guess_compare(api, w, T, np, torch)
-        extras["batched_vortex"] = batched_step(api, w, T, np, torch, N)
+        extras = run_extras_in_child()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -350,13 +350,15 @@ def test_pmg_solver_steady_matches_oracle():
     W = w.cylinder_steady(nr=6, nt=12, p=2, levels=[2, 1], mach=0.2, re=40)
     O = oracle.Oracle(W.mesh, W.phys, W.levels)
     G = api.fr_create(W.mesh, W.phys, W.levels)
+    dtau = 0.1 * W.mesh["h_min"] / (1.0 + 1.0 / 0.2)    # the pseudo step of the PTC tests, held fixed
     for nsm, ids, its in (((1,), 0.0, 3), ((2, 2), -1.0, 6)):
-        q_or, st_or = O.pmg_steady(W.q0, 1e-3, 1e-3, 0.0, its, O.opts(nsmooth=nsm, inv_dtau_star=ids))
+        q_or, st_or = O.pmg_steady(W.q0, dtau, dtau, 0.0, its, O.opts(nsmooth=nsm, inv_dtau_star=ids))
+        assert np.all(np.isfinite(q_or))
         go = api.solve_opts(nsmooth=nsm, inv_dtau_star=ids)
         qg = dev(W.q0)
-        st = api.pmg_solve_steady(G, qg, 1e-3, 1e-3, 0.0, its, go)
+        st = api.pmg_solve_steady(G, qg, dtau, dtau, 0.0, its, go)
         assert st["n_ptc"] == st_or["n_ptc"] == its
         assert relerr(qg, q_or) <= 1e-11, (nsm, relerr(qg, q_or))
         assert np.allclose(st["hist"], st_or["hist"], rtol=1e-11)
     with pytest.raises(Exception, match="FP64"):
-        api.pmg_solve_steady(G, dev(W.q0), 1e-3, 1e-3, 0.0, 1, api.solve_opts(nsmooth=(2, 2), precision="mixed"))
+        api.pmg_solve_steady(G, dev(W.q0), dtau, dtau, 0.0, 1, api.solve_opts(nsmooth=(2, 2), precision="mixed"))

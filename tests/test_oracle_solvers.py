@@ -218,7 +218,7 @@ def test_library_tableaux_match_oracle_tableaux():
 def test_pmg_solver_one_level_step_is_element_jacobi():
     W = w.cylinder_steady(nr=6, nt=12, p=2, levels=[2, 1], mach=0.2, re=40)
     O = oracle.Oracle(W.mesh, W.phys, W.levels)
-    dtau = 1e-3
+    dtau = 0.1 * W.mesh["h_min"] / (1.0 + 1.0 / 0.2)
     opts = O.opts(nsmooth=(1,), inv_dtau_star=0.0)
     q1, st = O.pmg_steady(W.q0, dtau, dtau, 0.0, 1, opts)
     assert st["n_ptc"] == 1
