@@ -279,6 +279,17 @@ int row_step(fr_ctx *ctx, const fr_row_tableau *tab, double dt, double *q, const
 int ptc_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, double tol_rel, int max_it,
                const fr_solve_opts *opts, fr_step_stats *stats, double *hist, void *stream);
 
+/* Checkpoint of a time-stepping run's library-side state (the paper resumes runs from
+ * saved solutions, Sec. 4): the learned guess's three converged states and training ring,
+ * and (mlp != NULL) the network's weights and Adam state.  The caller keeps q, t and the
+ * step count beside it; launch shapes have their own file (fr_autotune_save).  Loading
+ * into a context of the same mesh and levels, with a network of the same sizes, and
+ * stepping on reproduces the uninterrupted run bit for bit.  buf: host memory of at least
+ * fr_checkpoint_size bytes; save and load synchronise the device. */
+int fr_checkpoint_size(const fr_ctx *ctx, const fr_mlp *mlp, long long *bytes);
+int fr_checkpoint_save(const fr_ctx *ctx, const fr_mlp *mlp, void *buf, long long bytes);
+int fr_checkpoint_load(fr_ctx *ctx, fr_mlp *mlp, const void *buf, long long bytes);
+
 /* The pMG nonlinear solver for steady problems (Sec. 3.1, Eqs. 11-16), the paper's
  * comparison method: each iteration is one nonlinear V-cycle of pseudo-time marching on
  * R(q) = 0 from the current state — the preconditioner's cycle with X = R(q), which turns

@@ -25,7 +25,8 @@ EXPORTS = ["fr_create", "fr_destroy", "fr_last_error", "fr_kernel_launches", "fr
            "fr_set_mlp", "fr_reset_history", "fr_guess_features", "fr_batch_create", "fr_batch_destroy",
            "fr_batch_info", "fr_batch_set_graphs", "fr_batch_residual", "fr_batch_esdirk_step", "fr_autotune",
            "fr_get_tiles", "fr_set_tiles", "fr_autotune_save", "fr_autotune_load", "fr_batch_autotune", "fr_kernel_timeouts",
-           "fr_selftest_wait_timeout", "pmg_solve_steady"]
+           "fr_selftest_wait_timeout", "pmg_solve_steady", "fr_checkpoint_size", "fr_checkpoint_save",
+           "fr_checkpoint_load"]
 
 
 class MeshDesc(C.Structure):
@@ -136,6 +137,9 @@ def load(path: str = LIB_PATH):
         "fr_selftest_wait_timeout": ([], C.c_int),
         "pmg_solve_steady": ([VP, VP, C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(SolveOpts),
                               C.POINTER(StepStats), PD, VP], C.c_int),
+        "fr_checkpoint_size": ([VP, VP, C.POINTER(C.c_longlong)], C.c_int),
+        "fr_checkpoint_save": ([VP, VP, VP, C.c_longlong], C.c_int),
+        "fr_checkpoint_load": ([VP, VP, VP, C.c_longlong], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -354,6 +354,23 @@ def fr_autotune_load(path):
     N.check(N.load().fr_autotune_load(str(path).encode()), "fr_autotune_load")
 
 
+def fr_checkpoint_save(ctx, mlp=None) -> bytes:
+    """The library-side state of a time-stepping run (history, training ring, network)."""
+    lib = N.load()
+    h = mlp.handle if mlp is not None else None
+    n = C.c_longlong()
+    N.check(lib.fr_checkpoint_size(ctx.handle, h, C.byref(n)), "fr_checkpoint_size")
+    buf = C.create_string_buffer(n.value)
+    N.check(lib.fr_checkpoint_save(ctx.handle, h, buf, n.value), "fr_checkpoint_save")
+    return buf.raw
+
+
+def fr_checkpoint_load(ctx, data: bytes, mlp=None):
+    buf = C.create_string_buffer(data, len(data))
+    N.check(N.load().fr_checkpoint_load(ctx.handle, mlp.handle if mlp is not None else None, buf, len(data)),
+            "fr_checkpoint_load")
+
+
 def fr_reset_history(ctx):
     N.check(N.load().fr_reset_history(ctx.handle), "fr_reset_history")
 

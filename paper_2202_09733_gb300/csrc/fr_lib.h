@@ -139,3 +139,6 @@ int frkmlp_forward(fr_mlp *M, int B, const unsigned short *X, float *Y, cudaStre
 int frkmlp_dims(const fr_mlp *M, int *in, int *hid, int *out);
 int frkmlp_var_stats(int nv, long long per, const double *a, const double *b, const double *qinf_dev, double *part,
                      double *out_dev, cudaStream_t s);
+long long frkmlp_state_floats(const fr_mlp *M);
+int frkmlp_state_save(const fr_mlp *M, int *dims4, float *buf);
+int frkmlp_state_load(fr_mlp *M, const int *dims4, const float *buf);

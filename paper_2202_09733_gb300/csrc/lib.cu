@@ -1269,6 +1269,99 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
     return loc.converged ? FR_OK : fail(FR_ERR_NOT_CONVERGED, "steady PTC stopped at %g relative residual", loc.final_res);
 }
 
+// ------------------------------------------------------------------ checkpoints
+// Library-side state of a time-stepping run: the learned guess's converged-state history
+// and training ring, and the network's weights and Adam state.  Layout (host buffer):
+// a header of 24 int64 (magic, version, sizes, counters), then the three history states
+// (FP64), the ring's inputs (bf16) and targets (FP32), then the network (FP32 weights,
+// first and second moments).
+static const long long kCkMagic = 0x31504B43474D5046LL;   // "FPMGCKP1"
+enum { CK_MAGIC, CK_VERSION, CK_E, CK_NV, CK_NP, CK_NDOF, CK_HAS_GUESS, CK_K0, CK_O, CK_NHIST, CK_RING_CAP,
+       CK_RING_N, CK_RING_HEAD, CK_CURSOR, CK_MLP_STEPS, CK_HAS_MLP, CK_MLP_IN, CK_MLP_HID, CK_MLP_OUT, CK_MLP_T,
+       CK_MLP_FLOATS, CK_NHEAD = 24 };
+
+static long long ck_bytes(const fr_ctx *C, const fr_mlp *M) {
+    long long b = 8LL * CK_NHEAD;
+    if (C->qex) {
+        b += 3LL * C->L[0].ndof * 8;
+        b += (long long)C->ring_cap * C->K0 * 2 + (long long)C->ring_cap * C->O * 4;
+    }
+    if (M) b += frkmlp_state_floats(M) * 4;
+    return b;
+}
+
+extern "C" int fr_checkpoint_size(const fr_ctx *C, const fr_mlp *M, long long *bytes) {
+    if (!C || !bytes) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    *bytes = ck_bytes(C, M);
+    return FR_OK;
+}
+
+extern "C" int fr_checkpoint_save(const fr_ctx *C, const fr_mlp *M, void *buf, long long bytes) {
+    if (!C || !buf) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    if (bytes < ck_bytes(C, M)) return fail(FR_ERR_INVALID_ARG, "buffer of %lld bytes, %lld needed", bytes, ck_bytes(C, M));
+    CK(cudaDeviceSynchronize());
+    long long *h = (long long *)buf;
+    memset(h, 0, 8 * CK_NHEAD);
+    h[CK_MAGIC] = kCkMagic; h[CK_VERSION] = 1; h[CK_E] = C->E; h[CK_NV] = C->nv; h[CK_NP] = C->L[0].np;
+    h[CK_NDOF] = C->L[0].ndof; h[CK_HAS_GUESS] = C->qex != nullptr; h[CK_K0] = C->K0; h[CK_O] = C->O;
+    h[CK_NHIST] = C->nhist; h[CK_RING_CAP] = C->ring_cap; h[CK_RING_N] = C->ring_n; h[CK_RING_HEAD] = C->ring_head;
+    h[CK_CURSOR] = C->train_cursor; h[CK_MLP_STEPS] = C->mlp_steps; h[CK_HAS_MLP] = M != nullptr;
+    char *p = (char *)buf + 8 * CK_NHEAD;
+    if (C->qex) {
+        size_t sb = sizeof(double) * C->L[0].ndof;
+        for (int k = 0; k < 3; ++k, p += sb) CK(cudaMemcpy(p, C->hist[k], sb, cudaMemcpyDeviceToHost));
+        size_t xb = sizeof(unsigned short) * (size_t)C->ring_cap * C->K0, tb = sizeof(float) * (size_t)C->ring_cap * C->O;
+        CK(cudaMemcpy(p, C->ringX, xb, cudaMemcpyDeviceToHost)); p += xb;
+        CK(cudaMemcpy(p, C->ringT, tb, cudaMemcpyDeviceToHost)); p += tb;
+    }
+    if (M) {
+        int d4[4];
+        if (frkmlp_state_save(M, d4, (float *)p) != 0) return fail(FR_ERR_CUDA, "reading the network state");
+        h[CK_MLP_IN] = d4[0]; h[CK_MLP_HID] = d4[1]; h[CK_MLP_OUT] = d4[2]; h[CK_MLP_T] = d4[3];
+        h[CK_MLP_FLOATS] = frkmlp_state_floats(M);
+    }
+    return FR_OK;
+}
+
+extern "C" int fr_checkpoint_load(fr_ctx *C, fr_mlp *M, const void *buf, long long bytes) {
+    if (!C || !buf || bytes < 8 * CK_NHEAD) return fail(FR_ERR_INVALID_ARG, "NULL or short buffer");
+    const long long *h = (const long long *)buf;
+    if (h[CK_MAGIC] != kCkMagic || h[CK_VERSION] != 1) return fail(FR_ERR_INVALID_ARG, "not a checkpoint of this version");
+    if (h[CK_E] != C->E || h[CK_NV] != C->nv || h[CK_NP] != C->L[0].np || h[CK_NDOF] != C->L[0].ndof)
+        return fail(FR_ERR_INVALID_ARG, "checkpoint of another mesh or degree");
+    if (h[CK_HAS_MLP] && !M) return fail(FR_ERR_INVALID_ARG, "the checkpoint holds a network: pass one of its sizes");
+    long long need = 8LL * CK_NHEAD;
+    if (h[CK_HAS_GUESS])
+        need += 3LL * h[CK_NDOF] * 8 + h[CK_RING_CAP] * h[CK_K0] * 2 + h[CK_RING_CAP] * h[CK_O] * 4;
+    if (h[CK_HAS_MLP]) need += h[CK_MLP_FLOATS] * 4;
+    if (bytes < need) return fail(FR_ERR_INVALID_ARG, "checkpoint truncated (%lld of %lld bytes)", bytes, need);
+    const char *p = (const char *)buf + 8 * CK_NHEAD;
+    if (h[CK_HAS_GUESS]) {
+        int E = C->L[0].E;
+        long long per_stage = (long long)kRingSteps * E;
+        if (h[CK_RING_CAP] % per_stage) return fail(FR_ERR_INVALID_ARG, "checkpoint ring of another size");
+        TRY(ensure_guess_buffers(C, (int)(h[CK_RING_CAP] / per_stage) + 1));
+        if (C->ring_cap != h[CK_RING_CAP] || C->K0 != h[CK_K0] || C->O != h[CK_O])
+            return fail(FR_ERR_INVALID_ARG, "checkpoint ring does not match this context's");
+        size_t sb = sizeof(double) * C->L[0].ndof;
+        for (int k = 0; k < 3; ++k, p += sb) CK(cudaMemcpy(C->hist[k], p, sb, cudaMemcpyHostToDevice));
+        size_t xb = sizeof(unsigned short) * (size_t)C->ring_cap * C->K0, tb = sizeof(float) * (size_t)C->ring_cap * C->O;
+        CK(cudaMemcpy(C->ringX, p, xb, cudaMemcpyHostToDevice)); p += xb;
+        CK(cudaMemcpy(C->ringT, p, tb, cudaMemcpyHostToDevice)); p += tb;
+        C->nhist = (int)h[CK_NHIST]; C->ring_n = (int)h[CK_RING_N]; C->ring_head = (int)h[CK_RING_HEAD];
+        C->train_cursor = (int)h[CK_CURSOR];
+    } else {
+        C->nhist = 0; C->ring_n = 0; C->ring_head = 0; C->train_cursor = 0;
+    }
+    C->mlp_steps = (int)h[CK_MLP_STEPS];
+    if (h[CK_HAS_MLP]) {
+        int d4[4] = {(int)h[CK_MLP_IN], (int)h[CK_MLP_HID], (int)h[CK_MLP_OUT], (int)h[CK_MLP_T]};
+        if (frkmlp_state_floats(M) != h[CK_MLP_FLOATS] || frkmlp_state_load(M, d4, (const float *)p) != 0)
+            return fail(FR_ERR_INVALID_ARG, "network of other sizes, or copy failed");
+    }
+    return FR_OK;
+}
+
 // The pMG nonlinear solver for steady problems (Sec. 3.1, Eqs. 11-16): one nonlinear
 // V-cycle per iteration.  The preconditioner's cycle solves 0 = X + R(qh) - c (qh - q) -
 // R(q); with X = R(q) that is the backward-Euler pseudo step R(qh) - c (qh - q) = 0, so an

@@ -434,3 +434,22 @@ int frkmlp_var_stats(int nv, long long per, const double *a, const double *b, co
     CNT(); k_var_final<<<1, 32, 0, s>>>(nv, per, part, qinf_dev, out_dev);
     return 0;
 }
+
+// network state for checkpoints: sizes, Adam step, FP32 weights and moments (host copies)
+long long frkmlp_state_floats(const fr_mlp *M) { return 3LL * (long long)M->np; }
+int frkmlp_state_save(const fr_mlp *M, int *dims4, float *buf) {
+    dims4[0] = M->in; dims4[1] = M->hid; dims4[2] = M->out; dims4[3] = M->t;
+    if (cudaMemcpy(buf, M->p, sizeof(float) * M->np, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    if (cudaMemcpy(buf + M->np, M->m, sizeof(float) * M->np, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    if (cudaMemcpy(buf + 2 * M->np, M->v, sizeof(float) * M->np, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    return 0;
+}
+int frkmlp_state_load(fr_mlp *M, const int *dims4, const float *buf) {
+    if (dims4[0] != M->in || dims4[1] != M->hid || dims4[2] != M->out) return -1;
+    M->t = dims4[3];
+    if (cudaMemcpy(M->p, buf, sizeof(float) * M->np, cudaMemcpyHostToDevice) != cudaSuccess) return -1;
+    if (cudaMemcpy(M->m, buf + M->np, sizeof(float) * M->np, cudaMemcpyHostToDevice) != cudaSuccess) return -1;
+    if (cudaMemcpy(M->v, buf + 2 * M->np, sizeof(float) * M->np, cudaMemcpyHostToDevice) != cudaSuccess) return -1;
+    CNT(); k_to_bf16<<<nb(M->np), 256>>>(M->np, M->p, M->pb);
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : -1;
+}

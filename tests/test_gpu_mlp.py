@@ -250,3 +250,42 @@ def test_guess_requires_a_network():
         api.esdirk_step(G, A, b, wl.dt, q, o)
     with pytest.raises(Exception):
         api.fr_set_mlp(G, api.MLP(32, 16, 8, np.zeros(32 * 16 + 16 + 256 + 16 + 128 + 8, dtype=np.float32)))
+
+
+def test_checkpoint_resume_is_bit_identical():
+    """Save the learned guess's state (history, training ring, network and Adam moments)
+    after five steps, restore it into a fresh context and a fresh network, and step on:
+    the resumed run reproduces the uninterrupted one bit for bit."""
+    wl = _cyl_case()
+    A, b = GT.esdirk3()
+    dt = wl.dt
+    o = api.solve_opts(kdim=30, maxit_gmres=300, max_ptc=40, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-9,
+                       dtau=dt, inv_dtau_star=1.0 / dt, guess="mlp", train_iters=5, train_batch=1024, lr=1e-3)
+
+    def fresh(seed):
+        G = api.fr_create(wl.mesh, wl.phys, wl.levels)
+        K0, O = api.fr_mlp_dims(G)
+        net = api.MLP(K0, 64, O, _flat(_init(np.random.default_rng(seed), K0, 64, O, out_scale=0.1)))
+        api.fr_set_mlp(G, net)
+        return G, net
+
+    G1, net1 = fresh(1)
+    q = torch.from_numpy(np.ascontiguousarray(wl.q0)).cuda()
+    for _ in range(5):
+        api.esdirk_step(G1, A, b, dt, q, o, allow_not_converged=False)
+    ck = api.fr_checkpoint_save(G1, net1)
+    q_saved = q.clone()
+    for _ in range(3):
+        st1 = api.esdirk_step(G1, A, b, dt, q, o, allow_not_converged=False)
+    G2, net2 = fresh(2)                        # other initial weights: the checkpoint must carry them
+    api.fr_checkpoint_load(G2, ck, net2)
+    q2 = q_saved.clone()
+    for _ in range(3):
+        st2 = api.esdirk_step(G2, A, b, dt, q2, o, allow_not_converged=False)
+    assert torch.equal(q, q2)
+    assert st1["guess_pick"] == st2["guess_pick"] and st1["n_gmres"] == st2["n_gmres"]
+    assert np.array_equal(net1.params(), net2.params())
+    # a checkpoint of another mesh is refused
+    G3 = api.fr_create(w.cylinder_unsteady(nr=12, nt=24, p=3).mesh, wl.phys, wl.levels)
+    with pytest.raises(Exception, match="mesh"):
+        api.fr_checkpoint_load(G3, ck, net2)
