@@ -1,4 +1,4 @@
-// Per-element MLP for the Newton initial guess (the benchmark spec addition; the paper's guess is
+// Per-element MLP for the Newton initial guess (an addition to the method; the paper's guess is
 // q^n): forward, backward and Adam, BF16 operands with FP32 accumulation on the tensor
 // cores (mma.sync m16n8k16), plus the per-element feature / target / guess assembly.
 //
