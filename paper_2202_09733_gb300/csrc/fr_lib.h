@@ -83,7 +83,6 @@ void frk64_update_x(long long n, int m, const double *y_host, const double *cons
 
 // precision boundary of the mixed preconditioner
 void frk32_d2f(long long n, const double *x, float *y, cudaStream_t s);
-void frk32_f2d_scaled(long long n, const float *x, double inv_s, double *y, cudaStream_t s);
 void frk32_d2f_scaled(long long n, const double *x, const double *xmax_dev, double target, float *y, cudaStream_t s);
 // per-variable max |x| of a [nv][per] vector into out_dev[0..nv)
 int frk32_absmax_var(int nv, long long per, const double *x, double *out_dev, cudaStream_t s);

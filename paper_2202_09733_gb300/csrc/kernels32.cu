@@ -9,9 +9,6 @@
 
 // --------------------------------------------------------- precision boundary
 __global__ void k_d2f(long long n, const double *x, float *y) { GRID_STRIDE(i, n) y[i] = (float)x[i]; }
-__global__ void k_f2d_scaled(long long n, const float *x, double inv_s, double *y) {
-    GRID_STRIDE(i, n) y[i] = (double)x[i] * inv_s;
-}
 // y = float(x * s), s = target / max|x| read from the device (no host round trip)
 __global__ void k_d2f_scaled(long long n, const double *x, const double *xmax, double target, float *y) {
     double m = *xmax;
@@ -26,9 +23,6 @@ __global__ void k_absmax(long long n, const double *x, unsigned long long *out) 
 }
 
 void frk32_d2f(long long n, const double *x, float *y, cudaStream_t s) { CNT(); k_d2f<<<nblk(n), 256, 0, s>>>(n, x, y); }
-void frk32_f2d_scaled(long long n, const float *x, double inv_s, double *y, cudaStream_t s) {
-    CNT(); k_f2d_scaled<<<nblk(n), 256, 0, s>>>(n, x, inv_s, y);
-}
 void frk32_d2f_scaled(long long n, const double *x, const double *xmax_dev, double target, float *y, cudaStream_t s) {
     CNT(); k_d2f_scaled<<<nblk(n), 256, 0, s>>>(n, x, xmax_dev, target, y);
 }
