@@ -17,7 +17,7 @@
 #include "fr_dual.cuh"
 
 // Arithmetic type T of a kernel and the base type B = FrBase<T>::type of its operator
-// tables and geometric factors: B = T for double and float; float for DualF.
+// tables and geometric factors: B = T for double and float; float for the dual types.
 
 #define FR_MAXN 6
 #define FR_MAXP 5

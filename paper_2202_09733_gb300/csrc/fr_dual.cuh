@@ -1,46 +1,13 @@
-// Forward-mode dual number {value, derivative} in FP32.  Running the residual kernels on
-// DualF with a unit seed in one degree of freedom per element gives that column of the
+// Forward-mode dual numbers in FP32: a value and K tangents.  Running the residual kernels
+// on them with unit seeds in K degrees of freedom per element gives those K columns of the
 // element-diagonal Jacobian block exactly (to FP32 rounding of each term), with no
 // finite-difference step and no cancellation.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
 
-struct DualF {
-    float v, d;
-    DualF() = default;
-    __host__ __device__ constexpr DualF(float x) : v(x), d(0.f) {}
-    __host__ __device__ constexpr DualF(double x) : v((float)x), d(0.f) {}
-    __host__ __device__ constexpr DualF(int x) : v((float)x), d(0.f) {}
-    __host__ __device__ constexpr DualF(float x, float dx) : v(x), d(dx) {}
-};
-
-__device__ __forceinline__ DualF operator+(DualF a, DualF b) { return DualF(a.v + b.v, a.d + b.d); }
-__device__ __forceinline__ DualF operator-(DualF a, DualF b) { return DualF(a.v - b.v, a.d - b.d); }
-__device__ __forceinline__ DualF operator-(DualF a) { return DualF(-a.v, -a.d); }
-__device__ __forceinline__ DualF operator*(DualF a, DualF b) { return DualF(a.v * b.v, fmaf(a.d, b.v, a.v * b.d)); }
-__device__ __forceinline__ DualF operator*(float a, DualF b) { return DualF(a * b.v, a * b.d); }
-__device__ __forceinline__ DualF operator*(DualF a, float b) { return DualF(a.v * b, a.d * b); }
-__device__ __forceinline__ DualF operator/(DualF a, DualF b) {
-    float q = a.v / b.v;
-    return DualF(q, (a.d - q * b.d) / b.v);
-}
-__device__ __forceinline__ DualF fma(DualF a, DualF b, DualF c) {
-    return DualF(fmaf(a.v, b.v, c.v), fmaf(a.d, b.v, fmaf(a.v, b.d, c.d)));
-}
-__device__ __forceinline__ DualF fma(float a, DualF b, DualF c) { return DualF(fmaf(a, b.v, c.v), fmaf(a, b.d, c.d)); }
-__device__ __forceinline__ DualF fma(DualF a, float b, DualF c) { return DualF(fmaf(a.v, b, c.v), fmaf(a.d, b, c.d)); }
-__device__ __forceinline__ DualF sqrt(DualF a) {
-    float s = sqrtf(a.v);
-    return DualF(s, s > 0.f ? a.d / (2.f * s) : 0.f);
-}
-__device__ __forceinline__ DualF fabs(DualF a) { return a.v < 0.f ? -a : a; }
-__device__ __forceinline__ DualF fmax(DualF a, DualF b) { return a.v >= b.v ? a : b; }
-
-
-// Vector forward mode: K tangent directions carried at once, so that one residual
-// evaluation yields K columns of the element blocks (each tangent follows the same
-// formulas as DualF's one).  K = 3 makes a 16-byte value.
+// K tangent directions carried at once, so that one residual evaluation yields K columns
+// of the element blocks.  K = 3 makes a 16-byte value.
 template <int K>
 struct __align__(16) DualN {
     float v, d[K];
@@ -119,10 +86,6 @@ FR_DN DualN<K> fmax(DualN<K> a, DualN<K> b) { return a.v >= b.v ? a : b; }
 template <typename T>
 struct FrBase {
     typedef T type;
-};
-template <>
-struct FrBase<DualF> {
-    typedef float type;
 };
 template <int K>
 struct FrBase<DualN<K>> {
