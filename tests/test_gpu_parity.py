@@ -150,6 +150,7 @@ def test_pmg_precondition(case):
     Y_or = O.pmg_apply(q, Rq, X)
     Y_gpu = api.pmg_precondition(G, dev(q), dev(Rq), dev(X))
     assert relerr(Y_gpu, Y_or) <= 1e-12
+    assert np.array_equal(Y_gpu.cpu().numpy(), Y_or), "the FP64 V-cycle follows the oracle's order: bit for bit"
 
 
 def test_gmres_fixed_iterations(case):
