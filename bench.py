@@ -55,6 +55,45 @@ def parse():
     return ap.parse_args()
 
 
+SOLVE_TRAFFIC_16 = 1.845e9   # ncu DRAM bytes of one FP32 fine solve on 16^3 (4096 elements)
+
+
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (GB/s), else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy, burst)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+def solve_roofline(tune, E, nd):
+    """Roofline of the step's dominant kernel, the FP32 fine-level block solve: its time per
+    launch as the autotuner measured it in this run (CUDA events, the chosen variant, on
+    the blocks the first step factored) against the algorithmic bytes of one application:
+    the E nd^2 FP32 factors, the permutation and the vector read and written."""
+    import re
+    t_ms = None
+    for line in tune or []:
+        if line.startswith("d=3 p=3 fp32") and "ms per G" in line:
+            t_ms = min(float(x.split(":")[1]) for x in re.search(r"ms per G ([^)]*)\)", line).group(1).split())
+    peak, src = hbm_peak()
+    algo = E * nd * nd * 4 + E * nd * 4 + 2 * E * nd * 4
+    out = {"kernel": f"k_lu_solve (FP32 fine-level block solve, {E} LU factors of {nd}x{nd}, one application)",
+           "bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": src, "algorithmic_bytes": algo,
+           "traffic": SOLVE_TRAFFIC_16 * E / 4096,
+           "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on tgv3d 16^3 "
+                             "(4096 elements, 1.845 GB), scaled by the element count "
+                             "(profiles/lu_solve_tgv3d16_fp32_fp64.md)",
+           "share_of_step": "about a third of the step's kernel time (profiles/launches_tgv3d32_row_mixed.md)"}
+    if t_ms:
+        out.update({"achieved": algo / (t_ms * 1e-3) / 1e9, "frac": algo / (t_ms * 1e-3) / 1e9 / peak,
+                    "ms_per_launch": t_ms})
+    else:
+        out.update({"achieved": None, "frac": None, "note": "autotuner did not time the solve (--no-autotune)"})
+    return out
+
+
 def max_over_ranks(x, ws, device):
     """The largest of every rank's x (replica timings: the job takes as long as its
     slowest rank); x itself on a single rank."""
@@ -419,7 +458,8 @@ def gpu_arm(args):
             "residual_gdofs": gdofs,
             "residual_ms": t_R * 1e3,
             "gmres_iterations_per_step": statistics.mean(ng),
-            "roofline": {"kernel": "fr_residual (FP64 FR residual, 8 kernels per launch)", "bound": "alu",
+            "roofline": solve_roofline(tune, E, 5 * 64),
+            "roofline_residual": {"kernel": "fr_residual (FP64 FR residual, 8 kernels per launch)", "bound": "alu",
                          "achieved": flops / t_R / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
                          "frac": (flops / t_R) / FP64_PEAK_NOMINAL, "traffic": RESIDUAL_TRAFFIC_BYTES,
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 8 kernels of one "
