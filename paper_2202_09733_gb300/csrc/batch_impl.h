@@ -306,7 +306,17 @@ static int arnoldi_step(fr_batch *B, BGroup &g, int j, const double *q, const do
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(FR_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
     x.nkernels = (long long)captured;
-    g.graphs.push_back(x);
+    // one graph per Krylov index: a new key (another dt, level count, ...) replaces the old
+    // graph of that index, so the cache stays at kdim graphs however often dt changes
+    bool replaced = false;
+    for (auto &y : g.graphs)
+        if (y.j == j) {
+            cudaGraphExecDestroy(y.exec);
+            y = x;
+            replaced = true;
+            break;
+        }
+    if (!replaced) g.graphs.push_back(x);
     CK(cudaGraphLaunch(x.exec, s));
     g_graph_kernels += captured;
     return FR_OK;
