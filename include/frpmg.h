@@ -311,8 +311,8 @@ int pmg_solve_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, 
  * (G = 1) the kernel that streams the factor through shared memory with bulk async
  * copies (rows of a column that the pass needs only; nd * sizeof(scalar) % 16 == 0).  flags:
  * bit 0 FP64 levels, bit 1 FP32 levels, bit 2 re-tune even if cached.  Results are kept
- * in a process-wide cache keyed by (device name, d, p, precision, floor(log2 E)); new
- * contexts pick cached shapes up.  report (host, may be NULL): one line per level.
+ * in a process-wide cache keyed by (device name, d, p, precision, floor(log2 E)), safe
+ * to use from several host threads; new contexts pick cached shapes up.  report (host, may be NULL): one line per level.
  * Uses the legacy default stream and synchronises the device. */
 int fr_autotune(fr_ctx *ctx, int flags, int reps, char *report, int report_len);
 /* tiles[9]: the 8 CTA sizes (0 = default 128; else a multiple of 32 in 32..256) and G

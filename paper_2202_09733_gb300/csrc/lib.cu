@@ -10,6 +10,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 #include "../../include/frpmg.h"
@@ -1427,7 +1428,8 @@ struct TuneVal {
     short tile[8];
     short lu_g;
 };
-static std::vector<std::pair<TuneKey, TuneVal>> g_tune;
+static std::vector<std::pair<TuneKey, TuneVal>> g_tune;   // process-wide; guarded by g_tune_mu
+static std::mutex g_tune_mu;
 
 static int ebucket(long long E) {
     int b = 0;
@@ -1446,12 +1448,20 @@ static TuneKey tune_key(const FrLevel &L, int prec) {
     k.d = L.d; k.p = L.p; k.prec = prec; k.ebucket = ebucket(L.E);
     return k;
 }
-static TuneVal *tune_find(const TuneKey &k) {
+static bool same_key(const TuneKey &a, const TuneKey &b) {
+    return !strcmp(a.dev, b.dev) && a.d == b.d && a.p == b.p && a.prec == b.prec && a.ebucket == b.ebucket;
+}
+static bool tune_lookup(const TuneKey &k, TuneVal *out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
     for (auto &x : g_tune)
-        if (!strcmp(x.first.dev, k.dev) && x.first.d == k.d && x.first.p == k.p && x.first.prec == k.prec &&
-            x.first.ebucket == k.ebucket)
-            return &x.second;
-    return nullptr;
+        if (same_key(x.first, k)) { *out = x.second; return true; }
+    return false;
+}
+static void tune_store(const TuneKey &k, const TuneVal &v) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &x : g_tune)
+        if (same_key(x.first, k)) { x.second = v; return; }
+    g_tune.push_back({k, v});
 }
 
 template <typename T>
@@ -1532,8 +1542,7 @@ static int tune_level(fr_ctx *C, int l, int prec, int reps, char *rep, size_t re
     TuneVal val;
     memcpy(val.tile, L.tile, sizeof val.tile);
     val.lu_g = L.lu_g;
-    if (TuneVal *v = tune_find(key)) *v = val;
-    else g_tune.push_back({key, val});
+    tune_store(key, val);
     if (rep) {
         size_t u = strlen(rep);
         snprintf(rep + u, replen - u,
@@ -1554,11 +1563,13 @@ static void apply_tune(fr_ctx *C, int l, const TuneVal &v) {
 
 // a new context (or its FP32 levels) takes the shapes already tuned for its key
 static void apply_cached_tiles(fr_ctx *C, int prec) {
-    for (int l = 0; l < C->nlev; ++l)
-        if (TuneVal *v = tune_find(tune_key(C->L[l], prec))) {
-            if (prec) apply_tune<float>(C, l, *v);
-            else apply_tune<double>(C, l, *v);
+    for (int l = 0; l < C->nlev; ++l) {
+        TuneVal v;
+        if (tune_lookup(tune_key(C->L[l], prec), &v)) {
+            if (prec) apply_tune<float>(C, l, v);
+            else apply_tune<double>(C, l, v);
         }
+    }
 }
 
 extern "C" int fr_autotune(fr_ctx *C, int flags, int reps, char *report, int report_len) {
@@ -1570,10 +1581,10 @@ extern "C" int fr_autotune(fr_ctx *C, int flags, int reps, char *report, int rep
         if (!(flags & (1 << prec))) continue;
         if (prec == 1) TRY(ensure_levels32(C));
         for (int l = 0; l < C->nlev; ++l) {
-            TuneVal *v = (flags & 4) ? nullptr : tune_find(tune_key(C->L[l], prec));
-            if (v) {
-                if (prec) apply_tune<float>(C, l, *v);
-                else apply_tune<double>(C, l, *v);
+            TuneVal v;
+            if (!(flags & 4) && tune_lookup(tune_key(C->L[l], prec), &v)) {
+                if (prec) apply_tune<float>(C, l, v);
+                else apply_tune<double>(C, l, v);
                 if (rp) {
                     size_t u = strlen(rp);
                     snprintf(rp + u, rl - u, "d=%d p=%d %s E=%d: cached\n", C->L[l].d, C->L[l].p, prec ? "fp32" : "fp64",
@@ -1615,6 +1626,7 @@ extern "C" int fr_autotune_save(const char *path) {
     FILE *f = fopen(path, "w");
     if (!f) return fail(FR_ERR_INVALID_ARG, "cannot write %s", path);
     fprintf(f, "# frpmg launch shapes: device d p precision log2E tile0..tile7 solveG\n");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
     for (auto &x : g_tune) {
         fprintf(f, "%s %d %d %d %d", x.first.dev, x.first.d, x.first.p, x.first.prec, x.first.ebucket);
         for (int k = 0; k < 8; ++k) fprintf(f, " %d", x.second.tile[k]);
@@ -1645,8 +1657,7 @@ extern "C" int fr_autotune_load(const char *path) {
         if (!ok) continue;
         for (int i = 0; i < 8; ++i) v.tile[i] = (short)t[i];
         v.lu_g = (short)t[8];
-        if (TuneVal *o = tune_find(k)) *o = v;
-        else g_tune.push_back({k, v});
+        tune_store(k, v);
         ++n;
     }
     fclose(f);
