@@ -4,15 +4,15 @@
 // (one problem's element range of at most kSegChunk elements): one block per item sums
 // its share in a fixed order, then one thread per problem sums its items in item order,
 // so results are reproducible run to run.
+#include <atomic>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <algorithm>
 #include "fr_lib.h"
 
-static unsigned long long g_launches = 0;
+static std::atomic<unsigned long long> g_launches{0};   // host-side launch counter (any thread)
 unsigned long long frkb_launch_count() { return g_launches; }
-void frkb_add_launches(long long k) { g_launches += (unsigned long long)k; }
-#define CNT() (++g_launches)
+#define CNT() (g_launches.fetch_add(1, std::memory_order_relaxed))
 
 #define SEG_THREADS 256
 #define GRID_STRIDE(i, n) \

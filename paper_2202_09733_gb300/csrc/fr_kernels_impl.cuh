@@ -5,14 +5,15 @@
 //   FR_DOUBLE      1 for the FP64 unit (adds the Krylov/time-stepping vector kernels)
 // The FP64 unit is compiled with -fmad=false, so there the only fused multiply-adds are
 // the explicit fma() calls and every result follows the documented evaluation order.
+#include <atomic>
 #include <cuda_runtime.h>
 #include <algorithm>
 #include "fr_device.cuh"
 #include "fr_lib.h"
 
-static unsigned long long g_launches = 0;
+static std::atomic<unsigned long long> g_launches{0};   // host-side launch counter (any thread)
 unsigned long long FRK(launch_count)() { return g_launches; }
-#define CNT() (++g_launches)
+#define CNT() (g_launches.fetch_add(1, std::memory_order_relaxed))
 
 __constant__ FrTab<FRT> c_tab[FR_MAXP + 1];
 __constant__ FRT c_gam[FR_MAXP + 1][FR_MAXP + 1][FR_MAXN][FR_MAXN];

@@ -99,7 +99,6 @@ void frk32_next_target(int nv, const double *ymax_dev, const double *qref_dev, d
 
 // segmented vector kernels of the batched solver (batch_kernels.cu)
 unsigned long long frkb_launch_count();
-void frkb_add_launches(long long k);
 int frkb_segdots(int rows, int E, int nitems, const int4 *items, int nprob, const int *item_off, const double *w,
                  int m, const double *const *V, double *partial, double *out, int ld, cudaStream_t s);
 void frkb_seg_invnorm(int nprob, const double *sq, int ld, const double *mask, double *nrm, double *inv,

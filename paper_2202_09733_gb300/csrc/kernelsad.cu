@@ -3,13 +3,14 @@
 // j0 + t of every element of one colour (elements of a colour share no face), so R.d[t]
 // restricted to each of those elements is column j0 + t of its block dR_e/dq_e, exact up
 // to FP32 rounding of each term.  One residual evaluation gives FR_AD_K columns.
+#include <atomic>
 #include <algorithm>
 #include "fr_device.cuh"
 #include "fr_lib.h"
 
-static unsigned long long g_launches = 0;
+static std::atomic<unsigned long long> g_launches{0};   // host-side launch counter (any thread)
 unsigned long long frkad_launch_count() { return g_launches; }
-#define CNT() (++g_launches)
+#define CNT() (g_launches.fetch_add(1, std::memory_order_relaxed))
 
 __constant__ FrTab<float> c_tab_ad[FR_MAXP + 1];
 template <>

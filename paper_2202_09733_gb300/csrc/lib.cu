@@ -10,6 +10,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -126,8 +127,8 @@ static void apply_cached_tiles(fr_ctx *C, int prec);
 
 extern "C" const char *fr_last_error(void) { return g_err; }
 
-static unsigned long long g_graph_kernels = 0;    // kernels run by CUDA graph replays
-static unsigned long long g_capture_kernels = 0;  // launch-counter increments made while capturing graphs
+static std::atomic<unsigned long long> g_graph_kernels{0};    // kernels run by CUDA graph replays
+static std::atomic<unsigned long long> g_capture_kernels{0};  // launch-counter increments made while capturing graphs
 
 extern "C" unsigned long long fr_kernel_launches(void) {
     return frk64_launch_count() + frk32_launch_count() + frkad_launch_count() + frkmlp_launch_count() +

@@ -7,6 +7,7 @@
 // x, h1, h2, the output-side gradients and the weights enter every matrix product
 // rounded to bfloat16 (nearest, ties to even); sums run in FP32; master weights and Adam
 // moments are FP32.
+#include <atomic>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -17,9 +18,9 @@
 #include "../../include/frpmg.h"
 #include "fr_lib.h"
 
-static unsigned long long g_launches = 0;
+static std::atomic<unsigned long long> g_launches{0};   // host-side launch counter (any thread)
 unsigned long long frkmlp_launch_count() { return g_launches; }
-#define CNT() (++g_launches)
+#define CNT() (g_launches.fetch_add(1, std::memory_order_relaxed))
 
 typedef __nv_bfloat16 bf16;
 
