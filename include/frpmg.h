@@ -69,10 +69,14 @@ typedef struct {
 } fr_mesh_desc;
 
 /* gamma, Prandtl number, dynamic viscosity (1/Re in the dimensionless set-up of Sec. 2.2),
- * BR2 penalty, free-stream conservative state (nv values) used by far-field faces. */
+ * BR2 penalty, free-stream conservative state (nv values) used by far-field faces, and the
+ * inviscid common flux: 0 Rusanov (local Lax-Friedrichs), 1 Roe (the original Roe solver
+ * the paper uses in Sec. 4.2: |A| of the Roe-averaged state, no entropy fix).  Any other
+ * flux value is FR_ERR_INVALID_ARG. */
 typedef struct {
     double gamma, prandtl, mu, eta;
     double qinf[5];
+    int flux;
 } fr_physics;
 
 /* Create a context: operator tables, geometric factors of every level, connectivity and

@@ -81,6 +81,7 @@ def lib():
         L.or_flux_inviscid.argtypes = [C.c_void_p, PD, PD]
         L.or_flux_viscous.argtypes = [C.c_void_p, PD, PD, C.c_int, PD]
         L.or_rusanov.argtypes = [C.c_void_p, PD, PD, PD, PD]
+        L.or_roe.argtypes = [C.c_void_p, PD, PD, PD, PD]
         _lib = L
     return _lib
 
@@ -144,7 +145,10 @@ class Oracle:
         g = np.ascontiguousarray(mesh["gnodes"], dtype=np.float64)
         f = np.ascontiguousarray(mesh["faces"], dtype=np.int32)
         pl = np.array(self.levels, dtype=np.int32)
-        ph = np.ascontiguousarray(phys.packed() if hasattr(phys, "packed") else phys, dtype=np.float64)
+        ph = np.zeros(10)                           # gamma, Pr, mu, eta, qinf[5], flux code
+        src = np.asarray(phys.packed() if hasattr(phys, "packed") else phys, dtype=np.float64)
+        ph[:len(src)] = src
+        self.flux = ("rusanov", "roe")[int(ph[9])]
         self._keep = (g, f, pl, ph)
         self.h = lib().or_create(self.d, self.E, mesh["qg"], _d(g), len(f), _i(f), len(pl), _i(pl), _d(ph))
 
@@ -183,6 +187,22 @@ class Oracle:
         out = np.zeros((self.nv, self.np_(l)))
         lib().or_elem_residual(self.h, l, _d(np.ascontiguousarray(q)), e, _d(np.ascontiguousarray(qe)), _d(out))
         return out
+
+    def inviscid_flux(self, q):
+        """f(q) as [d][nv] for one conservative state."""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        f = np.zeros((3, 5))
+        lib().or_flux_inviscid(self.h, _d(q), _d(f))
+        return f[:self.d, :self.nv].copy()
+
+    def common_flux(self, qL, qR, n, kind=None):
+        """The inviscid common flux along the scaled normal n ("rusanov" or "roe"; default:
+        the context's physics)."""
+        kind = kind or self.flux
+        qL, qR, n = (np.ascontiguousarray(a, dtype=np.float64) for a in (qL, qR, n))
+        F = np.zeros(5)
+        (lib().or_roe if kind == "roe" else lib().or_rusanov)(self.h, _d(qL), _d(qR), _d(n), _d(F))
+        return F[:self.nv].copy()
 
     def restrict(self, x0, l=0):
         out = np.zeros(self.shape(l + 1))

@@ -134,6 +134,68 @@ void or_rusanov(const or_ctx *C, const double *qL, const double *qR, const doubl
     }
 }
 
+/* Roe's approximate Riemann solver along the scaled normal n (Sec. 4.2 names the original
+ * Roe solver as the inviscid common flux of the unsteady cases; no entropy fix).  Written from
+ * the textbook construction: Roe-averaged density sqrt(rhoL rhoR) and sqrt(rho)-weighted
+ * velocity and total enthalpy; the jump qR - qL split into the acoustic waves vn -/+ c
+ * (strengths (dp -/+ rho c dvn) / (2 c^2)), the entropy wave (drho - dp / c^2) and the shear
+ * waves (rho (du - dvn nh)), the last two at speed vn.  F = (FnL + FnR)/2 - |n| D / 2, with D
+ * the sum over waves of |speed| x strength x right eigenvector along the unit normal nh. */
+void or_roe(const or_ctx *C, const double *qL, const double *qR, const double *n, double *F) {
+    int d = C->d, nv = C->nv;
+    double gm1 = C->ph.gamma - 1.0;
+    double fL[3][5], fR[3][5];
+    or_flux_inviscid(C, qL, fL);
+    or_flux_inviscid(C, qR, fR);
+    double nn = 0.0;
+    for (int c = 0; c < d; ++c) nn = fma(n[c], n[c], nn);
+    double nmag = sqrt(nn);
+    double nh[3];
+    for (int c = 0; c < d; ++c) nh[c] = n[c] / nmag;
+    double rho[2], u[2][3], p[2], H[2];
+    for (int side = 0; side < 2; ++side) {
+        const double *q = side ? qR : qL;
+        double rinv = 1.0 / q[0], ke = 0.0;
+        rho[side] = q[0];
+        for (int j = 0; j < d; ++j) u[side][j] = q[1 + j] * rinv;
+        for (int j = 0; j < d; ++j) ke = fma(q[1 + j], u[side][j], ke);
+        p[side] = gm1 * (q[d + 1] - 0.5 * ke);
+        H[side] = (q[d + 1] + p[side]) * rinv;
+    }
+    /* Roe average */
+    double sL = sqrt(rho[0]), sR = sqrt(rho[1]), wt = 1.0 / (sL + sR);
+    double ut[3], q2 = 0.0, vn = 0.0, du[3], dvn = 0.0, udu = 0.0;
+    for (int j = 0; j < d; ++j) ut[j] = (sL * u[0][j] + sR * u[1][j]) * wt;
+    double Ht = (sL * H[0] + sR * H[1]) * wt;
+    for (int j = 0; j < d; ++j) q2 = fma(ut[j], ut[j], q2);
+    for (int j = 0; j < d; ++j) vn = fma(ut[j], nh[j], vn);
+    double c2 = gm1 * (Ht - 0.5 * q2);
+    double ct = sqrt(c2);
+    double rt = sL * sR;
+    /* jumps and wave strengths */
+    double drho = rho[1] - rho[0], dp = p[1] - p[0];
+    for (int j = 0; j < d; ++j) du[j] = u[1][j] - u[0][j];
+    for (int j = 0; j < d; ++j) dvn = fma(du[j], nh[j], dvn);
+    for (int j = 0; j < d; ++j) udu = fma(ut[j], du[j], udu);
+    double a1 = (dp - rt * ct * dvn) / (2.0 * c2);
+    double a3 = (dp + rt * ct * dvn) / (2.0 * c2);
+    double a2 = drho - dp / c2;
+    double l1 = fabs(vn - ct), l2 = fabs(vn), l3 = fabs(vn + ct);
+    double w1 = l1 * a1, w2 = l2 * a2, w3 = l3 * a3, ws = l2 * rt;
+    /* |A_nh| (qR - qL) */
+    double Dv[5];
+    Dv[0] = w1 + w2 + w3;
+    for (int j = 0; j < d; ++j)
+        Dv[1 + j] = w1 * (ut[j] - ct * nh[j]) + w2 * ut[j] + ws * (du[j] - dvn * nh[j]) + w3 * (ut[j] + ct * nh[j]);
+    Dv[d + 1] = w1 * (Ht - ct * vn) + w2 * (0.5 * q2) + ws * (udu - vn * dvn) + w3 * (Ht + ct * vn);
+    for (int v = 0; v < nv; ++v) {
+        double FnL = 0.0, FnR = 0.0;
+        for (int c = 0; c < d; ++c) FnL = fma(fL[c][v], n[c], FnL);
+        for (int c = 0; c < d; ++c) FnR = fma(fR[c][v], n[c], FnR);
+        F[v] = 0.5 * (FnL + FnR) - 0.5 * nmag * Dv[v];
+    }
+}
+
 /* boundary ghost state: 1 = far field (free stream), 2 = no-slip adiabatic wall */
 static void ghost(const or_ctx *C, int bc, const double *qL, double *qR) {
     int d = C->d;
@@ -272,7 +334,8 @@ static void pair_flux(const or_ctx *C, const or_level *L, int P, const double *q
     for (int v = 0; v < nv; ++v) qs[v] = 0.5 * (qL[v] + qR[v]);
     for (int c = 0; c < d; ++c)
         for (int v = 0; v < nv; ++v) Qs[c][v] = (bc == 0) ? 0.5 * (QL[c][v] + QR[c][v]) : QL[c][v];
-    or_rusanov(C, qL, qR, nrm, Fr);
+    if (C->ph.flux == 1) or_roe(C, qL, qR, nrm, Fr);
+    else or_rusanov(C, qL, qR, nrm, Fr);
     or_flux_viscous(C, qs, Qs, bc == 2, fv);
     for (int v = 0; v < nv; ++v) {
         double Fv = 0.0;

@@ -36,7 +36,7 @@ class MeshDesc(C.Structure):
 
 class Physics(C.Structure):
     _fields_ = [("gamma", C.c_double), ("prandtl", C.c_double), ("mu", C.c_double), ("eta", C.c_double),
-                ("qinf", C.c_double * 5)]
+                ("qinf", C.c_double * 5), ("flux", C.c_int)]
 
 
 class PmgOpts(C.Structure):

@@ -77,6 +77,7 @@ def fr_create(mesh: dict, phys, levels) -> Context:
     ph.gamma, ph.prandtl, ph.mu, ph.eta = phys.gamma, phys.Pr, phys.mu, phys.eta
     for v, x in enumerate(phys.qinf):
         ph.qinf[v] = float(x)
+    ph.flux = int(getattr(phys, "flux_code", 0))
     h = C.c_void_p()
     N.check(lib.fr_create(C.byref(h), C.byref(md), C.byref(ph)), "fr_create")
     return Context(h, mesh["d"], mesh["E"], list(levels), mesh["d"] + 2)
@@ -398,6 +399,7 @@ class Batch:
         ph.gamma, ph.prandtl, ph.mu, ph.eta = phys.gamma, phys.Pr, phys.mu, phys.eta
         for v, x in enumerate(phys.qinf):
             ph.qinf[v] = float(x)
+        ph.flux = int(getattr(phys, "flux_code", 0))
         h = C.c_void_p()
         N.check(lib.fr_batch_create(C.byref(h), len(problems), descs, C.byref(ph)), "fr_batch_create")
         self.handle = h

@@ -34,6 +34,7 @@ struct FrPhys {
     T gamma, gm1, mu, kappa, c23;
     T qinf[5];
     T etagL, etagR;   // eta * g_L'(-1), eta * g_R'(+1) of the level
+    int flux;         // inviscid common flux: 0 Rusanov, 1 Roe
 };
 
 template <int D, int P>
@@ -187,6 +188,77 @@ __device__ __forceinline__ void rusanov(const FrPhys<B> &ph, const T *qL, const 
 #pragma unroll
         for (int c = 0; c < D; ++c) FnR = fma(fR[c][v], n[c], FnR);
         F[v] = T(0.5) * (FnL + FnR) - T(0.5) * lmax * (qR[v] - qL[v]);
+    }
+}
+
+// Roe flux along the (scaled) normal n: the mean of the two normal fluxes minus
+// |A(Roe average)| (qR - qL) / 2, the wave families through the Roe-averaged state (density
+// sqrt(rhoL rhoR), velocity and total enthalpy weighted by sqrt(rho)); Roe's original solver,
+// without an entropy fix
+template <int D, typename T, typename B>
+__device__ __forceinline__ void roe(const FrPhys<B> &ph, const T *qL, const T *qR, const B *n, T *F) {
+    constexpr int nv = D + 2;
+    T fL[3][5], fR[3][5];
+    flux_inviscid<D, T, B>(ph, qL, fL);
+    flux_inviscid<D, T, B>(ph, qR, fR);
+    B nn = B(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) nn = fma(n[c], n[c], nn);
+    B nmag = sqrt(nn);
+    B nh[3];
+#pragma unroll
+    for (int c = 0; c < D; ++c) nh[c] = n[c] / nmag;
+    T rho[2], u[2][3], p[2], H[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const T *q = side ? qR : qL;
+        T rinv = T(1) / q[0], ke = T(0);
+        rho[side] = q[0];
+#pragma unroll
+        for (int j = 0; j < D; ++j) u[side][j] = q[1 + j] * rinv;
+#pragma unroll
+        for (int j = 0; j < D; ++j) ke = fma(q[1 + j], u[side][j], ke);
+        p[side] = ph.gm1 * (q[D + 1] - T(0.5) * ke);
+        H[side] = (q[D + 1] + p[side]) * rinv;
+    }
+    T sL = sqrt(rho[0]), sR = sqrt(rho[1]), wt = T(1) / (sL + sR);
+    T ut[3], q2 = T(0), vn = T(0), du[3], dvn = T(0), udu = T(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) ut[j] = (sL * u[0][j] + sR * u[1][j]) * wt;
+    T Ht = (sL * H[0] + sR * H[1]) * wt;
+#pragma unroll
+    for (int j = 0; j < D; ++j) q2 = fma(ut[j], ut[j], q2);
+#pragma unroll
+    for (int j = 0; j < D; ++j) vn = fma(ut[j], nh[j], vn);
+    T c2 = ph.gm1 * (Ht - T(0.5) * q2);
+    T ct = sqrt(c2);
+    T rt = sL * sR;
+    T drho = rho[1] - rho[0], dp = p[1] - p[0];
+#pragma unroll
+    for (int j = 0; j < D; ++j) du[j] = u[1][j] - u[0][j];
+#pragma unroll
+    for (int j = 0; j < D; ++j) dvn = fma(du[j], nh[j], dvn);
+#pragma unroll
+    for (int j = 0; j < D; ++j) udu = fma(ut[j], du[j], udu);
+    T a1 = (dp - rt * ct * dvn) / (T(2) * c2);
+    T a3 = (dp + rt * ct * dvn) / (T(2) * c2);
+    T a2 = drho - dp / c2;
+    T l1 = fabs(vn - ct), l2 = fabs(vn), l3 = fabs(vn + ct);
+    T w1 = l1 * a1, w2 = l2 * a2, w3 = l3 * a3, ws = l2 * rt;
+    T Dv[5];
+    Dv[0] = w1 + w2 + w3;
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+        Dv[1 + j] = w1 * (ut[j] - ct * nh[j]) + w2 * ut[j] + ws * (du[j] - dvn * nh[j]) + w3 * (ut[j] + ct * nh[j]);
+    Dv[D + 1] = w1 * (Ht - ct * vn) + w2 * (T(0.5) * q2) + ws * (udu - vn * dvn) + w3 * (Ht + ct * vn);
+#pragma unroll
+    for (int v = 0; v < nv; ++v) {
+        T FnL = T(0), FnR = T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) FnL = fma(fL[c][v], n[c], FnL);
+#pragma unroll
+        for (int c = 0; c < D; ++c) FnR = fma(fR[c][v], n[c], FnR);
+        F[v] = T(0.5) * (FnL + FnR) - T(0.5) * nmag * Dv[v];
     }
 }
 
@@ -393,7 +465,8 @@ __global__ void __launch_bounds__(256) k_pair_flux(const int4 *__restrict__ pair
 #pragma unroll
     for (int v = 0; v < nv; ++v) qs[v] = T(0.5) * (qL[v] + qR[v]);
     T Fr[5], fv[3][5];
-    rusanov<D, T, B>(ph, qL, qR, nrm, Fr);
+    if (ph.flux == 1) roe<D, T, B>(ph, qL, qR, nrm, Fr);
+    else rusanov<D, T, B>(ph, qL, qR, nrm, Fr);
     flux_viscous<D, T, B>(ph, qs, Qs, bc == 2, fv);
 #pragma unroll
     for (int v = 0; v < nv; ++v) {

@@ -46,6 +46,7 @@ static FrPhys<FRT> to_phys(const FrPhysH &h, const FrLevelT<FRT> &L) {
     p.gamma = (FRT)h.gamma; p.gm1 = (FRT)h.gm1; p.mu = (FRT)h.mu; p.kappa = (FRT)h.kappa; p.c23 = (FRT)h.c23;
     for (int v = 0; v < 5; ++v) p.qinf[v] = (FRT)h.qinf[v];
     p.etagL = (FRT)L.etagL; p.etagR = (FRT)L.etagR;
+    p.flux = h.flux;
     return p;
 }
 

@@ -31,6 +31,7 @@ typedef FrLevelT<DualT> FrLevelAD;
 
 struct FrPhysH {
     double gamma, gm1, mu, kappa, c23, qinf[5];
+    int flux;   // 0 Rusanov, 1 Roe
 };
 
 // tables: per degree p (0..5) and transfers per (p0, p1)

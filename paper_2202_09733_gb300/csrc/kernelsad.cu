@@ -50,6 +50,7 @@ int frkad_residual(const FrLevelAD &L, const FrPhysH &h, const DualT *q, DualT *
     ph.c23 = (float)h.c23;
     for (int v = 0; v < 5; ++v) ph.qinf[v] = (float)h.qinf[v];
     ph.etagL = (float)L.etagL; ph.etagR = (float)L.etagR;
+    ph.flux = h.flux;
     if (L.d == 2) {
         switch (L.p) {
             case 1: residual_ad<2, 1>(L, ph, q, R, s); return 0;

@@ -231,6 +231,7 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
     }
     if (!(ph->gamma > 1.0) || !(ph->prandtl > 0.0) || !(ph->mu >= 0.0) || !(ph->eta >= 0.0))
         return fail(FR_ERR_INVALID_ARG, "invalid physical parameters");
+    if (ph->flux != 0 && ph->flux != 1) return fail(FR_ERR_INVALID_ARG, "flux must be 0 (Rusanov) or 1 (Roe)");
     fr_ctx *C = new fr_ctx();
     C->d = m->dim; C->nv = m->dim + 2; C->E = m->nelem; C->qg = m->qg; C->nlev = m->nlevels;
     C->eta = ph->eta;
@@ -240,6 +241,7 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
     C->ph.kappa = (ph->gamma * ph->mu) / ph->prandtl;
     C->ph.c23 = 2.0 / 3.0;
     for (int v = 0; v < 5; ++v) C->ph.qinf[v] = v < C->nv ? ph->qinf[v] : 0.0;
+    C->ph.flux = ph->flux;
     int rc = upload_tables();
     for (int l = 0; rc == FR_OK && l < m->nlevels; ++l) rc = setup_level(C, l, m->plevels[l], m);
     if (rc == FR_OK) {

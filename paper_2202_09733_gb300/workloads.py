@@ -277,6 +277,9 @@ def to_state(field: np.ndarray) -> np.ndarray:
 
 
 # ------------------------------------------------------------------------ configs
+FLUXES = ("rusanov", "roe")
+
+
 @dataclass
 class Physics:
     gamma: float = GAMMA
@@ -284,9 +287,17 @@ class Physics:
     mu: float = 0.0
     eta: float = 2.0
     qinf: np.ndarray = field(default_factory=lambda: np.zeros(4))
+    flux: str = "rusanov"          # inviscid common flux: "rusanov" or "roe"
+
+    @property
+    def flux_code(self) -> int:
+        return FLUXES.index(self.flux)
 
     def packed(self) -> np.ndarray:
-        return np.concatenate([[self.gamma, self.Pr, self.mu, self.eta], self.qinf]).astype(np.float64)
+        """gamma, Pr, mu, eta, qinf padded to 5, flux code (0 Rusanov, 1 Roe)."""
+        qi = np.zeros(5)
+        qi[:len(self.qinf)] = self.qinf
+        return np.concatenate([[self.gamma, self.Pr, self.mu, self.eta], qi, [self.flux_code]]).astype(np.float64)
 
 
 @dataclass
