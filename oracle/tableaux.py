@@ -8,7 +8,16 @@ published third-order members of those families:
   ROS34PW2 - Rang & Angermann's four-stage third-order W-method, standard
              (alpha, gamma, b) form, converted here to the transformed variables of
              Eq. (3): a = alpha Gamma^-1, c = diag(1/gamma) - Gamma^-1, m = b Gamma^-1.
-Both are pinned by their order conditions in the tests.
+and the paper's own ESDIRK schemes (Sec. 2.1 names them; their coefficients are not
+printed there):
+  ESDIRK2  - the three-stage, L-stable, stiffly accurate second-order ESDIRK of Kennedy &
+             Carpenter's review, gamma = 1 - 1/sqrt(2), c2 = 2 gamma; with an explicit first
+             stage, stiff accuracy and c2 = 2 gamma the order conditions fix the last row
+             to b1 = b2 = (1 - gamma) / 2;
+  ESDIRK4  - the six-stage, L-stable, stiffly accurate fourth-order ESDIRK of Bijl et al.
+             (the implicit part of Kennedy & Carpenter's ARK4(3)6L[2]SA, gamma = 1/4),
+             given as exact rationals.
+All are pinned by their order conditions in the tests.
 """
 from fractions import Fraction as Fr
 import numpy as np
@@ -25,6 +34,30 @@ def esdirk3():
     b = A[3].copy()
     c = A.sum(axis=1)
     return A, b, c
+
+
+def esdirk2():
+    g = 1.0 - 1.0 / np.sqrt(2.0)
+    bb = 0.5 * (1.0 - g)
+    A = np.array([[0.0, 0.0, 0.0],
+                  [g, g, 0.0],
+                  [bb, bb, g]])
+    return A, A[2].copy(), A.sum(axis=1)
+
+
+def esdirk4():
+    g = Fr(1, 4)
+    z = Fr(0)
+    A = [[z, z, z, z, z, z],
+         [g, g, z, z, z, z],
+         [Fr(8611, 62500), Fr(-1743, 31250), g, z, z, z],
+         [Fr(5012029, 34652500), Fr(-654441, 2922500), Fr(174375, 388108), g, z, z],
+         [Fr(15267082809, 155376265600), Fr(-71443401, 120774400), Fr(730878875, 902184768),
+          Fr(2285395, 8070912), g, z],
+         [Fr(82889, 524892), z, Fr(15625, 83664), Fr(69875, 102672), Fr(-2260, 8211), g]]
+    c = np.array([float(sum(row)) for row in A])
+    A = np.array([[float(x) for x in row] for row in A])
+    return A, A[5].copy(), c
 
 
 def ros34pw2_standard():

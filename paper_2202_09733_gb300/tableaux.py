@@ -1,4 +1,4 @@
-"""Third-order time-integration schemes in the forms the paper writes them.
+"""Time-integration schemes in the forms the paper writes them.
 
 The paper (Eqs. 2-3) gives the ESDIRK and Rosenbrock-Wanner forms and cites its own
 second/fourth-order schemes; the two schemes used here are published members of those
@@ -7,7 +7,12 @@ families:
              implicit part of ARK3(2)4L[2]SA), coefficients as exact rationals;
   ROS34PW2 - four-stage third-order W-method of Rang & Angermann, converted from the
              standard (alpha, gamma, b) coefficients to the variables of Eq. (3):
-             a = alpha Gamma^-1, c = diag(1/gamma) - Gamma^-1, m = b Gamma^-1.
+             a = alpha Gamma^-1, c = diag(1/gamma) - Gamma^-1, m = b Gamma^-1;
+and the paper's own ESDIRK schemes (named in Sec. 2.1, coefficients not printed there):
+  ESDIRK2  - three stages, second order, L-stable, stiffly accurate (Kennedy & Carpenter's
+             review): gamma = 1 - 1/sqrt(2), c2 = 2 gamma, last row b1 = b2 = (1 - gamma)/2;
+  ESDIRK4  - six stages, fourth order, L-stable, stiffly accurate, gamma = 1/4 (Bijl et
+             al.; the implicit part of Kennedy & Carpenter's ARK4(3)6L[2]SA).
 """
 from fractions import Fraction
 
@@ -24,6 +29,35 @@ def esdirk3():
              Fraction(11266239266428, 11593286722821), g]]
     A = np.array([[float(x) for x in r] for r in rows])
     return A, A[3].copy()
+
+
+def esdirk2():
+    """(A, b): 3x3, A[0] = 0, b = A[2]."""
+    gam = 1.0 - 1.0 / np.sqrt(2.0)
+    w = 0.5 * (1.0 - gam)
+    A = np.zeros((3, 3))
+    A[1, :2] = gam
+    A[2] = (w, w, gam)
+    return A, A[2].copy()
+
+
+def esdirk4():
+    """(A, b): 6x6, A[0] = 0, b = A[5], exact rationals rounded once."""
+    F = Fraction
+    q = F(1, 4)
+    lower = {(1, 0): q,
+             (2, 0): F(8611, 62500), (2, 1): F(-1743, 31250),
+             (3, 0): F(5012029, 34652500), (3, 1): F(-654441, 2922500), (3, 2): F(174375, 388108),
+             (4, 0): F(15267082809, 155376265600), (4, 1): F(-71443401, 120774400),
+             (4, 2): F(730878875, 902184768), (4, 3): F(2285395, 8070912),
+             (5, 0): F(82889, 524892), (5, 2): F(15625, 83664), (5, 3): F(69875, 102672),
+             (5, 4): F(-2260, 8211)}
+    A = np.zeros((6, 6))
+    for (i, j), x in lower.items():
+        A[i, j] = float(x)
+    for i in range(1, 6):
+        A[i, i] = float(q)
+    return A, A[5].copy()
 
 
 def ros34pw2():

@@ -185,7 +185,8 @@ def test_gmres_fixed_iterations(case):
     assert relerr(x_gpu, x_or) <= 1e-5
 
 
-def test_esdirk_step_converged_state():
+@pytest.mark.parametrize("scheme", ["esdirk3", "esdirk2", "esdirk4"])
+def test_esdirk_step_converged_state(scheme):
     mesh = w.box2d(4, 4, 10, 10, qg=2, warp=0.1)
     ph = w.Physics(mu=0.01, qinf=w.freestream(2, 0.5))
     X = w.solution_point_coords(mesh, 2)
@@ -193,12 +194,12 @@ def test_esdirk_step_converged_state():
     dt = 10.0 * w.explicit_dt(mesh, 2, q0)
     O = oracle.Oracle(mesh, ph, [2, 1])
     G = api.fr_create(mesh, ph, [2, 1])
-    A, b, _ = OT.esdirk3()
+    A, b, _ = getattr(OT, scheme)()
     oo = O.opts(kdim=30, maxit_gmres=300, max_ptc=40, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-12, dtau=dt,
                 inv_dtau_star=1.0 / dt)
     q_or, st_or = O.esdirk_step(A, b, dt, q0, oo)
     from paper_2202_09733_gb300 import tableaux as GT
-    Ag, bg = GT.esdirk3()
+    Ag, bg = getattr(GT, scheme)()
     go = api.solve_opts(kdim=30, maxit_gmres=300, max_ptc=40, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-12,
                         dtau=dt, inv_dtau_star=1.0 / dt)
     qg = dev(q0)
