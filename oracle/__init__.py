@@ -59,7 +59,14 @@ def lib():
         L.or_lu_solve.argtypes = [C.c_int, PD, PI, PD]
         L.or_restrict.argtypes = [C.c_void_p, C.c_int, PD, PD]
         L.or_prolong.argtypes = [C.c_void_p, C.c_int, PD, PD]
-        L.or_pmg_setup.argtypes = [C.c_void_p, PD, C.c_int, PI, C.c_double, C.c_double]
+        L.or_pmg_setup.argtypes = [C.c_void_p, PD, C.c_int, PI, C.c_double, C.c_double, C.c_int, C.c_int,
+                                   C.c_double]
+        L.or_neighbours.argtypes = [C.c_void_p, PI]
+        L.or_nbr_blocks.argtypes = [C.c_void_p, C.c_int, PD, PI, PD]
+        L.or_mbnk_matvec.argtypes = [C.c_void_p, C.c_int, PD, PD]
+        L.or_mbnk_solve.argtypes = [C.c_void_p, C.c_int, PD]
+        L.or_mbnk_last_iters.restype = C.c_int
+        L.or_mbnk_last_relres.restype = C.c_double
         L.or_pmg_apply.argtypes = [C.c_void_p, PD, PD, PD, PD]
         L.or_block_solve.argtypes = [C.c_void_p, C.c_int, PD]
         L.or_gmres.argtypes = [C.c_void_p, PD, PD, PD, PD, C.c_int, C.c_double, C.c_int, C.c_double,
@@ -104,7 +111,8 @@ class SolveOpts(C.Structure):
     _fields_ = [("kdim", C.c_int), ("maxit_gmres", C.c_int), ("max_ptc", C.c_int), ("nlev", C.c_int),
                 ("nsmooth", C.c_int * 4), ("use_pmg", C.c_int), ("tol_gmres", C.c_double),
                 ("tol_newton", C.c_double), ("eps", C.c_double), ("dtau", C.c_double),
-                ("inv_dtau_star", C.c_double)]
+                ("inv_dtau_star", C.c_double), ("mbnk", C.c_int), ("mbnk_maxit", C.c_int),
+                ("mbnk_tol", C.c_double)]
 
 
 class StepStats(C.Structure):
@@ -219,9 +227,40 @@ class Oracle:
         lib().or_jacobian(self.h, l, _d(out))
         return out
 
-    def pmg_setup(self, q_ref, nsmooth, c, inv_dtau_star):
+    def pmg_setup(self, q_ref, nsmooth, c, inv_dtau_star, coarse="ej", mbnk_maxit=5, mbnk_tol=0.1):
+        """coarse: "ej" (element-Jacobi blocks on every level) or "mbnk" (the matrix-based
+        Newton-Krylov smoother on the coarsest level: GMRES of at most mbnk_maxit
+        iterations to the relative tolerance mbnk_tol on the assembled operator)."""
         ns = np.array(nsmooth, dtype=np.int32)
-        lib().or_pmg_setup(self.h, _d(np.ascontiguousarray(q_ref)), len(ns), _i(ns), c, inv_dtau_star)
+        lib().or_pmg_setup(self.h, _d(np.ascontiguousarray(q_ref)), len(ns), _i(ns), c, inv_dtau_star,
+                           int(coarse == "mbnk"), int(mbnk_maxit), float(mbnk_tol))
+
+    def neighbours(self):
+        """[E, 2d] face-neighbour table (-1: boundary, self or repeated neighbour)."""
+        nbr = np.zeros(self.E * 2 * self.d, dtype=np.int32)
+        lib().or_neighbours(self.h, _i(nbr))
+        return nbr.reshape(self.E, 2 * self.d)
+
+    def nbr_blocks(self, q, l=0):
+        """[E, 2d, nd, nd] blocks -dR_e/dq_nbr(e,f) (row-major), zero where there is no neighbour."""
+        nbr = np.ascontiguousarray(self.neighbours().ravel())
+        nd = self.nv * self.np_(l)
+        O = np.zeros(self.E * 2 * self.d * nd * nd)
+        lib().or_nbr_blocks(self.h, l, _d(np.ascontiguousarray(q)), _i(nbr), _d(O))
+        return O.reshape(self.E, 2 * self.d, nd, nd)
+
+    def mbnk_matvec(self, x, l):
+        """A x with the coarsest level's assembled operator of the last pmg_setup(coarse="mbnk")."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros_like(x)
+        lib().or_mbnk_matvec(self.h, l, _d(x), _d(y))
+        return y
+
+    def mbnk_solve(self, r, l):
+        """(delta, iterations, relative residual estimate) of one matrix-based smoothing solve."""
+        x = np.ascontiguousarray(r, dtype=np.float64).copy()
+        lib().or_mbnk_solve(self.h, l, _d(x))
+        return x, int(lib().or_mbnk_last_iters()), float(lib().or_mbnk_last_relres())
 
     def pmg_apply(self, q, Rq, X):
         Y = np.zeros(self.shape(0))
@@ -244,8 +283,9 @@ class Oracle:
 
     @staticmethod
     def opts(kdim=30, maxit_gmres=300, max_ptc=100, nsmooth=(2, 2), use_pmg=True, tol_gmres=1e-1,
-             tol_newton=1e-8, eps=1e-6, dtau=1.0, inv_dtau_star=0.0):
+             tol_newton=1e-8, eps=1e-6, dtau=1.0, inv_dtau_star=0.0, coarse="ej", mbnk_maxit=5, mbnk_tol=0.1):
         o = SolveOpts()
+        o.mbnk, o.mbnk_maxit, o.mbnk_tol = int(coarse == "mbnk"), int(mbnk_maxit), float(mbnk_tol)
         o.kdim, o.maxit_gmres, o.max_ptc, o.nlev = kdim, maxit_gmres, max_ptc, len(nsmooth)
         for i, n in enumerate(nsmooth):
             o.nsmooth[i] = n

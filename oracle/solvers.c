@@ -61,12 +61,73 @@ void or_jvp(or_ctx *C, const double *q, const double *Rq, const double *v, doubl
     free(qp); free(Rp);
 }
 
+/* ------------------------------------------------------------------ face neighbours */
+/* nbr[e * 2d + f] = the element across local face f of element e, or -1 where that face
+ * is a boundary, where it wraps onto e itself (a periodic mesh one element wide: that
+ * coupling belongs to the diagonal block) or where an earlier face of e already reaches
+ * the same element (a periodic mesh two elements wide: the first such face's block then
+ * holds the whole coupling).  Faces rows are (eL, fL, eR, fR, orient, bc). */
+void or_neighbours(const or_ctx *C, int *nbr) {
+    int nf = 2 * C->d, E = C->E;
+    for (int i = 0; i < E * nf; ++i) nbr[i] = -1;
+    for (int F = 0; F < C->nfaces; ++F) {
+        const int *fc = &C->faces[6 * F];
+        if (fc[2] < 0 || fc[2] == fc[0]) continue;
+        nbr[fc[0] * nf + fc[1]] = fc[2];
+        nbr[fc[2] * nf + fc[3]] = fc[0];
+    }
+    for (int e = 0; e < E; ++e)
+        for (int f = 0; f < nf; ++f)
+            for (int g = 0; g < f; ++g)
+                if (nbr[e * nf + f] >= 0 && nbr[e * nf + g] == nbr[e * nf + f]) nbr[e * nf + f] = -1;
+}
+
+/* Off-diagonal blocks of the shifted Jacobian A = shift I - dR/dq on level l at q: for
+ * element e and face slot f with neighbour n = nbr[e][f], block (e, f) is -dR_e/dq_n,
+ * column j the forward difference of the whole residual with the step
+ * eps_j = 1e-7 max(1, |q_n,j|) on dof j of element n alone (the element blocks' step).
+ * Stored row-major per block: O[((e * 2d + f) * nd + r) * nd + j]. */
+void or_nbr_blocks(or_ctx *C, int l, const double *q, const int *nbr, double *O) {
+    or_level *L = &C->L[l];
+    int E = C->E, nd = C->nv * L->np, nf = 2 * C->d;
+    size_t N = (size_t)nd * E;
+    double *R0 = malloc(sizeof(double) * N), *Rp = malloc(sizeof(double) * N), *qp = malloc(sizeof(double) * N);
+    memset(O, 0, sizeof(double) * (size_t)E * nf * nd * nd);
+    or_residual(C, l, q, R0);
+    memcpy(qp, q, sizeof(double) * N);
+    for (int n = 0; n < E; ++n)
+        for (int j = 0; j < nd; ++j) {
+            double x = q[(size_t)j * E + n];
+            double eps = 1e-7 * fmax(1.0, fabs(x));
+            qp[(size_t)j * E + n] = x + eps;
+            or_residual(C, l, qp, Rp);
+            qp[(size_t)j * E + n] = x;
+            for (int e = 0; e < E; ++e)
+                for (int f = 0; f < nf; ++f) {
+                    if (nbr[e * nf + f] != n) continue;
+                    double *B = &O[(size_t)(e * nf + f) * nd * nd];
+                    for (int r = 0; r < nd; ++r) {
+                        double m = (Rp[(size_t)r * E + e] - R0[(size_t)r * E + e]) / eps;
+                        B[(size_t)r * nd + j] = -m;
+                    }
+                }
+        }
+    free(R0); free(Rp); free(qp);
+}
+
 /* ------------------------------------------------------------------ pMG */
 typedef struct {
     int nlev, nsmooth[OR_MAXLEV];
     double c, inv_dtau_star;
     double *M[OR_MAXLEV];
     int *piv[OR_MAXLEV];
+    /* matrix-based Newton-Krylov smoother on the coarsest level (Sec. 3.2) */
+    int mbnk, mbnk_maxit;
+    double mbnk_tol;
+    double *Md, *O;                    /* unfactored diagonal blocks, neighbour blocks */
+    int *nbr;
+    int mbnk_last_iters;
+    double mbnk_last_relres;
     int ready;
 } or_pmg;
 
@@ -74,13 +135,20 @@ static or_pmg g_pmg;
 
 static void pmg_free(void) {
     for (int l = 0; l < OR_MAXLEV; ++l) { free(g_pmg.M[l]); free(g_pmg.piv[l]); g_pmg.M[l] = 0; g_pmg.piv[l] = 0; }
+    free(g_pmg.Md); free(g_pmg.O); free(g_pmg.nbr);
+    g_pmg.Md = 0; g_pmg.O = 0; g_pmg.nbr = 0;
     g_pmg.ready = 0;
 }
 
-/* blocks at the reference state q_ref (restricted level by level) and their LU factors */
-void or_pmg_setup(or_ctx *C, const double *q_ref, int nlev, const int *nsmooth, double c, double inv_dtau_star) {
+/* blocks at the reference state q_ref (restricted level by level) and their LU factors;
+ * mbnk != 0: the coarsest level also keeps its assembled operator (diagonal and neighbour
+ * blocks) for the matrix-based smoother, GMRES of at most mbnk_maxit iterations to the
+ * relative tolerance mbnk_tol */
+void or_pmg_setup(or_ctx *C, const double *q_ref, int nlev, const int *nsmooth, double c, double inv_dtau_star,
+                  int mbnk, int mbnk_maxit, double mbnk_tol) {
     pmg_free();
     g_pmg.nlev = nlev; g_pmg.c = c; g_pmg.inv_dtau_star = inv_dtau_star;
+    g_pmg.mbnk = mbnk; g_pmg.mbnk_maxit = mbnk_maxit; g_pmg.mbnk_tol = mbnk_tol;
     for (int l = 0; l < nlev; ++l) g_pmg.nsmooth[l] = nsmooth[l];
     int E = C->E;
     int *all = malloc(sizeof(int) * E);
@@ -92,6 +160,15 @@ void or_pmg_setup(or_ctx *C, const double *q_ref, int nlev, const int *nsmooth, 
         g_pmg.M[l] = malloc(sizeof(double) * (size_t)nd * nd * E);
         g_pmg.piv[l] = malloc(sizeof(int) * (size_t)nd * E);
         or_elem_blocks(C, l, qr, inv_dtau_star + c, all, E, g_pmg.M[l]);
+        if (mbnk && l == nlev - 1) {
+            int nf = 2 * C->d;
+            g_pmg.Md = malloc(sizeof(double) * (size_t)nd * nd * E);
+            memcpy(g_pmg.Md, g_pmg.M[l], sizeof(double) * (size_t)nd * nd * E);
+            g_pmg.nbr = malloc(sizeof(int) * (size_t)E * nf);
+            or_neighbours(C, g_pmg.nbr);
+            g_pmg.O = malloc(sizeof(double) * (size_t)E * nf * nd * nd);
+            or_nbr_blocks(C, l, qr, g_pmg.nbr, g_pmg.O);
+        }
         for (int e = 0; e < E; ++e)
             or_lu_factor(nd, &g_pmg.M[l][(size_t)e * nd * nd], &g_pmg.piv[l][(size_t)e * nd]);
         if (l + 1 < nlev) {
@@ -127,6 +204,94 @@ static void pmg_rhs(size_t N, double c, const double *d, const double *qh, const
     }
 }
 
+/* y = A x with the assembled operator of the coarsest level:
+ * y_e = Md_e x_e + sum_f O_(e,f) x_nbr(e,f) */
+void or_mbnk_matvec(or_ctx *C, int l, const double *x, double *y) {
+    int E = C->E, nd = C->nv * C->L[l].np, nf = 2 * C->d;
+    for (int e = 0; e < E; ++e)
+        for (int r = 0; r < nd; ++r) {
+            double acc = 0.0;
+            const double *Me = &g_pmg.Md[(size_t)e * nd * nd + (size_t)r * nd];
+            for (int j = 0; j < nd; ++j) acc = fma(Me[j], x[(size_t)j * E + e], acc);
+            for (int f = 0; f < nf; ++f) {
+                int n = g_pmg.nbr[e * nf + f];
+                if (n < 0) continue;
+                const double *B = &g_pmg.O[(size_t)(e * nf + f) * nd * nd + (size_t)r * nd];
+                for (int j = 0; j < nd; ++j) acc = fma(B[j], x[(size_t)j * E + n], acc);
+            }
+            y[(size_t)r * E + e] = acc;
+        }
+}
+
+/* one matrix-based Newton-Krylov smoothing solve (Sec. 3.2): GMRES on A delta = r from
+ * delta = 0, right-preconditioned by the element blocks (delta = Md^{-1} V y), modified
+ * Gram-Schmidt, Givens rotations; it stops after the first iteration k whose residual
+ * estimate |g_k+1| is <= mbnk_tol ||r||, or after mbnk_maxit iterations.  In place:
+ * x holds r on entry and delta on return. */
+void or_mbnk_solve(or_ctx *C, int l, double *x) {
+    size_t N = vlen(C, l);
+    int m = g_pmg.mbnk_maxit;
+    double *V = calloc((size_t)(m + 1) * N, sizeof(double)), *w = malloc(sizeof(double) * N);
+    double *z = malloc(sizeof(double) * N);
+    double *H = calloc((size_t)(m + 1) * m, sizeof(double));      /* H[i * m + k] */
+    double *cs = calloc(m, sizeof(double)), *sn = calloc(m, sizeof(double)), *g = calloc(m + 1, sizeof(double));
+    double *y = calloc(m, sizeof(double));
+    double beta = sqrt(dot(N, x, x));
+    int k_used = 0;
+    g_pmg.mbnk_last_relres = 0.0;
+    if (beta > 0.0) {
+        for (size_t i = 0; i < N; ++i) V[i] = x[i] / beta;
+        g[0] = beta;
+        for (int k = 0; k < m; ++k) {
+            double *vk = &V[(size_t)k * N], *vn = &V[(size_t)(k + 1) * N];
+            memcpy(z, vk, sizeof(double) * N);
+            block_solve(C, l, z);
+            or_mbnk_matvec(C, l, z, w);
+            for (int i = 0; i <= k; ++i) {
+                double h = dot(N, w, &V[(size_t)i * N]);
+                H[i * m + k] = h;
+                for (size_t t = 0; t < N; ++t) w[t] = w[t] - h * V[(size_t)i * N + t];
+            }
+            double hn = sqrt(dot(N, w, w));
+            H[(k + 1) * m + k] = hn;
+            if (hn > 0.0)
+                for (size_t t = 0; t < N; ++t) vn[t] = w[t] / hn;
+            /* earlier rotations on the new column, then the rotation that zeroes H[k+1][k] */
+            for (int i = 0; i < k; ++i) {
+                double a = H[i * m + k], b = H[(i + 1) * m + k];
+                H[i * m + k] = cs[i] * a + sn[i] * b;
+                H[(i + 1) * m + k] = -sn[i] * a + cs[i] * b;
+            }
+            double a = H[k * m + k], b = H[(k + 1) * m + k], rr = hypot(a, b);
+            cs[k] = rr > 0.0 ? a / rr : 1.0;
+            sn[k] = rr > 0.0 ? b / rr : 0.0;
+            H[k * m + k] = rr;
+            H[(k + 1) * m + k] = 0.0;
+            g[k + 1] = -sn[k] * g[k];
+            g[k] = cs[k] * g[k];
+            k_used = k + 1;
+            if (fabs(g[k + 1]) <= g_pmg.mbnk_tol * beta) break;
+        }
+        g_pmg.mbnk_last_relres = fabs(g[k_used]) / beta;
+        for (int i = k_used - 1; i >= 0; --i) {
+            double t = g[i];
+            for (int j = i + 1; j < k_used; ++j) t = t - H[i * m + j] * y[j];
+            y[i] = H[i * m + i] != 0.0 ? t / H[i * m + i] : 0.0;
+        }
+    }
+    for (size_t t = 0; t < N; ++t) {
+        double acc = 0.0;
+        for (int j = 0; j < k_used; ++j) acc = acc + y[j] * V[(size_t)j * N + t];
+        x[t] = acc;
+    }
+    block_solve(C, l, x);
+    g_pmg.mbnk_last_iters = k_used;
+    free(V); free(w); free(z); free(H); free(cs); free(sn); free(g); free(y);
+}
+
+int or_mbnk_last_iters(void) { return g_pmg.mbnk_last_iters; }
+double or_mbnk_last_relres(void) { return g_pmg.mbnk_last_relres; }
+
 static void smooth(or_ctx *C, int l, int nsteps, const double *b, const double *Rb, const double *d,
                    double *qh, int first_is_base) {
     size_t N = vlen(C, l);
@@ -137,7 +302,8 @@ static void smooth(or_ctx *C, int l, int nsteps, const double *b, const double *
             or_residual(C, l, qh, Rqh);
             pmg_rhs(N, g_pmg.c, d, qh, b, Rqh, Rb, rhs);
         }
-        block_solve(C, l, rhs);
+        if (g_pmg.mbnk && l == g_pmg.nlev - 1) or_mbnk_solve(C, l, rhs);
+        else block_solve(C, l, rhs);
         for (size_t i = 0; i < N; ++i) qh[i] = qh[i] + rhs[i];
     }
     free(Rqh); free(rhs);
@@ -266,6 +432,8 @@ done:
 typedef struct {
     int kdim, maxit_gmres, max_ptc, nlev, nsmooth[OR_MAXLEV], use_pmg;
     double tol_gmres, tol_newton, eps, dtau, inv_dtau_star;
+    int mbnk, mbnk_maxit;              /* matrix-based smoother on the coarsest level */
+    double mbnk_tol;
 } or_solve_opts;
 
 typedef struct { int n_ptc, n_gmres, converged; double final_res; } or_step_stats;
@@ -289,7 +457,7 @@ int or_esdirk_step(or_ctx *C, int s, const double *A, const double *bw, double d
     st->converged = 1;
     double aii = A[1 * s + 1];
     double c = 1.0 / o->dtau + 1.0 / (aii * dt);
-    if (o->use_pmg) or_pmg_setup(C, qn, o->nlev, o->nsmooth, c, o->inv_dtau_star);
+    if (o->use_pmg) or_pmg_setup(C, qn, o->nlev, o->nsmooth, c, o->inv_dtau_star, o->mbnk, o->mbnk_maxit, o->mbnk_tol);
     for (int i = 1; i < s; ++i) {
         double adt = A[i * s + i] * dt;
         for (size_t t = 0; t < N; ++t) {
@@ -339,7 +507,7 @@ int or_row_step(or_ctx *C, int s, double gam, const double *a, const double *cc,
     memset(st, 0, sizeof(*st));
     st->converged = 1;
     double c = 1.0 / (gam * dt);
-    if (o->use_pmg) or_pmg_setup(C, qn, o->nlev, o->nsmooth, c, o->inv_dtau_star);
+    if (o->use_pmg) or_pmg_setup(C, qn, o->nlev, o->nsmooth, c, o->inv_dtau_star, o->mbnk, o->mbnk_maxit, o->mbnk_tol);
     for (int i = 0; i < s; ++i) {
         for (size_t t = 0; t < N; ++t) {
             double acc = 0.0;
@@ -382,7 +550,9 @@ int or_ptc_steady(or_ctx *C, double *q, double dtau_init, double dtau_max, doubl
     for (k = 0; k < max_it; ++k) {
         if (rk <= tol_rel * r0) break;
         double c = 1.0 / dtau;
-        if (o->use_pmg) or_pmg_setup(C, q, o->nlev, o->nsmooth, c, o->inv_dtau_star < 0 ? c : o->inv_dtau_star);
+        if (o->use_pmg)
+            or_pmg_setup(C, q, o->nlev, o->nsmooth, c, o->inv_dtau_star < 0 ? c : o->inv_dtau_star, o->mbnk,
+                         o->mbnk_maxit, o->mbnk_tol);
         or_gmres_stats gs;
         or_gmres(C, q, R, R, dq, o->kdim, o->tol_gmres, o->maxit_gmres, c, o->eps, o->use_pmg, &gs);
         st->n_gmres += gs.iters;
@@ -417,7 +587,8 @@ int or_pmg_steady(or_ctx *C, double *q, double dtau_init, double dtau_max, doubl
     for (int k = 0; k < max_it; ++k) {
         if (rk <= tol_rel * r0) break;
         double c = 1.0 / dtau;
-        or_pmg_setup(C, q, o->nlev, o->nsmooth, c, o->inv_dtau_star < 0 ? c : o->inv_dtau_star);
+        or_pmg_setup(C, q, o->nlev, o->nsmooth, c, o->inv_dtau_star < 0 ? c : o->inv_dtau_star, o->mbnk,
+                     o->mbnk_maxit, o->mbnk_tol);
         or_pmg_apply(C, q, R, R, Y);
         for (size_t t = 0; t < N; ++t) q[t] = q[t] + Y[t];
         or_residual(C, 0, q, R);
