@@ -124,6 +124,22 @@ int fr_jvp(fr_ctx *ctx, const double *q, const double *Rq, const double *v, doub
  * E * nd * nd doubles, column-major per element (see Layouts). */
 int fr_elem_blocks(fr_ctx *ctx, int level, const double *q, double shift, double *M, void *stream);
 
+/* Sec. 3.2 matrix-based smoother: the element blocks M (as fr_elem_blocks) and the face
+ * neighbour blocks O of the shifted Jacobian on a level in one pass over a distance-2
+ * colouring: O[((e nf + f) nd + j) nd + r] (column-major per block, nf = 2d slots per
+ * element) = -dR_e[r]/dq_n[j] for the neighbour n = nbr[f E + e], by the forward difference
+ * with step 1e-7 max(1, |q_n,j|); zero where nbr is -1.  q: device level state; M, O:
+ * device, E nd^2 and E nf nd^2 doubles. */
+int fr_nbr_blocks(fr_ctx *ctx, int level, const double *q, double shift, double *M, double *O, void *stream);
+/* face-neighbour table nbr[f E + e] (host, 2d E ints): the element across local face f of
+ * element e; -1 for a boundary face, a face wrapping onto e itself (that coupling is in
+ * the element block) and any face after the first reaching the same element (the first
+ * slot's block holds the whole coupling). */
+int fr_neighbour_table(const fr_ctx *ctx, int *nbr);
+/* iterations and relative residual estimate of the last matrix-based smoothing solve
+ * (synchronises); FR_ERR_NOT_READY before the first one. */
+int fr_mbnk_last(const fr_ctx *ctx, int *iters, double *relres);
+
 /* In-place LU with partial pivoting of every block (first maximal |pivot|).  M as above,
  * receives L (unit, below the diagonal), U (above) and 1/u_kk on the diagonal; perm:
  * device int [E][nd], receives the row permutation (row i of LU is row perm[i] of the
@@ -154,13 +170,27 @@ int fr_prolong(fr_ctx *ctx, int level, const double *x_coarse, double *x_fine, v
  * min_v max|q_ref,v|) and follows the gain measured by the previous call, and a call
  * that lands more than 30x off repeats its cycle once at the measured gain), and Y is
  * scaled back and returned in FP64.  Each mixed call reads nv maxima back to the host
- * (one stream synchronisation). */
+ * (one stream synchronisation).
+ * coarse_smoother 0: element-Jacobi smoothing on every level.  1: the matrix-based
+ * Newton-Krylov (MBNK) smoother of Sec. 3.2 on the coarsest level: its linearised operator
+ * (1/dtau* + c) I - dR/dq is assembled at q_ref as the element blocks plus one block per
+ * face neighbour (finite differences in FP64, forward-mode derivatives in FP32, over a
+ * distance-2 colouring), and each smoothing step there solves it by GMRES (classical
+ * Gram-Schmidt with one re-orthogonalisation) from zero, right-preconditioned by the
+ * factored element blocks, stopping at the first iteration whose residual estimate is
+ * <= mbnk_tol ||rhs|| or after mbnk_maxit (1..16) iterations; the paper uses 5 and 1e-1,
+ * with per-block ILU0 where this uses the element blocks.  The whole GMRES runs on the
+ * device with no host synchronisation (iterations after the stopping one are computed
+ * and discarded), so the cycle stays capturable.  Extra device memory on the coarsest
+ * level: E (2d + 1) nd^2 + (mbnk_maxit + 3) N values of the cycle's precision. */
 typedef struct {
     int nlevels;
     int nsmooth[4];
     double c;
     double inv_dtau_star;
     int precision;
+    int coarse_smoother, mbnk_maxit;
+    double mbnk_tol;
 } fr_pmg_opts;
 int pmg_setup(fr_ctx *ctx, const double *q_ref, const fr_pmg_opts *opts, void *stream);
 /* Y ~ A^{-1} X: one V-cycle of pseudo-time marching of
@@ -203,6 +233,8 @@ typedef struct {
      * samples at learning rate lr. */
     int guess, train_iters, train_batch;
     double lr;
+    int coarse_smoother, mbnk_maxit;   /* as fr_pmg_opts (when use_pmg) */
+    double mbnk_tol;
 } fr_solve_opts;
 typedef struct {
     int n_ptc, n_gmres, converged;
@@ -359,7 +391,8 @@ int fr_batch_info(const fr_batch *batch, int *ngroups, int *group_of, int *elem_
 int fr_batch_set_graphs(fr_batch *batch, int on);
 /* R(q_k) for every problem: q, R host arrays of nprob device pointers ([nv][Np][E_k] each) */
 int fr_batch_residual(fr_batch *batch, double *const *q, double *const *R, void *stream);
-/* one ESDIRK step (as esdirk_step, guess 0, kdim <= 62) of every problem: q host array of
+/* one ESDIRK step (as esdirk_step, guess 0, kdim <= 62, element-Jacobi smoothing on every
+ * level: coarse_smoother 1 is FR_ERR_UNIMPLEMENTED) of every problem: q host array of
  * nprob device pointers, updated in place; stats host [nprob] (may be NULL).  Returns
  * FR_ERR_NOT_CONVERGED if any problem missed the Newton tolerance (all states are still
  * advanced). */

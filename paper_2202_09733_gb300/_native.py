@@ -19,7 +19,7 @@ ERRORS = {-1: "FR_ERR_INVALID_ARG", -2: "FR_ERR_CUDA", -3: "FR_ERR_OOM", -4: "FR
 # every symbol the header declares
 EXPORTS = ["fr_create", "fr_destroy", "fr_last_error", "fr_kernel_launches", "fr_level_info", "fr_num_colors", "fr_residual",
            "fr_residual_noalloc", "fr_jvp",
-           "fr_elem_blocks", "fr_block_factor", "fr_block_solve", "fr_restrict", "fr_prolong", "pmg_setup",
+           "fr_elem_blocks", "fr_nbr_blocks", "fr_neighbour_table", "fr_mbnk_last", "fr_block_factor", "fr_block_solve", "fr_restrict", "fr_prolong", "pmg_setup",
            "pmg_precondition", "gmres_solve", "esdirk_step", "row_step", "ptc_steady",
            "mlp_create", "mlp_destroy", "mlp_get_params", "mlp_forward", "mlp_train_step", "fr_mlp_dims",
            "fr_set_mlp", "fr_reset_history", "fr_guess_features", "fr_batch_create", "fr_batch_destroy",
@@ -41,7 +41,8 @@ class Physics(C.Structure):
 
 class PmgOpts(C.Structure):
     _fields_ = [("nlevels", C.c_int), ("nsmooth", C.c_int * 4), ("c", C.c_double), ("inv_dtau_star", C.c_double),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("coarse_smoother", C.c_int), ("mbnk_maxit", C.c_int),
+                ("mbnk_tol", C.c_double)]
 
 
 class GmresOpts(C.Structure):
@@ -58,7 +59,8 @@ class SolveOpts(C.Structure):
                 ("nsmooth", C.c_int * 4), ("use_pmg", C.c_int), ("tol_gmres", C.c_double),
                 ("tol_newton", C.c_double), ("eps", C.c_double), ("dtau", C.c_double),
                 ("inv_dtau_star", C.c_double), ("precision", C.c_int), ("guess", C.c_int),
-                ("train_iters", C.c_int), ("train_batch", C.c_int), ("lr", C.c_double)]
+                ("train_iters", C.c_int), ("train_batch", C.c_int), ("lr", C.c_double),
+                ("coarse_smoother", C.c_int), ("mbnk_maxit", C.c_int), ("mbnk_tol", C.c_double)]
 
 
 class StepStats(C.Structure):
@@ -98,6 +100,9 @@ def load(path: str = LIB_PATH):
         "fr_residual_noalloc": ([VP, C.c_int, VP, VP, VP], C.c_int),
         "fr_jvp": ([VP, VP, VP, VP, C.c_double, C.c_double, VP, VP], C.c_int),
         "fr_elem_blocks": ([VP, C.c_int, VP, C.c_double, VP, VP], C.c_int),
+        "fr_nbr_blocks": ([VP, C.c_int, VP, C.c_double, VP, VP, VP], C.c_int),
+        "fr_neighbour_table": ([VP, PI], C.c_int),
+        "fr_mbnk_last": ([VP, PI, PD], C.c_int),
         "fr_block_factor": ([VP, C.c_int, VP, VP, VP], C.c_int),
         "fr_block_solve": ([VP, C.c_int, VP, VP, VP, VP], C.c_int),
         "fr_restrict": ([VP, C.c_int, VP, VP, VP], C.c_int),

@@ -106,6 +106,31 @@ def fr_elem_blocks(ctx, level, q, shift, M=None, stream=None):
     return M
 
 
+def fr_nbr_blocks(ctx, level, q, shift, stream=None):
+    """(M, O): element blocks [E, nd(col), nd(row)] and face-neighbour blocks
+    [E, 2d, nd(col), nd(row)] (column-major per block) of the shifted Jacobian."""
+    nd, nf = ctx.nd(level), 2 * ctx.d
+    M = torch.empty((ctx.E, nd, nd), dtype=torch.float64, device="cuda")
+    O = torch.empty((ctx.E, nf, nd, nd), dtype=torch.float64, device="cuda")
+    N.check(N.load().fr_nbr_blocks(ctx.handle, level, _dev(q), float(shift), _dev(M), _dev(O), _stream(stream)),
+            "fr_nbr_blocks")
+    return M, O
+
+
+def fr_neighbour_table(ctx):
+    """[E, 2d] face-neighbour table (-1: boundary, self or repeated neighbour)."""
+    nbr = np.zeros(2 * ctx.d * ctx.E, dtype=np.int32)
+    N.check(N.load().fr_neighbour_table(ctx.handle, nbr.ctypes.data_as(N.PI)), "fr_neighbour_table")
+    return nbr.reshape(2 * ctx.d, ctx.E).T.copy()
+
+
+def fr_mbnk_last(ctx):
+    """(iterations, relative residual estimate) of the last matrix-based smoothing solve."""
+    it, rel = C.c_int(), C.c_double()
+    N.check(N.load().fr_mbnk_last(ctx.handle, C.byref(it), C.byref(rel)), "fr_mbnk_last")
+    return it.value, rel.value
+
+
 def fr_block_factor(ctx, level, M, perm=None, stream=None):
     perm = torch.empty((ctx.E, ctx.nd(level)), dtype=torch.int32, device="cuda") if perm is None else perm
     N.check(N.load().fr_block_factor(ctx.handle, level, _dev(M), _dev(perm, torch.int32), _stream(stream)),
@@ -131,14 +156,24 @@ def fr_prolong(ctx, level, xc, xf=None, stream=None):
     return xf
 
 
-def pmg_setup(ctx, q_ref, nsmooth, c, inv_dtau_star, precision="fp64", stream=None):
-    """precision: "fp64" (reproducible) or "mixed" (FP32 cycle, blocks and LU)."""
+def _coarse(coarse):
+    if coarse not in ("ej", "mbnk"):
+        raise ValueError('coarse must be "ej" (element-Jacobi) or "mbnk" (matrix-based Newton-Krylov)')
+    return int(coarse == "mbnk")
+
+
+def pmg_setup(ctx, q_ref, nsmooth, c, inv_dtau_star, precision="fp64", stream=None, coarse="ej", mbnk_maxit=5,
+              mbnk_tol=0.1):
+    """precision: "fp64" (reproducible) or "mixed" (FP32 cycle, blocks and LU).  coarse:
+    "ej" (element-Jacobi smoothing everywhere) or "mbnk" (the matrix-based Newton-Krylov
+    smoother on the coarsest level: GMRES of at most mbnk_maxit iterations to mbnk_tol)."""
     o = N.PmgOpts()
     o.nlevels = len(nsmooth)
     for i, n in enumerate(nsmooth):
         o.nsmooth[i] = int(n)
     o.c, o.inv_dtau_star = float(c), float(inv_dtau_star)
     o.precision = _prec(precision)
+    o.coarse_smoother, o.mbnk_maxit, o.mbnk_tol = _coarse(coarse), int(mbnk_maxit), float(mbnk_tol)
     N.check(N.load().pmg_setup(ctx.handle, _dev(q_ref), C.byref(o), _stream(stream)), "pmg_setup")
 
 
@@ -169,10 +204,11 @@ def _prec(p):
 
 def solve_opts(kdim=30, maxit_gmres=300, max_ptc=100, nsmooth=(2, 2), use_pmg=True, tol_gmres=1e-1,
                tol_newton=1e-8, eps=1e-6, dtau=1.0, inv_dtau_star=0.0, precision="fp64", guess="qn",
-               train_iters=0, train_batch=4096, lr=1e-3):
+               train_iters=0, train_batch=4096, lr=1e-3, coarse="ej", mbnk_maxit=5, mbnk_tol=0.1):
     """guess: "qn" (the paper's q^n), "extrap" (best of q^n and the quadratic extrapolation
     in time) or "mlp" (also the network-corrected extrapolation); train_iters > 0 trains
-    the attached network after every ESDIRK step."""
+    the attached network after every ESDIRK step.  coarse, mbnk_maxit, mbnk_tol: the
+    coarsest level's smoother, as in pmg_setup."""
     o = N.SolveOpts()
     o.kdim, o.maxit_gmres, o.max_ptc, o.nlevels = int(kdim), int(maxit_gmres), int(max_ptc), len(nsmooth)
     for i, n in enumerate(nsmooth):
@@ -184,6 +220,7 @@ def solve_opts(kdim=30, maxit_gmres=300, max_ptc=100, nsmooth=(2, 2), use_pmg=Tr
     if guess not in guesses:
         raise ValueError(f"guess must be one of {sorted(guesses)}")
     o.guess, o.train_iters, o.train_batch, o.lr = guesses[guess], int(train_iters), int(train_batch), float(lr)
+    o.coarse_smoother, o.mbnk_maxit, o.mbnk_tol = _coarse(coarse), int(mbnk_maxit), float(mbnk_tol)
     return o
 
 

@@ -8,6 +8,7 @@ Translation units:
   csrc/noalloc.cu     fr_residual_noalloc (stage scratch in a fixed device array)
   csrc/mlp.cu         per-element BF16 MLP for the Newton initial guess
   csrc/batch_kernels.cu  segmented (per-problem) vector kernels of the batched solver
+  csrc/mbnk.cu        matrix-based Newton-Krylov smoother of the coarsest pMG level
   csrc/host_tables.c  binary128 operator tables         (gcc -ffp-contract=off)
   csrc/host_geometry.c geometric factors, connectivity  (gcc -ffp-contract=off)
 """
@@ -45,6 +46,7 @@ def _units():
         ([nv] + common + ["-c"], "noalloc.cu"),
         ([nv] + common + ["-c"], "mlp.cu"),
         ([nv] + common + ["-fmad=false", "-c"], "batch_kernels.cu"),
+        ([nv] + common + ["-fmad=false", "-c"], "mbnk.cu"),
         (["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC"] + inc + ["-c"], "host_tables.c"),
         (["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC"] + inc + ["-c"], "host_geometry.c"),
     ]

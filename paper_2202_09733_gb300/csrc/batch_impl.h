@@ -480,6 +480,7 @@ static int esdirk_group(fr_batch *B, BGroup &g, const fr_esdirk_tableau *tab, do
         po.c = c;
         po.inv_dtau_star = o->inv_dtau_star;
         po.precision = o->precision;
+        coarse_opts_copy(o, &po);
         TRY(pmg_setup_(C, qn, &po, s));
         if (o->precision == 1) {
             // device-held scale of the FP32 cycle: its first target from the setup's gain
@@ -544,6 +545,9 @@ extern "C" int fr_batch_esdirk_step(fr_batch *B, const fr_esdirk_tableau *tab, d
     if (tab->stages < 2 || tab->stages > 6 || !(dt > 0.0)) return fail(FR_ERR_INVALID_ARG, "bad tableau or dt");
     if (o->guess != 0 || o->train_iters != 0)
         return fail(FR_ERR_UNIMPLEMENTED, "the batched step starts every stage from q^n (guess 0, no training)");
+    if (o->use_pmg && o->coarse_smoother != 0)
+        return fail(FR_ERR_UNIMPLEMENTED, "the matrix-based coarse smoother's inner products would couple the problems "
+                                          "of a group; batched steps smooth with element-Jacobi blocks");
     if (o->kdim > kBatchLD - 2) return fail(FR_ERR_INVALID_ARG, "batched FGMRES needs kdim <= %d", kBatchLD - 2);
     for (int k = 0; k < B->nprob; ++k)
         if (!q[k]) return fail(FR_ERR_INVALID_ARG, "state of problem %d is NULL", k);

@@ -122,6 +122,36 @@ void frkad_seed(const FrLevelAD &L, const int *color, int col, int j0, DualT *qd
 void frkad_block_column(const FrLevelAD &L, const int *color, int col, int j0, const DualT *Rd, double shift,
                         float *M, cudaStream_t s);
 
+void frkad_nbr_column(const FrLevelAD &L, int nf, const int *nbr, const int *color2, int col, int j0,
+                      const DualT *Rd, float *O, cudaStream_t s);
+
+// matrix-based Newton-Krylov smoother of the coarsest level (mbnk.cu).  Device scratch
+// gm (FRMB_GM doubles): Hessenberg H[i m + k] at 0, Gram-Schmidt coefficients at
+// FRMB_H, ||r|| at FRMB_BETA, y at FRMB_Y, iterations used at FRMB_KUSED, relative
+// residual estimate at FRMB_REL; partial sums: FRMB_MAXBLK x (FRMB_MAXIT + 1) doubles.
+#define FRMB_MAXIT 16
+#define FRMB_MAXBLK 608
+#define FRMB_H ((FRMB_MAXIT + 1) * FRMB_MAXIT)
+#define FRMB_BETA (FRMB_H + FRMB_MAXIT + 1)
+#define FRMB_Y (FRMB_BETA + 1)
+#define FRMB_KUSED (FRMB_Y + FRMB_MAXIT)
+#define FRMB_REL (FRMB_KUSED + 1)
+#define FRMB_GM (FRMB_REL + 1)
+unsigned long long frmb_launch_count();
+void frmb_nbr_column(int E, int nd, int nf, const int *nbr, const int *color2, int col, int j, const double *q,
+                     const double *R0, const double *Rp, double epsrel, double *O, cudaStream_t s);
+void frmb_bsr_mv(int E, int nd, int nf, const int *nbr, const double *Md, const double *O, const double *x, double *y,
+                 cudaStream_t s);
+void frmb_bsr_mv(int E, int nd, int nf, const int *nbr, const float *Md, const float *O, const float *x, float *y,
+                 cudaStream_t s);
+void frmb_start(long long N, const double *r, double *V, double *partial, double *gm, cudaStream_t s);
+void frmb_start(long long N, const float *r, float *V, double *partial, double *gm, cudaStream_t s);
+void frmb_arnoldi(long long N, int m, int k, double *V, double *w, double *partial, double *gm, cudaStream_t s);
+void frmb_arnoldi(long long N, int m, int k, float *V, float *w, double *partial, double *gm, cudaStream_t s);
+void frmb_small_solve(int m, double tol, double *gm, cudaStream_t s);
+void frmb_combine(long long N, int m, const double *V, const double *gm, double *u, cudaStream_t s);
+void frmb_combine(long long N, int m, const float *V, const double *gm, float *u, cudaStream_t s);
+
 // learned initial guess (mlp.cu)
 struct fr_mlp;
 unsigned long long frkmlp_launch_count();

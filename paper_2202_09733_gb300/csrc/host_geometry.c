@@ -176,3 +176,49 @@ int frh_color(int E, int nfaces, const int *faces, int *color) {
     free(deg); free(off); free(adj);
     return ncol;
 }
+
+int frh_neighbours(int E, int nf, int nfaces, const int *faces, int *nbr) {
+    for (long long i = 0; i < (long long)E * nf; ++i) nbr[i] = -1;
+    for (int F = 0; F < nfaces; ++F) {
+        int a = faces[6 * F], fa = faces[6 * F + 1], b = faces[6 * F + 2], fb = faces[6 * F + 3];
+        if (b < 0 || a == b) continue;
+        if (fa < 0 || fa >= nf || fb < 0 || fb >= nf) return -1;
+        nbr[(long long)fa * E + a] = b;
+        nbr[(long long)fb * E + b] = a;
+    }
+    for (int e = 0; e < E; ++e)
+        for (int f = 1; f < nf; ++f) {
+            int n = nbr[(long long)f * E + e];
+            if (n < 0) continue;
+            for (int g = 0; g < f; ++g)
+                if (nbr[(long long)g * E + e] == n) { nbr[(long long)f * E + e] = -1; break; }
+        }
+    return 0;
+}
+
+int frh_color2(int E, int nf, const int *nbr, int *color) {
+    enum { MAXC = 1024 };
+    int *stamp = malloc(sizeof(int) * MAXC);
+    for (int c = 0; c < MAXC; ++c) stamp[c] = -1;
+    for (int e = 0; e < E; ++e) color[e] = -1;
+    int ncol = 0;
+    for (int e = 0; e < E; ++e) {
+        /* mark the colours of every element within two face steps */
+        for (int f = 0; f < nf; ++f) {
+            int n = nbr[(long long)f * E + e];
+            if (n < 0) continue;
+            if (color[n] >= 0) stamp[color[n]] = e;
+            for (int g = 0; g < nf; ++g) {
+                int m = nbr[(long long)g * E + n];
+                if (m >= 0 && m != e && color[m] >= 0) stamp[color[m]] = e;
+            }
+        }
+        int c = 0;
+        while (c < MAXC && stamp[c] == e) ++c;
+        if (c == MAXC) { free(stamp); return -1; }
+        color[e] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(stamp);
+    return ncol;
+}

@@ -33,6 +33,13 @@ int frh_pairs(int d, int n, int E, int nfaces, const int *faces, int *pairs, int
 
 /* greedy distance-1 colouring of the element face graph; color[E]; returns #colours */
 int frh_color(int E, int nfaces, const int *faces, int *color);
+/* face-neighbour table nbr[f * E + e] (nf = 2d face slots): the element across face f of
+ * e, or -1 for a boundary face, a face wrapping onto e itself and any face after the first
+ * one reaching the same neighbour.  Returns 0, or -1 on a face naming a slot >= nf. */
+int frh_neighbours(int E, int nf, int nfaces, const int *faces, int *nbr);
+/* greedy distance-2 colouring from the neighbour table (no two elements within two face
+ * steps share a colour); returns the number of colours, or -1 past 1024 colours */
+int frh_color2(int E, int nf, const int *nbr, int *color);
 
 #ifdef __cplusplus
 }

@@ -124,3 +124,26 @@ void frkad_block_column(const FrLevelAD &L, const int *color, int col, int j0, c
                         float *M, cudaStream_t s) {
     CNT(); k_ad_column<<<(L.E + 31) / 32, 256, 0, s>>>(L.E, L.nd, color, col, j0, Rd, (float)shift, M);
 }
+
+// O_(e,f)[j][r] (column-major blocks) = -dR_e[r]/dq_n[j] for the face neighbour
+// n = nbr[f E + e] of colour col, j = j0 + t, t < FR_AD_K (distance-2 colours: at most one
+// seeded element among e and its neighbours); one thread per (element, row)
+__global__ void k_ad_nbr_column(int E, int nd, int nf, const int *nbr, const int *color2, int col, int j0,
+                                const DualT *Rd, float *O) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)E * nd) return;
+    int e = (int)(t / nd), r = (int)(t - (long long)e * nd);
+    for (int f = 0; f < nf; ++f) {
+        int n = nbr[(size_t)f * E + e];
+        if (n < 0 || color2[n] != col) continue;
+        DualT R = Rd[(size_t)r * E + e];
+#pragma unroll
+        for (int k = 0; k < FR_AD_K; ++k)
+            if (j0 + k < nd) O[(((size_t)e * nf + f) * nd + j0 + k) * nd + r] = -R.d[k];
+    }
+}
+void frkad_nbr_column(const FrLevelAD &L, int nf, const int *nbr, const int *color2, int col, int j0,
+                      const DualT *Rd, float *O, cudaStream_t s) {
+    long long n = (long long)L.E * L.nd;
+    CNT(); k_ad_nbr_column<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L.E, L.nd, nf, nbr, color2, col, j0, Rd, O);
+}

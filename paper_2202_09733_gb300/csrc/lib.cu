@@ -48,6 +48,21 @@ static int fail(int code, const char *fmt, ...) {
         if (_r != FR_OK) return _r;  \
     } while (0)
 
+// options of the coarsest level's smoother (fr_pmg_opts / fr_solve_opts)
+static int check_coarse_opts(int coarse, int maxit, double tol) {
+    if (coarse != 0 && coarse != 1)
+        return fail(FR_ERR_INVALID_ARG, "coarse_smoother must be 0 (element-Jacobi) or 1 (matrix-based)");
+    if (coarse == 1 && (maxit < 1 || maxit > FRMB_MAXIT))
+        return fail(FR_ERR_INVALID_ARG, "mbnk_maxit outside 1..%d", FRMB_MAXIT);
+    if (coarse == 1 && !(tol >= 0.0)) return fail(FR_ERR_INVALID_ARG, "mbnk_tol must be >= 0");
+    return FR_OK;
+}
+static void coarse_opts_copy(const fr_solve_opts *o, fr_pmg_opts *po) {
+    po->coarse_smoother = o->coarse_smoother;
+    po->mbnk_maxit = o->mbnk_maxit;
+    po->mbnk_tol = o->mbnk_tol;
+}
+
 template <typename T>
 struct PmgBuf {
     T *M[FRL_MAXLEV];
@@ -56,6 +71,10 @@ struct PmgBuf {
     T *b[FRL_MAXLEV], *Rb[FRL_MAXLEV], *d[FRL_MAXLEV], *qh[FRL_MAXLEV], *Rqh[FRL_MAXLEV], *rhs[FRL_MAXLEV],
         *C[FRL_MAXLEV];
     T *blk_R0, *blk_Rp, *blk_qp;  // element-block assembly temporaries (finest-level size)
+    // matrix-based smoother of the coarsest level: unfactored diagonal blocks, neighbour
+    // blocks, Krylov basis (FRMB_MAXIT + 1 vectors), two work vectors; capacities in T
+    T *Md, *O, *V, *mz, *mw;
+    size_t Md_cap, O_cap, V_cap, w_cap;
 };
 
 struct fr_ctx {
@@ -69,6 +88,12 @@ struct fr_ctx {
     DualT *qd, *Rd;
     int ncolor;
     int *color;
+    int ncolor2;
+    int *color2;                  // distance-2 colouring (assembly of the neighbour blocks)
+    int *nbr;                     // face neighbours nbr[f E + e], -1 none
+    int mbnk, mbnk_maxit;         // matrix-based smoother on the coarsest level (last pmg_setup)
+    double mbnk_tol;
+    double *mb_partial, *mb_gm;
     int *info;
     std::vector<void *> allocs;
     double *jv_qp, *jv_Rp;
@@ -132,7 +157,7 @@ static std::atomic<unsigned long long> g_capture_kernels{0};  // launch-counter 
 
 extern "C" unsigned long long fr_kernel_launches(void) {
     return frk64_launch_count() + frk32_launch_count() + frkad_launch_count() + frkmlp_launch_count() +
-           frkb_launch_count() - g_capture_kernels + g_graph_kernels;
+           frkb_launch_count() + frmb_launch_count() - g_capture_kernels + g_graph_kernels;
 }
 
 // ---------------------------------------------------------------- context set-up
@@ -250,6 +275,19 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
         rc = dalloc_t(C, &C->color, C->E);
         if (rc == FR_OK && cudaMemcpy(C->color, col.data(), sizeof(int) * C->E, cudaMemcpyHostToDevice) != cudaSuccess)
             rc = fail(FR_ERR_CUDA, "copying colours");
+    }
+    if (rc == FR_OK) {
+        int nf = 2 * C->d;
+        std::vector<int> nb((size_t)C->E * nf), c2(C->E);
+        if (frh_neighbours(C->E, nf, m->nfaces, m->faces, nb.data()) != 0)
+            rc = fail(FR_ERR_INVALID_ARG, "a face names a local face index outside 0..%d", nf - 1);
+        else if ((C->ncolor2 = frh_color2(C->E, nf, nb.data(), c2.data())) < 0)
+            rc = fail(FR_ERR_INVALID_ARG, "the distance-2 colouring needs more than 1024 colours");
+        if (rc == FR_OK) rc = dalloc_t(C, &C->nbr, nb.size());
+        if (rc == FR_OK) rc = dalloc_t(C, &C->color2, c2.size());
+        if (rc == FR_OK && (cudaMemcpy(C->nbr, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                            cudaMemcpy(C->color2, c2.data(), sizeof(int) * c2.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+            rc = fail(FR_ERR_CUDA, "copying the neighbour table");
     }
     long long n0 = C->L[0].ndof;
     if (rc == FR_OK) rc = dalloc_t(C, &C->info, 1);
@@ -496,6 +534,63 @@ int elem_blocks_t<double>(fr_ctx *C, int l, const double *q, double shift, doubl
     return FR_OK;
 }
 
+// diagonal and neighbour blocks of level l in one pass over the distance-2 colours (for
+// the matrix-based smoother): the diagonal columns equal those of elem_blocks_t, since
+// each element's residual sees the same single perturbation either way
+template <typename T>
+static int elem_blocks_mbnk_t(fr_ctx *C, int l, const T *q, double shift, T *M, T *O, cudaStream_t s);
+template <>
+int elem_blocks_mbnk_t<float>(fr_ctx *C, int l, const float *q, double shift, float *M, float *O, cudaStream_t s) {
+    TRY(ensure_levelsAD(C));
+    FrLevelAD &A = C->LA[l];
+    int nf = 2 * C->d;
+    CK(cudaMemsetAsync(O, 0, sizeof(float) * (size_t)A.E * nf * A.nd * A.nd, s));
+    frkad_init(A.ndof, q, C->qd, s);
+    for (int col = 0; col < C->ncolor2; ++col)
+        for (int j0 = 0; j0 < A.nd; j0 += FR_AD_K) {
+            frkad_seed(A, C->color2, col, j0, C->qd, 1.f, s);
+            if (frkad_residual(A, C->ph, C->qd, C->Rd, s) != 0)
+                return fail(FR_ERR_UNIMPLEMENTED, "no kernel for d=%d p=%d", C->d, A.p);
+            frkad_block_column(A, C->color2, col, j0, C->Rd, shift, M, s);
+            frkad_nbr_column(A, nf, C->nbr, C->color2, col, j0, C->Rd, O, s);
+            frkad_seed(A, C->color2, col, j0, C->qd, 0.f, s);
+        }
+    CKLAUNCH();
+    return FR_OK;
+}
+template <>
+int elem_blocks_mbnk_t<double>(fr_ctx *C, int l, const double *q, double shift, double *M, double *O, cudaStream_t s) {
+    typedef double T;
+    TRY(ensure_blk_tmp<T>(C));
+    PmgBuf<T> &P = pbuf<T>(C);
+    FrLevelT<T> &L = levels<T>(C)[l];
+    int nf = 2 * C->d;
+    CK(cudaMemsetAsync(O, 0, sizeof(T) * (size_t)L.E * nf * L.nd * L.nd, s));
+    TRY(residual_t<T>(C, l, q, P.blk_R0, s));
+    Kn<T>::copy(L.ndof, q, P.blk_qp, s);
+    for (int col = 0; col < C->ncolor2; ++col)
+        for (int j = 0; j < L.nd; ++j) {
+            Kn<T>::perturb(L, C->color2, col, j, q, P.blk_qp, Kn<T>::epsrel, s);
+            TRY(residual_t<T>(C, l, P.blk_qp, P.blk_Rp, s));
+            Kn<T>::column(L, C->color2, col, j, q, P.blk_R0, P.blk_Rp, shift, Kn<T>::epsrel, M, s);
+            frmb_nbr_column(L.E, L.nd, nf, C->nbr, C->color2, col, j, q, P.blk_R0, P.blk_Rp, Kn<T>::epsrel, O, s);
+            Kn<T>::restore(L, C->color2, col, j, q, P.blk_qp, s);
+        }
+    CKLAUNCH();
+    return FR_OK;
+}
+
+extern "C" int fr_nbr_blocks(fr_ctx *C, int l, const double *q, double shift, double *M, double *O, void *stream) {
+    if (!C || l < 0 || l >= C->nlev || !q || !M || !O) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    return elem_blocks_mbnk_t<double>(C, l, q, shift, M, O, S_(stream));
+}
+
+extern "C" int fr_neighbour_table(const fr_ctx *C, int *nbr) {
+    if (!C || !nbr) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    CK(cudaMemcpy(nbr, C->nbr, sizeof(int) * (size_t)C->E * 2 * C->d, cudaMemcpyDeviceToHost));
+    return FR_OK;
+}
+
 extern "C" int fr_elem_blocks(fr_ctx *C, int l, const double *q, double shift, double *M, void *stream) {
     if (!C || l < 0 || l >= C->nlev || !q || !M) return fail(FR_ERR_INVALID_ARG, "bad argument");
     return elem_blocks_t<double>(C, l, q, shift, M, S_(stream));
@@ -568,7 +663,41 @@ static int pmg_alloc_t(fr_ctx *C, int nlev) {
     return FR_OK;
 }
 
-// blocks (1/dtau* + c) I - J_ee at q_ref restricted level by level, and their LU factors
+template <typename T>
+static int ensure_cap(fr_ctx *C, T **p, size_t *cap, size_t need) {
+    if (*p && *cap >= need) return FR_OK;
+    dfree(C, *p);
+    *p = nullptr;
+    *cap = 0;
+    TRY(dalloc_t(C, p, need));
+    *cap = need;
+    return FR_OK;
+}
+
+// buffers of the matrix-based smoother on level l
+template <typename T>
+static int mbnk_alloc_t(fr_ctx *C, int l) {
+    PmgBuf<T> &P = pbuf<T>(C);
+    const FrLevel &L = C->L[l];
+    size_t blk = (size_t)L.nd * L.nd, N = (size_t)L.ndof;
+    TRY(ensure_cap(C, &P.Md, &P.Md_cap, (size_t)L.E * blk));
+    TRY(ensure_cap(C, &P.O, &P.O_cap, (size_t)L.E * 2 * C->d * blk));
+    TRY(ensure_cap(C, &P.V, &P.V_cap, (size_t)(FRMB_MAXIT + 1) * N));
+    size_t wc = P.w_cap;
+    TRY(ensure_cap(C, &P.mz, &wc, N));
+    wc = P.w_cap;
+    TRY(ensure_cap(C, &P.mw, &P.w_cap, N));
+    if (!C->mb_gm) {
+        TRY(dalloc_t(C, &C->mb_gm, FRMB_GM));
+        TRY(dalloc_t(C, &C->mb_partial, (size_t)FRMB_MAXBLK * (FRMB_MAXIT + 1)));
+        CK(cudaMemset(C->mb_gm, 0, sizeof(double) * FRMB_GM));
+    }
+    return FR_OK;
+}
+
+// blocks (1/dtau* + c) I - J_ee at q_ref restricted level by level, and their LU factors;
+// with the matrix-based smoother the coarsest level also keeps its diagonal blocks
+// unfactored and its neighbour blocks
 template <typename T>
 static int pmg_factor_levels(fr_ctx *C, const T *q_ref, const fr_pmg_opts *o, cudaStream_t s) {
     PmgBuf<T> &P = pbuf<T>(C);
@@ -579,7 +708,14 @@ static int pmg_factor_levels(fr_ctx *C, const T *q_ref, const fr_pmg_opts *o, cu
             TRY(transfer_t<T>(C, l - 1, true, qr, P.b[l], s));   // P.b[l] is free until the first cycle
             qr = P.b[l];
         }
-        TRY(elem_blocks_t<T>(C, l, qr, shift, P.M[l], s));
+        if (C->mbnk && l == o->nlevels - 1) {
+            const FrLevel &L = C->L[l];
+            TRY(mbnk_alloc_t<T>(C, l));
+            TRY(elem_blocks_mbnk_t<T>(C, l, qr, shift, P.M[l], P.O, s));
+            CK(cudaMemcpyAsync(P.Md, P.M[l], sizeof(T) * (size_t)L.E * L.nd * L.nd, cudaMemcpyDeviceToDevice, s));
+        } else {
+            TRY(elem_blocks_t<T>(C, l, qr, shift, P.M[l], s));
+        }
         TRY(block_factor_t<T>(C, l, P.M[l], P.perm[l], s));
     }
     return FR_OK;
@@ -592,6 +728,9 @@ static int pmg_setup_(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, cuda
     C->pmg_c = o->c;
     C->pmg_ids = o->inv_dtau_star;
     C->pmg_prec = o->precision;
+    C->mbnk = o->coarse_smoother == 1;
+    C->mbnk_maxit = o->mbnk_maxit;
+    C->mbnk_tol = o->mbnk_tol;
     C->pmg_gain = o->c + o->inv_dtau_star > 0.0 ? 1.0 / (o->c + o->inv_dtau_star) : 1.0;
     if (o->precision == 0) {
         TRY(pmg_alloc_t<double>(C, o->nlevels));
@@ -632,10 +771,44 @@ extern "C" int pmg_setup(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, v
     if (o->precision != 0 && o->precision != 1) return fail(FR_ERR_INVALID_ARG, "precision must be 0 (FP64) or 1 (FP32)");
     for (int l = 0; l < o->nlevels; ++l)
         if (o->nsmooth[l] < 0) return fail(FR_ERR_INVALID_ARG, "negative smoothing count");
+    TRY(check_coarse_opts(o->coarse_smoother, o->mbnk_maxit, o->mbnk_tol));
     return pmg_setup_(C, q_ref, o, S_(stream));
 }
 
-// smoothing steps on level l: qh <- qh + M^{-1} (d - (c (qh - b) - (R(qh) - Rb)))
+// one matrix-based smoothing solve on level l, in place (x: r in, delta out): GMRES on
+// A delta = r from 0, right-preconditioned by the factored diagonal blocks, at most
+// mbnk_maxit iterations to the relative tolerance mbnk_tol (the stopping iteration is
+// taken on the device; later iterations run and are ignored), delta = Md^{-1} V y
+template <typename T>
+static int mbnk_solve_t(fr_ctx *C, int l, T *x, cudaStream_t s) {
+    PmgBuf<T> &P = pbuf<T>(C);
+    FrLevelT<T> &L = levels<T>(C)[l];
+    long long N = L.ndof;
+    int m = C->mbnk_maxit, nf = 2 * C->d;
+    frmb_start(N, x, P.V, C->mb_partial, C->mb_gm, s);
+    for (int k = 0; k < m; ++k) {
+        Kn<T>::copy(N, P.V + (size_t)k * N, P.mz, s);
+        TRY(Kn<T>::solve(L, P.M[l], P.perm[l], P.mz, s));
+        frmb_bsr_mv(L.E, L.nd, nf, C->nbr, P.Md, P.O, P.mz, P.mw, s);
+        frmb_arnoldi(N, m, k, P.V, P.mw, C->mb_partial, C->mb_gm, s);
+    }
+    frmb_small_solve(m, C->mbnk_tol, C->mb_gm, s);
+    frmb_combine(N, m, P.V, C->mb_gm, x, s);
+    TRY(Kn<T>::solve(L, P.M[l], P.perm[l], x, s));
+    return FR_OK;
+}
+
+extern "C" int fr_mbnk_last(const fr_ctx *C, int *iters, double *relres) {
+    if (!C || !C->mb_gm) return fail(FR_ERR_NOT_READY, "no matrix-based smoother has run");
+    double g[2];
+    CK(cudaMemcpy(g, C->mb_gm + FRMB_KUSED, sizeof(double) * 2, cudaMemcpyDeviceToHost));
+    if (iters) *iters = (int)g[0];
+    if (relres) *relres = g[1];
+    return FR_OK;
+}
+
+// smoothing steps on level l: qh <- qh + M^{-1} (d - (c (qh - b) - (R(qh) - Rb))); on the
+// coarsest level with the matrix-based smoother, M^{-1} is the GMRES solve with A
 template <typename T>
 static int smooth_t(fr_ctx *C, int l, int nsteps, const T *b, const T *Rb, const T *d, T *qh, bool first_is_base,
                     cudaStream_t s) {
@@ -647,7 +820,8 @@ static int smooth_t(fr_ctx *C, int l, int nsteps, const T *b, const T *Rb, const
             TRY(residual_t<T>(C, l, qh, P.Rqh[l], s));
             Kn<T>::pmg_rhs(L.ndof, C->pmg_c, d, qh, b, P.Rqh[l], Rb, P.rhs[l], s);
         }
-        Kn<T>::solve(L, P.M[l], P.perm[l], P.rhs[l], s);
+        if (C->mbnk && l == C->pmg_nlev - 1) TRY(mbnk_solve_t<T>(C, l, P.rhs[l], s));
+        else Kn<T>::solve(L, P.M[l], P.perm[l], P.rhs[l], s);
         Kn<T>::add(L.ndof, qh, P.rhs[l], qh, s);
     }
     CKLAUNCH();
@@ -908,6 +1082,7 @@ static int check_solve_opts(const fr_ctx *C, const fr_solve_opts *o) {
     if (o->use_pmg && (o->nlevels < 1 || o->nlevels > C->nlev))
         return fail(FR_ERR_INVALID_ARG, "nlevels outside 1..%d", C->nlev);
     if (o->precision != 0 && o->precision != 1) return fail(FR_ERR_INVALID_ARG, "precision must be 0 or 1");
+    if (o->use_pmg) TRY(check_coarse_opts(o->coarse_smoother, o->mbnk_maxit, o->mbnk_tol));
     return FR_OK;
 }
 
@@ -1074,6 +1249,7 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
         po.c = c;
         po.inv_dtau_star = o->inv_dtau_star;
         po.precision = o->precision;
+        coarse_opts_copy(o, &po);
         TRY(pmg_setup_(C, qn, &po, s));
     }
     fr_gmres_opts go = gm_opts(o, c);
@@ -1189,6 +1365,7 @@ extern "C" int row_step(fr_ctx *C, const fr_row_tableau *tab, double dt, double 
         po.c = c;
         po.inv_dtau_star = o->inv_dtau_star;
         po.precision = o->precision;
+        coarse_opts_copy(o, &po);
         TRY(pmg_setup_(C, qn, &po, s));
     }
     fr_gmres_opts go = gm_opts(o, c);
@@ -1242,6 +1419,7 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
             po.c = c;
             po.inv_dtau_star = o->inv_dtau_star < 0 ? c : o->inv_dtau_star;
             po.precision = prec;
+            coarse_opts_copy(o, &po);
             TRY(pmg_setup_(C, q, &po, s));
         }
         fr_gmres_opts go = gm_opts(o, c);
@@ -1399,6 +1577,7 @@ extern "C" int pmg_solve_steady(fr_ctx *C, double *q, double dtau_init, double d
         po.c = c;
         po.inv_dtau_star = o->inv_dtau_star < 0 ? c : o->inv_dtau_star;
         po.precision = 0;
+        coarse_opts_copy(o, &po);
         TRY(pmg_setup_(C, q, &po, s));
         TRY(pmg_apply(C, q, R, R, Y, s));
         frk64_add(n, q, Y, q, s);

@@ -1,0 +1,178 @@
+"""GPU matrix-based Newton-Krylov (MBNK) smoother of the coarsest level (Sec. 3.2) vs the
+oracle.  Bars:
+  neighbour table            equal to the oracle's;
+  element + neighbour blocks bit for bit (the same forward differences; the GPU perturbs a
+                             distance-2 colour class at once, which leaves every element's
+                             residual with the same single perturbation);
+  FP64 cycle with MBNK       1e-10 relative, and the same GMRES iteration count in the last
+                             smoothing solve: the GPU orthogonalises by classical
+                             Gram-Schmidt with one re-orthogonalisation, the oracle by
+                             modified Gram-Schmidt, equal in exact arithmetic; the
+                             difference is rounding through at most 5 iterations of a
+                             well-conditioned (block-Jacobi preconditioned) system;
+  mixed cycle with MBNK      5e-3 at the library's input scaling (as the element-Jacobi
+                             mixed cycle; the FP32 blocks are exact derivatives);
+  ESDIRK3 step               converged states within 1e-10 of the oracle's MBNK step, FP64
+                             and mixed preconditioner;
+  batched step               coarse_smoother 1 is refused (FR_ERR_UNIMPLEMENTED).
+Meshes: curved O-mesh with wall and far-field faces (E = 72), a periodic box two elements
+wide in x (a neighbour reached through two faces), hexes."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import tableaux as OT
+from paper_2202_09733_gb300 import api, workloads as w
+from paper_2202_09733_gb300 import build as B
+from paper_2202_09733_gb300 import tableaux as GT
+from paper_2202_09733_gb300 import _native as N
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    B.build()
+
+
+def relerr(a, b):
+    a = a.detach().cpu().numpy() if torch.is_tensor(a) else a
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def wavy(mesh, p, seed=0):
+    X = w.solution_point_coords(mesh, p)
+    rng = np.random.default_rng(seed)
+    k = rng.uniform(0.3, 1.2, size=(4, mesh["d"]))
+    s = [np.sin(sum(k[i, c] * X[c] for c in range(mesh["d"])) + i) for i in range(4)]
+    vel = [math.cos(0.4) + 0.1 * s[1], math.sin(0.4) + 0.1 * s[2]] + ([0.05 * s[3]] if mesh["d"] == 3 else [])
+    return np.ascontiguousarray(w.prim_to_cons(1.0 + 0.05 * s[0], vel, (1.0 / (1.4 * 0.09)) * (1 + 0.05 * s[3])))
+
+
+CASES = {
+    "omesh_p3": (lambda: w.omesh(6, 12, 0.5, 5.0, 0.02, jitter=0.05, seed=3), [3, 2], 0.02),
+    "box2d_two_wide": (lambda: w.box2d(2, 3, 4.0, 6.0, qg=2, warp=0.1), [2, 1], 0.02),
+    "box3d_p2": (lambda: w.box3d(3, 2.0), [2, 1], 0.01),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    mk, levels, mu = CASES[request.param]
+    mesh = mk()
+    ph = w.Physics(mu=mu, qinf=w.freestream(mesh["d"], 0.3))
+    return dict(name=request.param, mesh=mesh, levels=levels, O=oracle.Oracle(mesh, ph, levels),
+                G=api.fr_create(mesh, ph, levels), q=wavy(mesh, levels[0]))
+
+
+def test_neighbour_table(case):
+    assert np.array_equal(api.fr_neighbour_table(case["G"]), case["O"].neighbours())
+
+
+def test_blocks_bitwise(case):
+    O, G, q = case["O"], case["G"], case["q"]
+    l = len(case["levels"]) - 1
+    qc = O.restrict(q, 0)
+    shift = 4.2
+    M, Ob = api.fr_nbr_blocks(G, l, dev(qc), shift)
+    M_or = O.elem_blocks(qc, shift, np.arange(case["mesh"]["E"]), l)
+    Ob_or = O.nbr_blocks(qc, l)
+    assert np.array_equal(M.transpose(1, 2).cpu().numpy(), M_or)
+    assert np.array_equal(Ob.transpose(2, 3).cpu().numpy(), Ob_or)
+
+
+def _setup_both(case, precision, nsm=(2, 3), maxit=5, tol=0.1):
+    O, G, q = case["O"], case["G"], case["q"]
+    dt = 0.3
+    c = 1.0 / dt + 1.0 / (0.4358665215084590 * dt)
+    O.pmg_setup(q, list(nsm), c, 1.0 / dt, coarse="mbnk", mbnk_maxit=maxit, mbnk_tol=tol)
+    api.pmg_setup(G, dev(q), list(nsm), c, 1.0 / dt, precision=precision, coarse="mbnk", mbnk_maxit=maxit,
+                  mbnk_tol=tol)
+    return c, dt
+
+
+@pytest.mark.parametrize("maxit,tol", [(5, 0.1), (12, 1e-6)])
+def test_pmg_fp64_with_mbnk(case, maxit, tol):
+    O, G, q = case["O"], case["G"], case["q"]
+    _setup_both(case, "fp64", maxit=maxit, tol=tol)
+    Rq = O.residual(q)
+    X = np.random.default_rng(10).standard_normal(q.shape)
+    X /= np.linalg.norm(X)
+    Y_or = O.pmg_apply(q, Rq, X)
+    it_or = oracle.lib().or_mbnk_last_iters()
+    Y = api.pmg_precondition(G, dev(q), dev(Rq), dev(X))
+    assert relerr(Y, Y_or) <= 1e-10
+    it, rel = api.fr_mbnk_last(G)
+    assert it == it_or and 1 <= it <= maxit
+    assert rel <= tol or it == maxit
+
+
+def test_pmg_mixed_with_mbnk(case):
+    O, G, q = case["O"], case["G"], case["q"]
+    c, dt = _setup_both(case, "mixed")
+    Rq = O.residual(q)
+    X = np.random.default_rng(12).standard_normal(q.shape)
+    X /= np.linalg.norm(X)
+    qref = np.abs(q).max(axis=(1, 2))
+    qref = np.maximum(qref, 1e-3 * qref.max())
+    want, gain = 1e-2, 1.0 / ((c + 1.0 / dt) * qref.min())
+    for _ in range(2):
+        target = want / gain
+        s = target / np.abs(X).max()
+        Ys = O.pmg_apply(q, Rq, s * X)
+        ym = (np.abs(Ys).max(axis=(1, 2)) / qref).max()
+        gain = ym / target
+        if want / 30 <= ym <= want * 30:
+            break
+    Y = api.pmg_precondition(G, dev(q), dev(Rq), dev(X))
+    assert relerr(Y, Ys / s) <= 5e-3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_esdirk_step_with_mbnk(precision):
+    mesh = w.box2d(4, 4, 10, 10, qg=2, warp=0.1)
+    ph = w.Physics(mu=0.01, qinf=w.freestream(2, 0.5))
+    X = w.solution_point_coords(mesh, 2)
+    q0 = np.ascontiguousarray(w.isentropic_vortex(X, 5, 5, 5.0, 0.5, 10, 10))
+    dt = 10.0 * w.explicit_dt(mesh, 2, q0)
+    O = oracle.Oracle(mesh, ph, [2, 1])
+    G = api.fr_create(mesh, ph, [2, 1])
+    A, b, _ = OT.esdirk3()
+    oo = O.opts(kdim=30, maxit_gmres=300, max_ptc=40, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-12, dtau=dt,
+                inv_dtau_star=1.0 / dt, coarse="mbnk")
+    q_or, st_or = O.esdirk_step(A, b, dt, q0, oo)
+    Ag, bg = GT.esdirk3()
+    go = api.solve_opts(kdim=30, maxit_gmres=300, max_ptc=40, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-12,
+                        dtau=dt, inv_dtau_star=1.0 / dt, precision=precision, coarse="mbnk")
+    qg = dev(q0)
+    st = api.esdirk_step(G, Ag, bg, dt, qg, go)
+    assert st_or["converged"] and st["converged"]
+    assert relerr(qg, q_or) <= 1e-10
+    assert api.fr_kernel_timeouts() == 0
+
+
+def test_mbnk_options_are_checked(case):
+    G, q = case["G"], case["q"]
+    for bad in (dict(mbnk_maxit=0), dict(mbnk_maxit=17), dict(mbnk_tol=-1.0)):
+        kw = dict(coarse="mbnk", mbnk_maxit=5, mbnk_tol=0.1)
+        kw.update(bad)
+        with pytest.raises(RuntimeError):
+            api.pmg_setup(G, dev(q), [1, 1], 3.0, 1.0, **kw)
+
+
+def test_batch_refuses_mbnk():
+    probs, states, phys, dt = w.vortex_batch(nprob=4, seed=3)
+    Bt = api.Batch(probs, phys)
+    A, b = GT.esdirk3()
+    o = api.solve_opts(kdim=30, maxit_gmres=300, max_ptc=10, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-8,
+                       dtau=dt, inv_dtau_star=1.0 / dt, coarse="mbnk")
+    with pytest.raises(RuntimeError, match="UNIMPLEMENTED|couple"):
+        Bt.esdirk_step(A, b, dt, [dev(q) for q in states], o)
