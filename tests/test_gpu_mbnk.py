@@ -10,8 +10,15 @@ oracle.  Bars:
                              modified Gram-Schmidt, equal in exact arithmetic; the
                              difference is rounding through at most 5 iterations of a
                              well-conditioned (block-Jacobi preconditioned) system;
-  mixed cycle with MBNK      5e-3 at the library's input scaling (as the element-Jacobi
-                             mixed cycle; the FP32 blocks are exact derivatives);
+  mixed cycle with MBNK      with a fixed GMRES count (tol 0) 5e-3 at the library's input
+                             scaling, as the element-Jacobi mixed cycle (the FP32 blocks
+                             are exact derivatives, the smoother a continuous map); with
+                             the 1e-1 stopping rule 2e-2: FP32 and FP64 residual estimates
+                             can straddle the tolerance in a smoothing solve, and one more
+                             or one fewer GMRES iteration there changes the coarse
+                             correction by up to the tolerance fraction (1e-1) of its
+                             right-hand side before prolongation and post-smoothing
+                             (measured 8e-3 on the curved O-mesh);
   ESDIRK3 step               converged states within 1e-10 of the oracle's MBNK step, FP64
                              and mixed preconditioner;
   batched step               coarse_smoother 1 is refused (FR_ERR_UNIMPLEMENTED).
@@ -115,9 +122,10 @@ def test_pmg_fp64_with_mbnk(case, maxit, tol):
     assert rel <= tol or it == maxit
 
 
-def test_pmg_mixed_with_mbnk(case):
+@pytest.mark.parametrize("tol,bar", [(0.0, 5e-3), (0.1, 2e-2)])
+def test_pmg_mixed_with_mbnk(case, tol, bar):
     O, G, q = case["O"], case["G"], case["q"]
-    c, dt = _setup_both(case, "mixed")
+    c, dt = _setup_both(case, "mixed", tol=tol)
     Rq = O.residual(q)
     X = np.random.default_rng(12).standard_normal(q.shape)
     X /= np.linalg.norm(X)
@@ -133,7 +141,7 @@ def test_pmg_mixed_with_mbnk(case):
         if want / 30 <= ym <= want * 30:
             break
     Y = api.pmg_precondition(G, dev(q), dev(Rq), dev(X))
-    assert relerr(Y, Ys / s) <= 5e-3
+    assert relerr(Y, Ys / s) <= bar
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
