@@ -136,6 +136,11 @@ int fr_nbr_blocks(fr_ctx *ctx, int level, const double *q, double shift, double 
  * the element block) and any face after the first reaching the same element (the first
  * slot's block holds the whole coupling). */
 int fr_neighbour_table(const fr_ctx *ctx, int *nbr);
+/* copy of the coarsest level's assembled operator of the last pmg_setup with
+ * coarse_smoother 1: unfactored element blocks Md (E nd^2) and neighbour blocks O
+ * (E 2d nd^2), layouts as fr_nbr_blocks, in the cycle's precision (FP32 values when the
+ * setup was mixed, else FP64).  Md, O: device; FR_ERR_NOT_READY without such a setup. */
+int fr_mbnk_operator(const fr_ctx *ctx, void *Md, void *O, void *stream);
 /* iterations and relative residual estimate of the last matrix-based smoothing solve
  * (synchronises); FR_ERR_NOT_READY before the first one. */
 int fr_mbnk_last(const fr_ctx *ctx, int *iters, double *relres);

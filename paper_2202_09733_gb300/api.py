@@ -124,6 +124,17 @@ def fr_neighbour_table(ctx):
     return nbr.reshape(2 * ctx.d, ctx.E).T.copy()
 
 
+def fr_mbnk_operator(ctx, level, precision="fp64", stream=None):
+    """(Md, O) of the last pmg_setup(coarse="mbnk"): [E, nd(col), nd(row)] and
+    [E, 2d, nd(col), nd(row)] in the cycle's precision; level is the coarsest level used."""
+    nd, nf = ctx.nd(level), 2 * ctx.d
+    dt = torch.float32 if _prec(precision) else torch.float64
+    Md = torch.empty((ctx.E, nd, nd), dtype=dt, device="cuda")
+    O = torch.empty((ctx.E, nf, nd, nd), dtype=dt, device="cuda")
+    N.check(N.load().fr_mbnk_operator(ctx.handle, _dev(Md, dt), _dev(O, dt), _stream(stream)), "fr_mbnk_operator")
+    return Md, O
+
+
 def fr_mbnk_last(ctx):
     """(iterations, relative residual estimate) of the last matrix-based smoothing solve."""
     it, rel = C.c_int(), C.c_double()

@@ -798,6 +798,19 @@ static int mbnk_solve_t(fr_ctx *C, int l, T *x, cudaStream_t s) {
     return FR_OK;
 }
 
+extern "C" int fr_mbnk_operator(const fr_ctx *C, void *Md, void *O, void *stream) {
+    if (!C || !Md || !O) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    if (!C->pmg_ready || !C->mbnk) return fail(FR_ERR_NOT_READY, "no pmg_setup with the matrix-based smoother");
+    const FrLevel &L = C->L[C->pmg_nlev - 1];
+    size_t nb = (size_t)L.E * L.nd * L.nd, es = C->pmg_prec ? sizeof(float) : sizeof(double);
+    const void *src_M = C->pmg_prec ? (const void *)C->p32.Md : (const void *)C->p64.Md;
+    const void *src_O = C->pmg_prec ? (const void *)C->p32.O : (const void *)C->p64.O;
+    cudaStream_t s = S_(stream);
+    CK(cudaMemcpyAsync(Md, src_M, es * nb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(O, src_O, es * nb * 2 * C->d, cudaMemcpyDeviceToDevice, s));
+    return FR_OK;
+}
+
 extern "C" int fr_mbnk_last(const fr_ctx *C, int *iters, double *relres) {
     if (!C || !C->mb_gm) return fail(FR_ERR_NOT_READY, "no matrix-based smoother has run");
     double g[2];
