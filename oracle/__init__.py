@@ -112,7 +112,7 @@ class SolveOpts(C.Structure):
                 ("nsmooth", C.c_int * 4), ("use_pmg", C.c_int), ("tol_gmres", C.c_double),
                 ("tol_newton", C.c_double), ("eps", C.c_double), ("dtau", C.c_double),
                 ("inv_dtau_star", C.c_double), ("mbnk", C.c_int), ("mbnk_maxit", C.c_int),
-                ("mbnk_tol", C.c_double)]
+                ("mbnk_tol", C.c_double), ("nonlinear", C.c_int)]
 
 
 class StepStats(C.Structure):
@@ -283,8 +283,13 @@ class Oracle:
 
     @staticmethod
     def opts(kdim=30, maxit_gmres=300, max_ptc=100, nsmooth=(2, 2), use_pmg=True, tol_gmres=1e-1,
-             tol_newton=1e-8, eps=1e-6, dtau=1.0, inv_dtau_star=0.0, coarse="ej", mbnk_maxit=5, mbnk_tol=0.1):
+             tol_newton=1e-8, eps=1e-6, dtau=1.0, inv_dtau_star=0.0, coarse="ej", mbnk_maxit=5, mbnk_tol=0.1,
+             nonlinear="jfnk"):
+        """nonlinear: the ESDIRK stage solver, "jfnk" (Newton-Krylov) or "pmg" (V-cycles)."""
         o = SolveOpts()
+        o.nonlinear = {"jfnk": 0, "pmg": 1}[nonlinear]
+        if o.nonlinear and not use_pmg:
+            raise ValueError("the pMG nonlinear solver needs the pMG levels (use_pmg)")
         o.mbnk, o.mbnk_maxit, o.mbnk_tol = int(coarse == "mbnk"), int(mbnk_maxit), float(mbnk_tol)
         o.kdim, o.maxit_gmres, o.max_ptc, o.nlev = kdim, maxit_gmres, max_ptc, len(nsmooth)
         for i, n in enumerate(nsmooth):

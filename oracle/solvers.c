@@ -434,6 +434,7 @@ typedef struct {
     double tol_gmres, tol_newton, eps, dtau, inv_dtau_star;
     int mbnk, mbnk_maxit;              /* matrix-based smoother on the coarsest level */
     double mbnk_tol;
+    int nonlinear;                     /* ESDIRK stage solver: 0 JFNK, 1 pMG V-cycles */
 } or_solve_opts;
 
 typedef struct { int n_ptc, n_gmres, converged; double final_res; } or_step_stats;
@@ -444,7 +445,11 @@ static double rms_scaled(size_t N, double a, const double *F) {
     return sqrt(s / (double)N);
 }
 
-/* ESDIRK step, Eqs. (2), (5)-(8); A is s x s row-major, b length s */
+/* ESDIRK step, Eqs. (2), (5)-(8); A is s x s row-major, b length s.
+ * o->nonlinear 0: each stage's pseudo-time Newton iteration solves (Eq. 8) A dq = -F by
+ * FGMRES (JFNK).  1: the pMG nonlinear solver (Sec. 3.1): dq is one V-cycle of the
+ * stage's pseudo-time equation, the preconditioner's cycle with X = -F, i.e. the FAS
+ * cycle for (1/dtau + 1/(a_ii dt)) dq - (R(q + dq) - R(q)) = -F(q). */
 int or_esdirk_step(or_ctx *C, int s, const double *A, const double *bw, double dt, double *q,
                    const or_solve_opts *o, or_step_stats *st) {
     size_t N = vlen(C, 0);
@@ -476,9 +481,13 @@ int or_esdirk_step(or_ctx *C, int s, const double *A, const double *bw, double d
             if (res <= o->tol_newton) { conv = 1; break; }
             if (k == o->max_ptc) break;
             for (size_t t = 0; t < N; ++t) F[t] = -F[t];
-            or_gmres_stats gs;
-            or_gmres(C, q, Rk, F, dq, o->kdim, o->tol_gmres, o->maxit_gmres, c, o->eps, o->use_pmg, &gs);
-            st->n_gmres += gs.iters;
+            if (o->nonlinear == 1) {
+                or_pmg_apply(C, q, Rk, F, dq);
+            } else {
+                or_gmres_stats gs;
+                or_gmres(C, q, Rk, F, dq, o->kdim, o->tol_gmres, o->maxit_gmres, c, o->eps, o->use_pmg, &gs);
+                st->n_gmres += gs.iters;
+            }
             for (size_t t = 0; t < N; ++t) q[t] = q[t] + dq[t];
             st->n_ptc++;
         }

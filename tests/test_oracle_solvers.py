@@ -275,3 +275,52 @@ def test_pmg_solver_reduces_the_residual():
     h = st["hist"]
     assert st["n_ptc"] == 150 and h[-1] < 1e-3 * h[0]
     assert np.all(h[-30:] <= 1.05 * h[-31:-1])
+
+
+def test_pmg_nonlinear_stage_solver_one_update_is_element_jacobi():
+    """ESDIRK3 with the pMG nonlinear stage solver, one level, one smoothing step, 1/dtau* = 0
+    and one update per stage (max_ptc = 1): every stage does q <- q^n - M^-1 F(q^n) with
+    M = (1/dtau + 1/(a_ii dt)) I - dR_e/dq_e at q^n, and the step is q^n + dt sum_j b_j R(Q_j);
+    rebuilt here in numpy from the residual and the element blocks."""
+    mesh = w.box2d(3, 3, 10, 10, qg=2, warp=0.1)
+    ph = w.Physics(mu=0.02, qinf=w.freestream(2, 0.3))
+    O = oracle.Oracle(mesh, ph, [2])
+    qn = angled_flow(mesh, 2)
+    A, b, _ = TB.esdirk3()
+    dt, dtau = 0.4, 0.7
+    o = O.opts(nsmooth=(1,), max_ptc=1, tol_newton=0.0, dtau=dtau, inv_dtau_star=0.0, nonlinear="pmg")
+    q_or, st = O.esdirk_step(A, b, dt, qn, o)
+    s = len(b)
+    c = 1.0 / dtau + 1.0 / (A[1, 1] * dt)
+    E = mesh["E"]
+    M = O.elem_blocks(qn, c, np.arange(E))
+    nd = M.shape[1]
+    Rs = [O.residual(qn)]
+    for i in range(1, s):
+        adt = A[i, i] * dt
+        sv = qn + dt * sum(A[i, j] * Rs[j] for j in range(i))
+        F = (qn - sv) / adt - O.residual(qn)
+        dq = np.stack([np.linalg.solve(M[e], -F.reshape(nd, E)[:, e]) for e in range(E)], axis=1).reshape(qn.shape)
+        Rs.append(O.residual(qn + dq))
+    ref = qn + dt * sum(b[j] * Rs[j] for j in range(s))
+    assert st["n_ptc"] == s - 1 and st["n_gmres"] == 0
+    assert np.abs(q_or - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_pmg_nonlinear_stage_solver_reaches_the_jfnk_state():
+    mesh = w.box2d(4, 4, 10, 10, qg=2, warp=0.1)
+    ph = w.Physics(mu=0.01, qinf=w.freestream(2, 0.5))
+    X = w.solution_point_coords(mesh, 2)
+    q0 = np.ascontiguousarray(w.isentropic_vortex(X, 5, 5, 5.0, 0.5, 10, 10))
+    dt = 10.0 * w.explicit_dt(mesh, 2, q0)
+    O = oracle.Oracle(mesh, ph, [2, 1])
+    A, b, _ = TB.esdirk3()
+    out = {}
+    for nl in ("jfnk", "pmg"):
+        o = O.opts(kdim=30, maxit_gmres=300, max_ptc=400, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-11,
+                   dtau=dt, inv_dtau_star=1.0 / dt, nonlinear=nl)
+        out[nl] = O.esdirk_step(A, b, dt, q0, o)
+    (qj, sj), (qp, sp) = out["jfnk"], out["pmg"]
+    assert sj["converged"] and sp["converged"] and sp["n_gmres"] == 0
+    assert sp["n_ptc"] > sj["n_ptc"]            # V-cycles converge linearly, Newton faster
+    assert np.abs(qp - qj).max() <= 1e-9 * np.abs(qj).max()
