@@ -240,6 +240,12 @@ typedef struct {
     double lr;
     int coarse_smoother, mbnk_maxit;   /* as fr_pmg_opts (when use_pmg) */
     double mbnk_tol;
+    /* ESDIRK stage solver (esdirk_step only): 0 JFNK (each pseudo-time Newton update by
+     * FGMRES, Eq. 8); 1 the pMG nonlinear solver of Sec. 3.1: each update is one V-cycle
+     * of the stage's pseudo-time equation, (1/dtau + 1/(a_ii dt)) dq - (R(q + dq) - R(q))
+     * = -F(q), i.e. pmg_precondition with X = -F; max_ptc bounds the cycles per stage.
+     * Needs use_pmg and precision 0; row_step and the batched step refuse it. */
+    int nonlinear;
 } fr_solve_opts;
 typedef struct {
     int n_ptc, n_gmres, converged;

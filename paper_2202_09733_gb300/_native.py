@@ -60,7 +60,8 @@ class SolveOpts(C.Structure):
                 ("tol_newton", C.c_double), ("eps", C.c_double), ("dtau", C.c_double),
                 ("inv_dtau_star", C.c_double), ("precision", C.c_int), ("guess", C.c_int),
                 ("train_iters", C.c_int), ("train_batch", C.c_int), ("lr", C.c_double),
-                ("coarse_smoother", C.c_int), ("mbnk_maxit", C.c_int), ("mbnk_tol", C.c_double)]
+                ("coarse_smoother", C.c_int), ("mbnk_maxit", C.c_int), ("mbnk_tol", C.c_double),
+                ("nonlinear", C.c_int)]
 
 
 class StepStats(C.Structure):

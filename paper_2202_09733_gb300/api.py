@@ -215,11 +215,13 @@ def _prec(p):
 
 def solve_opts(kdim=30, maxit_gmres=300, max_ptc=100, nsmooth=(2, 2), use_pmg=True, tol_gmres=1e-1,
                tol_newton=1e-8, eps=1e-6, dtau=1.0, inv_dtau_star=0.0, precision="fp64", guess="qn",
-               train_iters=0, train_batch=4096, lr=1e-3, coarse="ej", mbnk_maxit=5, mbnk_tol=0.1):
+               train_iters=0, train_batch=4096, lr=1e-3, coarse="ej", mbnk_maxit=5, mbnk_tol=0.1,
+               nonlinear="jfnk"):
     """guess: "qn" (the paper's q^n), "extrap" (best of q^n and the quadratic extrapolation
     in time) or "mlp" (also the network-corrected extrapolation); train_iters > 0 trains
     the attached network after every ESDIRK step.  coarse, mbnk_maxit, mbnk_tol: the
-    coarsest level's smoother, as in pmg_setup."""
+    coarsest level's smoother, as in pmg_setup.  nonlinear: the ESDIRK stage solver,
+    "jfnk" (pseudo-time Newton updates by FGMRES) or "pmg" (one V-cycle per update)."""
     o = N.SolveOpts()
     o.kdim, o.maxit_gmres, o.max_ptc, o.nlevels = int(kdim), int(maxit_gmres), int(max_ptc), len(nsmooth)
     for i, n in enumerate(nsmooth):
@@ -232,6 +234,9 @@ def solve_opts(kdim=30, maxit_gmres=300, max_ptc=100, nsmooth=(2, 2), use_pmg=Tr
         raise ValueError(f"guess must be one of {sorted(guesses)}")
     o.guess, o.train_iters, o.train_batch, o.lr = guesses[guess], int(train_iters), int(train_batch), float(lr)
     o.coarse_smoother, o.mbnk_maxit, o.mbnk_tol = _coarse(coarse), int(mbnk_maxit), float(mbnk_tol)
+    if nonlinear not in ("jfnk", "pmg"):
+        raise ValueError('nonlinear must be "jfnk" or "pmg"')
+    o.nonlinear = int(nonlinear == "pmg")
     return o
 
 

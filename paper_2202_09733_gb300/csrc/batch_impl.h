@@ -545,6 +545,8 @@ extern "C" int fr_batch_esdirk_step(fr_batch *B, const fr_esdirk_tableau *tab, d
     if (tab->stages < 2 || tab->stages > 6 || !(dt > 0.0)) return fail(FR_ERR_INVALID_ARG, "bad tableau or dt");
     if (o->guess != 0 || o->train_iters != 0)
         return fail(FR_ERR_UNIMPLEMENTED, "the batched step starts every stage from q^n (guess 0, no training)");
+    if (o->nonlinear != 0)
+        return fail(FR_ERR_UNIMPLEMENTED, "the batched step solves its stages by JFNK (nonlinear 0)");
     if (o->use_pmg && o->coarse_smoother != 0)
         return fail(FR_ERR_UNIMPLEMENTED, "the matrix-based coarse smoother's inner products would couple the problems "
                                           "of a group; batched steps smooth with element-Jacobi blocks");

@@ -1096,6 +1096,9 @@ static int check_solve_opts(const fr_ctx *C, const fr_solve_opts *o) {
         return fail(FR_ERR_INVALID_ARG, "nlevels outside 1..%d", C->nlev);
     if (o->precision != 0 && o->precision != 1) return fail(FR_ERR_INVALID_ARG, "precision must be 0 or 1");
     if (o->use_pmg) TRY(check_coarse_opts(o->coarse_smoother, o->mbnk_maxit, o->mbnk_tol));
+    if (o->nonlinear != 0 && o->nonlinear != 1) return fail(FR_ERR_INVALID_ARG, "nonlinear must be 0 (JFNK) or 1 (pMG)");
+    if (o->nonlinear == 1 && (!o->use_pmg || o->precision != 0))
+        return fail(FR_ERR_INVALID_ARG, "the pMG nonlinear solver needs use_pmg and the FP64 cycle (precision 0)");
     return FR_OK;
 }
 
@@ -1329,9 +1332,13 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
             if (res <= o->tol_newton) { conv = 1; break; }
             if (k == o->max_ptc) break;
             frk64_neg(n, F, F, s);
-            fr_gmres_stats gs;
-            TRY(gmres(C, q, Rk, F, dq, &go, &gs, s));
-            loc.n_gmres += gs.iters;
+            if (o->nonlinear == 1) {
+                TRY(pmg_apply(C, q, Rk, F, dq, s));       // one V-cycle of the stage's pseudo-time equation
+            } else {
+                fr_gmres_stats gs;
+                TRY(gmres(C, q, Rk, F, dq, &go, &gs, s));
+                loc.n_gmres += gs.iters;
+            }
             frk64_add(n, q, dq, q, s);
             loc.n_ptc++;
         }
@@ -1359,6 +1366,7 @@ extern "C" int row_step(fr_ctx *C, const fr_row_tableau *tab, double dt, double 
     if (!C || !tab || !q || !o) return fail(FR_ERR_INVALID_ARG, "NULL argument");
     if (tab->stages < 1 || tab->stages > 6 || !(dt > 0.0) || !(tab->gamma > 0.0)) return fail(FR_ERR_INVALID_ARG, "bad tableau or dt");
     TRY(check_solve_opts(C, o));
+    if (o->nonlinear != 0) return fail(FR_ERR_INVALID_ARG, "ROW stages are linear solves: nonlinear must be 0");
     cudaStream_t s = S_(stream);
     int ns = tab->stages;
     TRY(stepper_alloc(C, ns + 5));

@@ -364,3 +364,35 @@ def test_pmg_solver_steady_matches_oracle():
         assert np.allclose(st["hist"], st_or["hist"], rtol=1e-11)
     with pytest.raises(Exception, match="FP64"):
         api.pmg_solve_steady(G, dev(W.q0), dtau, dtau, 0.0, 1, api.solve_opts(nsmooth=(2, 2), precision="mixed"))
+
+
+def test_esdirk_step_pmg_nonlinear_solver():
+    """ESDIRK3 with the pMG nonlinear stage solver (one V-cycle per update, no FGMRES): the
+    residual, stage residual, linear combinations and the FP64 V-cycle all follow the
+    oracle's order, so the iterates match; only the stopping norms are summed in another
+    order.  Same cycle count, states within 1e-12.  ROW and the batched step refuse it."""
+    mesh = w.box2d(4, 4, 10, 10, qg=2, warp=0.1)
+    ph = w.Physics(mu=0.01, qinf=w.freestream(2, 0.5))
+    X = w.solution_point_coords(mesh, 2)
+    q0 = np.ascontiguousarray(w.isentropic_vortex(X, 5, 5, 5.0, 0.5, 10, 10))
+    dt = 10.0 * w.explicit_dt(mesh, 2, q0)
+    O = oracle.Oracle(mesh, ph, [2, 1])
+    G = api.fr_create(mesh, ph, [2, 1])
+    A, b, _ = OT.esdirk3()
+    oo = O.opts(kdim=30, maxit_gmres=300, max_ptc=400, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-10, dtau=dt,
+                inv_dtau_star=1.0 / dt, nonlinear="pmg")
+    q_or, st_or = O.esdirk_step(A, b, dt, q0, oo)
+    from paper_2202_09733_gb300 import tableaux as GT
+    Ag, bg = GT.esdirk3()
+    go = api.solve_opts(kdim=30, maxit_gmres=300, max_ptc=400, nsmooth=(2, 2), tol_gmres=1e-2, tol_newton=1e-10,
+                        dtau=dt, inv_dtau_star=1.0 / dt, nonlinear="pmg")
+    qg = dev(q0)
+    st = api.esdirk_step(G, Ag, bg, dt, qg, go)
+    assert st_or["converged"] and st["converged"] and st["n_gmres"] == 0
+    assert st["n_ptc"] == st_or["n_ptc"]
+    assert relerr(qg, q_or) <= 1e-12
+    g, a, c, m = GT.ros34pw2()
+    with pytest.raises(RuntimeError):
+        api.row_step(G, g, a, c, m, dt, dev(q0), go)
+    with pytest.raises(RuntimeError):
+        api.esdirk_step(G, Ag, bg, dt, dev(q0), api.solve_opts(nonlinear="pmg", precision="mixed"))
