@@ -13,6 +13,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <nvtx3/nvToolsExt.h>
 #include <vector>
 #include "../../include/frpmg.h"
 #include "fr_lib.h"
@@ -41,6 +42,17 @@ static int fail(int code, const char *fmt, ...) {
         if (_e != cudaSuccess)                                                                \
             return fail(FR_ERR_CUDA, "%s:%d kernel launch: %s", __FILE__, __LINE__, cudaGetErrorString(_e)); \
     } while (0)
+
+// NVTX range for a profiler's timeline (a no-op unless a tool is attached): time steps,
+// stages, pseudo-time updates, FGMRES solves, pMG set-ups and V-cycle levels
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+static const char *const kVcycleRange[FRL_MAXLEV] = {"vcycle level 0", "vcycle level 1", "vcycle level 2",
+                                                     "vcycle level 3"};
 
 #define TRY(x)                       \
     do {                             \
@@ -722,6 +734,7 @@ static int pmg_factor_levels(fr_ctx *C, const T *q_ref, const fr_pmg_opts *o, cu
 }
 
 static int pmg_setup_(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, cudaStream_t s) {
+    NvtxRange nv("pmg setup");
     C->pmg_ready = 0;
     C->pmg_nlev = o->nlevels;
     for (int l = 0; l < o->nlevels; ++l) C->nsmooth[l] = o->nsmooth[l];
@@ -843,6 +856,7 @@ static int smooth_t(fr_ctx *C, int l, int nsteps, const T *b, const T *Rb, const
 
 template <typename T>
 static int vcycle_t(fr_ctx *C, int l, const T *b, const T *Rb, const T *d, T *qh, cudaStream_t s) {
+    NvtxRange nv(kVcycleRange[l]);
     PmgBuf<T> &P = pbuf<T>(C);
     int n = C->nsmooth[l];
     TRY(smooth_t<T>(C, l, n, b, Rb, d, qh, true, s));
@@ -963,6 +977,7 @@ static int gmres_(fr_ctx *C, const double *q, const double *Rq, const double *b,
 // residual are formed by the first preconditioner application and reused by the rest
 static int gmres(fr_ctx *C, const double *q, const double *Rq, const double *b, double *x, const fr_gmres_opts *o,
                  fr_gmres_stats *st, cudaStream_t s) {
+    NvtxRange nv("fgmres");
     C->q32_of = nullptr;
     int rc = gmres_(C, q, Rq, b, x, o, st, s);
     C->q32_of = nullptr;
@@ -1271,6 +1286,7 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
     fr_gmres_opts go = gm_opts(o, c);
     int nguess_stages = 0;
     for (int i = 1; i < ns; ++i) {
+        NvtxRange nv_stage("esdirk stage");
         double adt = tab->A[i * ns + i] * dt;
         double coef[6], ci = 0.0;
         for (int j = 0; j < i; ++j) coef[j] = tab->A[i * ns + j];
@@ -1331,6 +1347,7 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
             if (!isfinite(res)) return fail(FR_ERR_NONFINITE, "non-finite stage residual (stage %d, iteration %d)", i, k);
             if (res <= o->tol_newton) { conv = 1; break; }
             if (k == o->max_ptc) break;
+            NvtxRange nv_upd("pseudo-time update");
             frk64_neg(n, F, F, s);
             if (o->nonlinear == 1) {
                 TRY(pmg_apply(C, q, Rk, F, dq, s));       // one V-cycle of the stage's pseudo-time equation
