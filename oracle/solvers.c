@@ -30,6 +30,16 @@
  *    q^{n+1} = q^n + sum m_j Y_j.
  *  - Steady PTC with SER (Eq. 10, read with the ratio ||F^k|| / ||F^{k+1}|| so that the
  *    pseudo step grows as the residual falls).
+ *  - Matrix-based Newton-Krylov smoother of the coarsest level (Sec. 3.2): the level's
+ *    shifted Jacobian assembled as element blocks plus face-neighbour blocks (forward
+ *    differences of the whole level residual, one dof at a time), and each smoothing
+ *    step's block solve replaced by GMRES (modified Gram-Schmidt, Givens) from zero,
+ *    right-preconditioned by the element blocks (block-Jacobi where the paper used ILU0),
+ *    stopping at the first iteration whose estimate meets the relative tolerance.
+ *  - pMG nonlinear solver: steady (one cycle with X = R(q) per SER pseudo step) and for
+ *    the ESDIRK stages (one cycle with X = -F per pseudo-time update, Sec. 3.1).
+ * Every function here is pinned by tests/test_oracle_*.py (the pins are listed in each
+ * file's docstring).
  */
 #include <math.h>
 #include <stdlib.h>
