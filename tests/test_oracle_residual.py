@@ -7,7 +7,9 @@
     (inviscid order p, viscous part order >= p-1), 2-D curved and 3-D;
   - linear stability: the linearised operator about a rest state has no eigenvalue with a
     positive real part beyond finite-difference noise;
-  - bitwise consistency of the element-local residual with the full residual."""
+  - bitwise consistency of the element-local residual with the full residual;
+  - the viscous part linearised about rest: mass-symmetric (affine) and negative
+    semidefinite (affine and curved)."""
 import math
 
 import numpy as np
@@ -166,3 +168,38 @@ def test_element_residual_matches_full_residual():
         qq[:, :, e] = qe
         Rfull = O.residual(qq)
         assert np.array_equal(Re, Rfull[:, :, e])
+
+
+@pytest.mark.parametrize("warp,p", [(0.0, 1), (0.0, 2), (0.1, 1), (0.1, 2)])
+def test_br2_viscous_operator_at_rest(warp, p):
+    """The viscous part of R linearised about a uniform rest state, momentum rows and
+    columns (the vector Laplacian of the stress), weighted by the Gauss-Legendre mass
+    matrix w_i J_i: symmetric to finite-difference accuracy on affine quads (BR2 is a
+    symmetric primal scheme) and negative semidefinite; on curved quads (metric terms
+    collocated, not integrated exactly) only its symmetric part is required to be
+    negative semidefinite."""
+    mesh = w.box2d(3, 3, 3.0, 3.0, qg=2, warp=warp)
+    q0 = np.array([1.0, 0.0, 0.0, (1 / (1.4 * 0.09)) / 0.4])
+
+    def jac(mu):
+        O = oracle.Oracle(mesh, w.Physics(mu=mu, qinf=q0.copy()), [p])
+        q = _uniform(O, 0, q0)
+        N = q.size
+        J = np.zeros((N, N))
+        for j in range(N):
+            e = np.zeros(N)
+            e[j] = 1e-6
+            J[:, j] = (O.residual(q + e.reshape(q.shape)) - O.residual(q - e.reshape(q.shape))).ravel() / 2e-6
+        return J, O
+
+    J1, O = jac(0.1)
+    J0, _ = jac(0.0)
+    Np, E = (p + 1) ** 2, mesh["E"]
+    t = oracle.table(p)
+    Wm = (np.outer(t["w"], t["w"]).ravel()[:, None] * O.jacobian_det()).ravel()
+    idx = np.concatenate([v * Np * E + np.arange(Np * E) for v in (1, 2)])
+    S = np.concatenate([Wm, Wm])[:, None] * (J1 - J0)[np.ix_(idx, idx)]
+    scale = np.abs(S).max()
+    if warp == 0.0:
+        assert np.abs(S - S.T).max() <= 1e-7 * scale
+    assert np.linalg.eigvalsh(0.5 * (S + S.T)).max() <= 1e-8 * scale
