@@ -26,7 +26,8 @@
  * Arithmetic.  The FP64 residual, Jacobian-vector product, element blocks, block LU,
  * block solves, transfers and preconditioner cycle evaluate every sum of products as an
  * fma chain in a fixed order with no other contraction, so they are reproducible bit
- * for bit run to run.  GMRES inner products use a fixed two-level reduction tree.
+ * for bit run to run.  GMRES inner products (the outer FGMRES and the matrix-based
+ * coarse smoother's) use fixed-order two-level reductions, so they too repeat bit for bit.
  */
 #ifndef FRPMG_H
 #define FRPMG_H
