@@ -68,3 +68,38 @@ def block_solve_flops(d: int, p: int) -> float:
     n, nv, np_, nfp = _shape(d, p)
     nd = nv * np_
     return float(2 * nd * nd)
+
+
+def assembled_product_bytes(d: int, p: int, word: int = 8, neighbours: int | None = None) -> float:
+    """one element's rows of the matrix-based smoother's product y = A x: its diagonal
+    block and one block per face neighbour (2d on an interior element), its own x and the
+    neighbours' x read, y written"""
+    n, nv, np_, nfp = _shape(d, p)
+    nd = nv * np_
+    nb = 2 * d if neighbours is None else neighbours
+    return float(word * ((nb + 1) * nd * nd + (nb + 1) * nd + nd))
+
+
+def assembled_product_flops(d: int, p: int, neighbours: int | None = None) -> float:
+    n, nv, np_, nfp = _shape(d, p)
+    nd = nv * np_
+    nb = 2 * d if neighbours is None else neighbours
+    return float(2 * (nb + 1) * nd * nd)
+
+
+def mbnk_solve_bytes(d: int, p: int, m: int, word: int = 8) -> float:
+    """compulsory bytes per element of one matrix-based smoothing solve with m Arnoldi
+    steps: per step a block solve, the assembled product and classical Gram-Schmidt twice
+    over the k + 1 basis vectors (each pass reads them twice: inner products, update) plus
+    the norm and scaling; then the combination of m vectors and the final block solve"""
+    n, nv, np_, nfp = _shape(d, p)
+    nd = nv * np_
+    per_vec = word * nd
+    total = per_vec * 2                                   # norm and scaling of the start vector
+    for k in range(m):
+        total += block_solve_bytes(d, p, word) + per_vec  # copy in, solve in place
+        total += assembled_product_bytes(d, p, word)
+        total += 2 * (2 * (k + 1) * per_vec + 2 * per_vec)    # two CGS passes
+        total += 3 * per_vec                              # norm (read) and scaling (read, write)
+    total += (m + 1) * per_vec + block_solve_bytes(d, p, word)
+    return float(total)

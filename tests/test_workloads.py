@@ -77,3 +77,4 @@ def test_states_are_physical():
         p = (w.GAMMA - 1.0) * (q[d + 1] - ke)
         assert np.all(rho > 0) and np.all(p > 0)
         assert wl.dt > 0
+
