@@ -57,6 +57,8 @@ def lib():
         L.or_elem_blocks.argtypes = [C.c_void_p, C.c_int, PD, C.c_double, PI, C.c_int, PD]
         L.or_lu_factor.argtypes = [C.c_int, PD, PI]
         L.or_lu_solve.argtypes = [C.c_int, PD, PI, PD]
+        L.or_lu_factor_div.argtypes = [C.c_int, PD, PI]
+        L.or_lu_solve_div.argtypes = [C.c_int, PD, PI, PD]
         L.or_restrict.argtypes = [C.c_void_p, C.c_int, PD, PD]
         L.or_prolong.argtypes = [C.c_void_p, C.c_int, PD, PD]
         L.or_pmg_setup.argtypes = [C.c_void_p, PD, C.c_int, PI, C.c_double, C.c_double, C.c_int, C.c_int,

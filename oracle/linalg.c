@@ -15,6 +15,8 @@
  * (the paper leaves the LU arithmetic open; one division per pivot instead of one per
  * solve).  Triangular solves as fma chains in the order the unknowns become known
  * (ascending column index forward, descending column index backward), x_k = s_k (1/u_kk).
+ * or_lu_factor_div / or_lu_solve_div are the textbook division form of the same
+ * elimination (x_k = s_k / u_kk), kept for the pin that the two forms agree.
  *
  * Transfers (Eqs. 17-18): the 1-D Gamma / Pi applied along direction 0, then 1, then 2.
  */
@@ -49,7 +51,8 @@ void or_elem_blocks(or_ctx *C, int l, const double *q, double shift, const int *
     free(R); free(qe); free(qp); free(R0); free(Rp);
 }
 
-void or_lu_factor(int n, double *A, int *piv) {
+/* the elimination; u_kk stays on the diagonal */
+static void lu_eliminate(int n, double *A, int *piv) {
     for (int k = 0; k < n; ++k) {
         int p = k;
         double best = fabs(A[(size_t)k * n + k]);
@@ -71,7 +74,30 @@ void or_lu_factor(int n, double *A, int *piv) {
                 A[(size_t)i * n + j] = fma(-li, A[(size_t)k * n + j], A[(size_t)i * n + j]);
         }
     }
+}
+
+void or_lu_factor(int n, double *A, int *piv) {
+    lu_eliminate(n, A, piv);
     for (int k = 0; k < n; ++k) A[(size_t)k * n + k] = 1.0 / A[(size_t)k * n + k];
+}
+
+/* Textbook form of the same factor and solve, for the pin that the reciprocal form above
+ * changes nothing beyond round-off: the diagonal keeps u_kk and the backward substitution
+ * divides, x_k = s_k / u_kk. */
+void or_lu_factor_div(int n, double *A, int *piv) { lu_eliminate(n, A, piv); }
+void or_lu_solve_div(int n, const double *A, const int *piv, double *b) {
+    for (int k = 0; k < n; ++k)
+        if (piv[k] != k) { double t = b[k]; b[k] = b[piv[k]]; b[piv[k]] = t; }
+    for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s = fma(-A[(size_t)i * n + k], b[k], s);
+        b[i] = s;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int k = n - 1; k > i; --k) s = fma(-A[(size_t)i * n + k], b[k], s);
+        b[i] = s / A[(size_t)i * n + i];
+    }
 }
 
 void or_lu_solve(int n, const double *A, const int *piv, double *b) {
