@@ -232,8 +232,12 @@ typedef struct {
      * 0: q^n; 1: the better (smaller FP64 stage residual RMS(a_ii dt F)) of q^n and the
      * quadratic extrapolation in time of the last three converged steps to t_n + c_i dt;
      * 2: as 1 plus the extrapolation corrected by the attached network (fr_set_mlp): the
- *    network's correction d enters scaled by the beta in [-1, 2] that minimises the
- *    linearised ||F(qex + beta d)|| (one extra residual), or unscaled if that is better.
+     * network's correction d enters scaled by the beta in [-1, 2] that minimises the
+     * linearised ||F(qex + beta d)|| (one extra residual), or unscaled if that is better.
+     * Only converged steps join the history, so a step that returns FR_ERR_NOT_CONVERGED
+     * leaves it as it was; a step whose dt differs from the history's spacing restarts
+     * the history from the current state (no extrapolation until three states of that
+     * spacing exist).
      * train_iters > 0: after the step, the converged stages join a training ring (the
      * last six steps) and the network takes train_iters Adam steps of train_batch
      * samples at learning rate lr. */
@@ -373,7 +377,9 @@ int fr_set_tiles(fr_ctx *ctx, int level, int precision, const int *tiles);
 int fr_autotune_save(const char *path);
 int fr_autotune_load(const char *path);
 /* bounded device-side waits that ran out since the last clear (bit 0: block-solve stage
- * barriers); such a kernel records the failure and returns instead of hanging */
+ * barriers); such a kernel records the failure and returns instead of hanging.  Bit 1:
+ * the bulk-copy block solve also gave up waiting for its own copies in flight, which may
+ * then land in shared memory after its CTA exited: treat the device as unusable. */
 int fr_kernel_timeouts(int clear);
 /* runs the time-out path of those waits on purpose (a barrier that nothing completes,
  * 4096 polls) so that callers can check that it reports through fr_kernel_timeouts and

@@ -535,8 +535,11 @@ __global__ void __launch_bounds__(128) k_lu_solve(const FRT *__restrict__ M, con
 // boundary at or after k+1), so the factor is read about once per solve; the warp
 // computes on stage t while stages t+1, t+2 are in flight.  The arithmetic is the
 // register kernel's, fma for fma, so both give the same result bits.  Every wait is
-// bounded: on time-out the warp records the failure in g_lub_err, waits (bounded) for its
-// own copies in flight and returns.  Needs nd * sizeof(FRT) % 16 == 0.
+// bounded: on time-out the warp waits (bounded) for its own copies in flight, records the
+// failure in g_lub_err (bit 0) and returns; if that drain wait also ran out, copies may
+// still land in the CTA's shared memory after it has exited, and bit 1 is set as well:
+// the device's state is then undefined and the process should not launch more work.
+// Needs nd * sizeof(FRT) % 16 == 0.
 #define LUB_W 6
 #define LUB_NS 3
 #define LUB_STAGE_BYTES 12288
@@ -631,13 +634,14 @@ __global__ void __launch_bounds__(32 * LUB_W) k_lu_solve_bulk(const FRT *__restr
         bool ok = lub_wait(&bars[st], (phase >> st) & 1u);
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) {
-                atomicExch(&g_lub_err, 1);
+                int code = 1;
                 // copies still in flight (issued for chunks t .. min(nt, t + LUB_NS) - 1)
                 for (int u = t; u < nt && u < t + LUB_NS; ++u) {
                     int su = u % LUB_NS;
-                    lub_wait(&bars[su], (phase >> su) & 1u);
+                    if (!lub_wait(&bars[su], (phase >> su) & 1u)) code = 3;
                     phase ^= 1u << su;
                 }
+                atomicOr(&g_lub_err, code);
             }
             __syncwarp();
             return;
@@ -720,7 +724,7 @@ static __global__ void k_wait_selftest(int limit) {
     if (threadIdx.x == 0) lub_expect(&bar, 16);
     __syncwarp();
     bool ok = lub_wait(&bar, 0, limit);
-    if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicExch(&g_lub_err, 1);
+    if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicOr(&g_lub_err, 1);
 }
 void FRK(wait_selftest)(int limit, cudaStream_t s) { CNT(); k_wait_selftest<<<1, 32, 0, s>>>(limit); }
 

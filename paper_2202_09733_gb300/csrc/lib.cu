@@ -129,6 +129,7 @@ struct fr_ctx {
     // initial guess: last three converged states, extrapolation, learned correction
     double *hist[3];              // q^{n-2}, q^{n-1}, q^n
     int nhist;
+    double hist_dt;               // step between the history states (0: not yet spaced)
     fr_mlp *mlp;
     int K0, O, mlp_steps;
     double *qex, *qcand, *Rtmp, *Ftmp, *Fex, *sdev, *qinf_dev, *vpart;
@@ -1149,6 +1150,7 @@ extern "C" int fr_set_mlp(fr_ctx *C, fr_mlp *M) {
 extern "C" int fr_reset_history(fr_ctx *C) {
     if (!C) return fail(FR_ERR_INVALID_ARG, "NULL context");
     C->nhist = 0;
+    C->hist_dt = 0.0;
     C->ring_n = 0;
     C->ring_head = 0;
     C->train_cursor = 0;
@@ -1265,7 +1267,14 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
     bool learn = o->guess > 0 || o->train_iters > 0;
     if (learn) {
         TRY(ensure_guess_buffers(C, ns));
-        if (C->nhist == 0) push_history(C, q, s);
+        // the extrapolation and the network's features assume states spaced by this dt:
+        // a history taken at another step (a caller that halved dt after a failed step)
+        // restarts from the current state
+        if (C->nhist >= 2 && C->hist_dt != 0.0 && fabs(C->hist_dt - dt) > 1e-12 * dt) C->nhist = 0;
+        if (C->nhist == 0) {
+            push_history(C, q, s);
+            C->hist_dt = 0.0;
+        }
     }
     bool have3 = learn && C->nhist >= 3;
     if (have3) frkmlp_var_stats(L0.nv, (long long)L0.np * L0.E, C->hist[2], C->hist[1], C->qinf_dev, C->vpart, C->sdev, s);
@@ -1370,7 +1379,12 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
     for (int k = 0; k < 3 && nguess_stages; ++k) loc.guess_rms[k] /= nguess_stages;
     if (nguess_stages) loc.guess_beta /= nguess_stages;
     frk64_lincomb(n, ns, tab->b, (const double *const *)Rs, qn, dt, q, s);
-    if (learn) push_history(C, q, s);
+    // only a converged step extends the history: a caller that undoes a failed step (and
+    // retries it) finds the history as it was before the attempt
+    if (learn && loc.converged) {
+        push_history(C, q, s);
+        C->hist_dt = dt;
+    }
     if (o->train_iters > 0) TRY(train_from_ring(C, o, &loc, s));
     CKLAUNCH();
     CK(cudaStreamSynchronize(s));
@@ -1498,7 +1512,7 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
 static const long long kCkMagic = 0x31504B43474D5046LL;   // "FPMGCKP1"
 enum { CK_MAGIC, CK_VERSION, CK_E, CK_NV, CK_NP, CK_NDOF, CK_HAS_GUESS, CK_K0, CK_O, CK_NHIST, CK_RING_CAP,
        CK_RING_N, CK_RING_HEAD, CK_CURSOR, CK_MLP_STEPS, CK_HAS_MLP, CK_MLP_IN, CK_MLP_HID, CK_MLP_OUT, CK_MLP_T,
-       CK_MLP_FLOATS, CK_NHEAD = 24 };
+       CK_MLP_FLOATS, CK_HIST_DT, CK_NHEAD = 24 };
 
 static long long ck_bytes(const fr_ctx *C, const fr_mlp *M) {
     long long b = 8LL * CK_NHEAD;
@@ -1526,6 +1540,7 @@ extern "C" int fr_checkpoint_save(const fr_ctx *C, const fr_mlp *M, void *buf, l
     h[CK_NDOF] = C->L[0].ndof; h[CK_HAS_GUESS] = C->qex != nullptr; h[CK_K0] = C->K0; h[CK_O] = C->O;
     h[CK_NHIST] = C->nhist; h[CK_RING_CAP] = C->ring_cap; h[CK_RING_N] = C->ring_n; h[CK_RING_HEAD] = C->ring_head;
     h[CK_CURSOR] = C->train_cursor; h[CK_MLP_STEPS] = C->mlp_steps; h[CK_HAS_MLP] = M != nullptr;
+    memcpy(&h[CK_HIST_DT], &C->hist_dt, sizeof(double));
     char *p = (char *)buf + 8 * CK_NHEAD;
     if (C->qex) {
         size_t sb = sizeof(double) * C->L[0].ndof;
@@ -1570,8 +1585,10 @@ extern "C" int fr_checkpoint_load(fr_ctx *C, fr_mlp *M, const void *buf, long lo
         CK(cudaMemcpy(C->ringT, p, tb, cudaMemcpyHostToDevice)); p += tb;
         C->nhist = (int)h[CK_NHIST]; C->ring_n = (int)h[CK_RING_N]; C->ring_head = (int)h[CK_RING_HEAD];
         C->train_cursor = (int)h[CK_CURSOR];
+        memcpy(&C->hist_dt, &h[CK_HIST_DT], sizeof(double));
     } else {
         C->nhist = 0; C->ring_n = 0; C->ring_head = 0; C->train_cursor = 0;
+        C->hist_dt = 0.0;
     }
     C->mlp_steps = (int)h[CK_MLP_STEPS];
     if (h[CK_HAS_MLP]) {

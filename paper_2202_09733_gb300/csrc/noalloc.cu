@@ -15,6 +15,7 @@
 // contexts, other host threads) race on it.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <mutex>
 #include "../../include/frpmg.h"
 #include "fr_lib.h"
 
@@ -24,8 +25,12 @@
 static __device__ __align__(256) double g_fr_noalloc_scratch[FR_NOALLOC_MAX_DOUBLES];
 
 // host copies of the array's device address, one per device ordinal, filled on the first
-// call made with that device current
+// call made with that device current (under g_scratch_mutex, so first calls on several
+// host threads do not race).  The address belongs to the device's primary context: after
+// cudaDeviceReset the library's module, and with it this array, is gone, and the process
+// must not call into the library again.
 static double *g_scratch_addr[FR_NOALLOC_MAX_DEVICES];
+static std::mutex g_scratch_mutex;
 
 // access to the context's level data (defined in lib.cu)
 extern "C++" int fr_internal_level(const fr_ctx *ctx, int level, FrLevel *out, FrPhysH *ph);
@@ -52,14 +57,18 @@ extern "C" int fr_residual_noalloc(fr_ctx *ctx, int level, const double *q, doub
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= FR_NOALLOC_MAX_DEVICES)
         return fr_internal_fail(FR_ERR_CUDA, "fr_residual_noalloc: no usable current device");
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_fr_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fr_internal_fail(FR_ERR_CUDA, "fr_residual_noalloc: cudaGetSymbolAddress failed");
-        g_scratch_addr[dev] = (double *)p;
+    double *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (!g_scratch_addr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_fr_noalloc_scratch);
+            if (e != cudaSuccess || !p)
+                return fr_internal_fail(FR_ERR_CUDA, "fr_residual_noalloc: cudaGetSymbolAddress failed");
+            g_scratch_addr[dev] = (double *)p;
+        }
+        base = g_scratch_addr[dev];
     }
-    double *base = g_scratch_addr[dev];
     L.qf = base;
     L.dq = base + nfv;
     L.fn = base + 2 * nfv;

@@ -89,3 +89,36 @@ def test_retrying_driver_restores_and_halves(vortex):
     for _ in range(2):
         api.esdirk_step(G, A, b, 0.5 * dt, ref, opts(dt))
     assert float((q - ref).abs().max() / ref.abs().max()) <= 1e-9
+
+
+def test_failed_step_leaves_the_guess_history_unchanged(vortex):
+    """A step that does not converge must not enter the learned guess's history, and a
+    retry at dt/2 must not extrapolate from states spaced by dt: a context that saw the
+    failed attempt and one that never did take the same (bit for bit) steps afterwards."""
+    _, q0, dt = vortex
+    mesh = w.box2d(4, 4, 10, 10, qg=2, warp=0.1)
+    ph = w.Physics(mu=0.01, qinf=w.freestream(2, 0.5))
+    A, b = GT.esdirk3()
+    GA, GB = api.fr_create(mesh, ph, [2, 1]), api.fr_create(mesh, ph, [2, 1])
+    qa, qb = torch.from_numpy(q0.copy()).cuda(), torch.from_numpy(q0.copy()).cuda()
+    for _ in range(3):
+        api.esdirk_step(GA, A, b, dt, qa, opts(dt, guess="extrap"))
+        api.esdirk_step(GB, A, b, dt, qb, opts(dt, guess="extrap"))
+    before = api.fr_checkpoint_save(GA)
+    qf = qa.clone()
+    st = api.esdirk_step(GA, A, b, dt, qf, opts(dt, guess="extrap", tol_newton=0.0, max_ptc=1))
+    assert not st["converged"]
+    assert api.fr_checkpoint_save(GA) == before           # history and ring untouched
+    picks = []
+    for G, q in ((GA, qa), (GB, qb)):
+        ps = []
+        for h in (0.5 * dt,) * 4:
+            s = api.esdirk_step(G, A, b, h, q, opts(dt, guess="extrap"))
+            assert s["converged"]
+            ps.append(tuple(s["guess_pick"]))
+        picks.append(ps)
+    assert picks[0] == picks[1]
+    # a changed dt restarts the history: the first two half steps have no extrapolation
+    # candidate, the later ones do (three states spaced by dt/2)
+    assert sum(picks[0][0]) == sum(picks[0][1]) == 0 and sum(picks[0][3]) > 0
+    assert torch.equal(qa, qb)
