@@ -124,6 +124,15 @@ int fr_jvp(fr_ctx *ctx, const double *q, const double *Rq, const double *v, doub
  * forward difference with step 1e-7 max(1, |q_j|).  q: device level state; M: device,
  * E * nd * nd doubles, column-major per element (see Layouts). */
 int fr_elem_blocks(fr_ctx *ctx, int level, const double *q, double shift, double *M, void *stream);
+/* The same blocks in FP32 (the mixed preconditioner's), exact derivatives of the FP32
+ * residual instead of differences: q device FP32 [nv][Np][E] level state, M device FP32,
+ * E nd^2 values column-major per element.  method 0: element by element, each element's
+ * residual differentiated with its neighbours' face traces and face gradients frozen
+ * (the neighbour's face gradient still follows the common solution through its BR2
+ * lifting); method 1: whole-level forward-mode residuals over an element colouring, a few
+ * columns per evaluation.  The two agree to FP32 rounding; method 0 is refused
+ * (FR_ERR_INVALID_ARG) on meshes where a face joins an element to itself. */
+int fr_elem_blocks_f32(fr_ctx *ctx, int level, const float *q, double shift, float *M, int method, void *stream);
 
 /* Sec. 3.2 matrix-based smoother: the element blocks M (as fr_elem_blocks) and the face
  * neighbour blocks O of the shifted Jacobian on a level in one pass over a distance-2
@@ -354,7 +363,7 @@ int pmg_solve_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, 
 
 /* ---------------------------------------------------------------- autotuner
  * Launch shapes (not in the paper; no result bit depends on them): the CTA size (elements
- * per CTA tile, 64/128/256) of each of the 8 kernels of the residual, per level and
+ * per CTA tile, 64/128/256) of each of the 7 kernels of the residual, per level and
  * precision, and the columns in flight G (2/4/8) of the block solve.  fr_autotune times
  * the candidates with CUDA events on the context's own levels (reps launches each after
  * a warm-up; a coordinate-descent pass over the residual kernels, then the solve variant
@@ -367,7 +376,8 @@ int pmg_solve_steady(fr_ctx *ctx, double *q, double dtau_init, double dtau_max, 
  * to use from several host threads; new contexts pick cached shapes up.  report (host, may be NULL): one line per level.
  * Uses the legacy default stream and synchronises the device. */
 int fr_autotune(fr_ctx *ctx, int flags, int reps, char *report, int report_len);
-/* tiles[9]: the 8 CTA sizes (0 = default 128; else a multiple of 32 in 32..256) and G
+/* tiles[9]: 8 CTA-size slots (the residual's 7 kernels, slot 5 unused; 0 = default 128;
+ * else a multiple of 32 in 32..256) and G
  * (0 = default, 1 = bulk-copy kernel, 2, 4 or 8) of level `level` in precision 0 (FP64)
  * or 1 (FP32) */
 int fr_get_tiles(const fr_ctx *ctx, int level, int precision, int *tiles);

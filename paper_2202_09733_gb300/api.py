@@ -106,6 +106,17 @@ def fr_elem_blocks(ctx, level, q, shift, M=None, stream=None):
     return M
 
 
+def fr_elem_blocks_f32(ctx, level, q32, shift, method="local", M=None, stream=None):
+    """FP32 blocks of the FP32 state q32 as a [E, nd(col j), nd(row r)] float32 tensor;
+    method "local" (element by element) or "colour" (whole-level evaluations)."""
+    nd = ctx.nd(level)
+    M = torch.empty((ctx.E, nd, nd), dtype=torch.float32, device="cuda") if M is None else M
+    meth = {"local": 0, "colour": 1}[method]
+    N.check(N.load().fr_elem_blocks_f32(ctx.handle, level, _dev(q32, torch.float32, "q32"), float(shift),
+                                        _dev(M, torch.float32, "M"), meth, _stream(stream)), "fr_elem_blocks_f32")
+    return M
+
+
 def fr_nbr_blocks(ctx, level, q, shift, stream=None):
     """(M, O): element blocks [E, nd(col), nd(row)] and face-neighbour blocks
     [E, 2d, nd(col), nd(row)] (column-major per block) of the shifted Jacobian."""

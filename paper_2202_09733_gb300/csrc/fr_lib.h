@@ -17,10 +17,13 @@ struct FrLevelT {
     int4 *pairs;                  // (eL, kL, eR, kR), sorted by (kL, eL)
     int *bc;
     typename FrBase<T>::type *S, *G, *invJ, *Sf, *Gf;
-    // residual workspace
-    T *qf, *dq, *Q, *Qf, *fn, *Ft, *Ftf;
+    // residual workspace: traces, jumps, face gradients, common fluxes, transformed fluxes
+    // (volume and at the faces); the corrected volume gradient lives in registers only
+    T *qf, *dq, *Qf, *fn, *Ft, *Ftf;
     double etagL, etagR;
-    // launch shapes (0 = default): CTA size of the 8 residual kernels; block solve: columns
+    // launch shapes (0 = default): CTA size of the residual kernels (0 interpolation,
+    // 1 common solution, 2 gradient + volume flux, 3 face gradients, 4 face flux, 5 unused,
+    // 6 face values of the transformed flux, 7 divergence); block solve: columns
     // in flight of the register kernel (2, 4, 8) or 1 = the bulk-copy (TMA) kernel
     short tile[8];
     short lu_g;
@@ -124,6 +127,12 @@ void frkad_block_column(const FrLevelAD &L, const int *color, int col, int j0, c
 
 void frkad_nbr_column(const FrLevelAD &L, int nf, const int *nbr, const int *color2, int col, int j0,
                       const DualT *Rd, float *O, cudaStream_t s);
+// element-local FP32 blocks (fr_ad_elem.cuh): qf, Qf are the FP32 residual workspace's
+// traces and face gradients at q (a residual at q must precede the call); NT (floats,
+// frkad_elem_nt_floats) and BCk (nfp E bytes) are scratch
+long long frkad_elem_nt_floats(const FrLevel32 &L);
+int frkad_elem_blocks(const FrLevel32 &L, const FrPhysH &h, const float *q, const float *qf, const float *Qf,
+                      float *NT, signed char *BCk, double shift, float *M, cudaStream_t s);
 
 // matrix-based Newton-Krylov smoother of the coarsest level (mbnk.cu).  Device scratch
 // gm (FRMB_GM doubles): Hessenberg H[i m + k] at 0, Gram-Schmidt coefficients at

@@ -34,14 +34,13 @@ template <int D, int P>
 static void residual_ad(const FrLevelAD &L, const FrPhys<float> &ph, const DualT *q, DualT *R, cudaStream_t s) {
     using S = Sh<D, P>;
     const int E = L.E, gx = (E + 127) / 128, gp = (L.npairs + 127) / 128;
-    CNT(); k_interp<D, P, DualT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, E);
+    CNT(); k_interp<D, P, DualT><<<dim3(gx, S::nfp), 128, 0, s>>>(q, L.qf, E);
     CNT(); k_pair_common<D, P, DualT><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.dq, E, ph);
-    CNT(); k_grad_sp<D, P, DualT><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(q, L.dq, L.G, L.Q, E);
-    CNT(); k_grad_fp<D, P, DualT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
+    CNT(); k_grad_fp<D, P, DualT><<<dim3(gx, S::nfp), 128, 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
     CNT(); k_pair_flux<D, P, DualT><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.Qf, L.Sf, L.fn, E, ph);
-    CNT(); k_vflux<D, P, DualT><<<dim3(gx, S::np), 128, 0, s>>>(q, L.Q, L.S, L.Ft, E, ph);
-    CNT(); k_face_ft<D, P, DualT><<<dim3(gx, S::nv * S::nfp), 128, 0, s>>>(L.Ft, L.Ftf, E);
-    CNT(); k_div<D, P, DualT><<<dim3(gx, S::nv * S::np), 128, 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
+    CNT(); k_grad_vflux<D, P, DualT><<<dim3(gx, S::np), 128, 0, s>>>(q, L.dq, L.G, L.S, L.Ft, E, ph);
+    CNT(); k_face_ft<D, P, DualT><<<dim3(gx, S::nfp), 128, 0, s>>>(L.Ft, L.Ftf, E);
+    CNT(); k_div<D, P, DualT><<<dim3(gx, S::np), 128, 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
 }
 
 int frkad_residual(const FrLevelAD &L, const FrPhysH &h, const DualT *q, DualT *R, cudaStream_t s) {
@@ -146,4 +145,62 @@ void frkad_nbr_column(const FrLevelAD &L, int nf, const int *nbr, const int *col
                       const DualT *Rd, float *O, cudaStream_t s) {
     long long n = (long long)L.E * L.nd;
     CNT(); k_ad_nbr_column<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L.E, L.nd, nf, nbr, color2, col, j0, Rd, O);
+}
+
+// ------------------------------------------- element-local blocks (fr_ad_elem.cuh)
+#include "fr_ad_elem.cuh"
+
+static FrPhys<float> ad_phys(const FrPhysH &h, const FrLevel32 &L) {
+    FrPhys<float> ph;
+    ph.gamma = (float)h.gamma; ph.gm1 = (float)h.gm1; ph.mu = (float)h.mu; ph.kappa = (float)h.kappa;
+    ph.c23 = (float)h.c23;
+    for (int v = 0; v < 5; ++v) ph.qinf[v] = (float)h.qinf[v];
+    ph.etagL = (float)L.etagL; ph.etagR = (float)L.etagR;
+    ph.flux = h.flux;
+    return ph;
+}
+
+// elements per CTA: two CTAs of 128 threads per SM within about 100 KB of shared memory each
+template <int D, int P>
+static int ad_elem_te() {
+    int te = (int)((100 * 1024) / AdElem<D, P>::bytes_per_elem);
+    return te < 1 ? 1 : (te > 32 ? 32 : te);
+}
+
+template <int D, int P>
+static void ad_elem_t(const FrLevel32 &L, const FrPhys<float> &ph, const float *q, const float *qf, const float *Qf,
+                      float *NT, signed char *BCk, double shift, float *M, cudaStream_t s) {
+    const int E = L.E, TE = ad_elem_te<D, P>();
+    const size_t smem = (size_t)TE * AdElem<D, P>::bytes_per_elem;
+    static bool attr_done = false;   // per instantiation; set before the first launch
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_ad_elem_blocks<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_done = true;
+    }
+    CNT(); k_ad_traces<D, P><<<(L.npairs + 255) / 256, 256, 0, s>>>(L.pairs, L.bc, L.npairs, qf, Qf, L.Gf,
+                                                                    ph.etagL, ph.etagR, E, NT, BCk);
+    CNT(); k_ad_elem_blocks<D, P><<<(E + TE - 1) / TE, 128, smem, s>>>(q, L.G, L.S, L.invJ, L.Gf, L.Sf, NT, BCk, E, TE,
+                                                                        ph, (float)shift, M);
+}
+
+long long frkad_elem_nt_floats(const FrLevel32 &L) { return (long long)(L.nv + L.d * L.nv + L.d) * L.nfp * L.E; }
+
+int frkad_elem_blocks(const FrLevel32 &L, const FrPhysH &h, const float *q, const float *qf, const float *Qf,
+                      float *NT, signed char *BCk, double shift, float *M, cudaStream_t s) {
+    FrPhys<float> ph = ad_phys(h, L);
+    if (L.d == 2) {
+        switch (L.p) {
+            case 1: ad_elem_t<2, 1>(L, ph, q, qf, Qf, NT, BCk, shift, M, s); return 0;
+            case 2: ad_elem_t<2, 2>(L, ph, q, qf, Qf, NT, BCk, shift, M, s); return 0;
+            case 3: ad_elem_t<2, 3>(L, ph, q, qf, Qf, NT, BCk, shift, M, s); return 0;
+            case 4: ad_elem_t<2, 4>(L, ph, q, qf, Qf, NT, BCk, shift, M, s); return 0;
+        }
+    } else if (L.d == 3) {
+        switch (L.p) {
+            case 1: ad_elem_t<3, 1>(L, ph, q, qf, Qf, NT, BCk, shift, M, s); return 0;
+            case 2: ad_elem_t<3, 2>(L, ph, q, qf, Qf, NT, BCk, shift, M, s); return 0;
+            case 3: ad_elem_t<3, 3>(L, ph, q, qf, Qf, NT, BCk, shift, M, s); return 0;
+        }
+    }
+    return -1;
 }

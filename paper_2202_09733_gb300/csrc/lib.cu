@@ -100,6 +100,9 @@ struct fr_ctx {
     DualT *qd, *Rd;
     int ncolor;
     int *color;
+    int self_face;                // a face joins an element to itself (periodic, one element wide)
+    float *ad_nt;                 // element-local FP32 blocks: the other sides' frozen face data
+    signed char *ad_bck;          //   and the boundary code of every element face point
     int ncolor2;
     int *color2;                  // distance-2 colouring (assembly of the neighbour blocks)
     int *nbr;                     // face neighbours nbr[f E + e], -1 none
@@ -238,7 +241,7 @@ static int setup_level(fr_ctx *C, int l, int p, const fr_mesh_desc *m) {
     CK(cudaMemcpy(L.bc, bc.data(), sizeof(int) * bc.size(), cudaMemcpyHostToDevice));
     size_t nfv = (size_t)C->nv * L.nfp * E, npv = (size_t)C->nv * L.np * E;
     TRY(dalloc_t(C, &L.qf, nfv)); TRY(dalloc_t(C, &L.dq, nfv)); TRY(dalloc_t(C, &L.fn, nfv));
-    TRY(dalloc_t(C, &L.Ftf, nfv)); TRY(dalloc_t(C, &L.Q, d * npv)); TRY(dalloc_t(C, &L.Ft, d * npv));
+    TRY(dalloc_t(C, &L.Ftf, nfv)); TRY(dalloc_t(C, &L.Ft, d * npv));
     TRY(dalloc_t(C, &L.Qf, d * nfv));
     return FR_OK;
 }
@@ -282,6 +285,8 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
     C->ph.flux = ph->flux;
     int rc = upload_tables();
     for (int l = 0; rc == FR_OK && l < m->nlevels; ++l) rc = setup_level(C, l, m->plevels[l], m);
+    for (int F = 0; F < m->nfaces; ++F)
+        if (m->faces[6 * F + 2] == m->faces[6 * F]) C->self_face = 1;
     if (rc == FR_OK) {
         std::vector<int> col(C->E);
         C->ncolor = frh_color(C->E, m->nfaces, m->faces, col.data());
@@ -457,7 +462,7 @@ static int ensure_levels32(fr_ctx *C) {
         frk32_d2f(nfpt, L.Sf, M.Sf, 0); frk32_d2f(nfpt, L.Gf, M.Gf, 0);
         size_t nfv = (size_t)L.nv * L.nfp * E, npv = (size_t)L.nv * L.np * E;
         TRY(dalloc_t(C, &M.qf, nfv)); TRY(dalloc_t(C, &M.dq, nfv)); TRY(dalloc_t(C, &M.fn, nfv));
-        TRY(dalloc_t(C, &M.Ftf, nfv)); TRY(dalloc_t(C, &M.Q, L.d * npv)); TRY(dalloc_t(C, &M.Ft, L.d * npv));
+        TRY(dalloc_t(C, &M.Ftf, nfv)); TRY(dalloc_t(C, &M.Ft, L.d * npv));
         TRY(dalloc_t(C, &M.Qf, L.d * nfv));
     }
     long long n0 = C->L[0].ndof;
@@ -493,7 +498,7 @@ static int ensure_levelsAD(fr_ctx *C) {
         A.S = F.S; A.G = F.G; A.invJ = F.invJ; A.Sf = F.Sf; A.Gf = F.Gf;
         size_t E = F.E, nfv = (size_t)F.nv * F.nfp * E, npv = (size_t)F.nv * F.np * E;
         TRY(dalloc_t(C, &A.qf, nfv)); TRY(dalloc_t(C, &A.dq, nfv)); TRY(dalloc_t(C, &A.fn, nfv));
-        TRY(dalloc_t(C, &A.Ftf, nfv)); TRY(dalloc_t(C, &A.Q, F.d * npv)); TRY(dalloc_t(C, &A.Ft, F.d * npv));
+        TRY(dalloc_t(C, &A.Ftf, nfv)); TRY(dalloc_t(C, &A.Ft, F.d * npv));
         TRY(dalloc_t(C, &A.Qf, F.d * nfv));
     }
     TRY(dalloc_t(C, &C->qd, C->L[0].ndof));
@@ -502,9 +507,29 @@ static int ensure_levelsAD(fr_ctx *C) {
     return FR_OK;
 }
 
-// FP32 blocks of level l: one forward-mode residual per (colour, column), seed 1 in
-// degree of freedom j of the colour's elements
-static int elem_blocks_ad(fr_ctx *C, int l, const float *q, double shift, float *M, cudaStream_t s) {
+// FP32 blocks of level l, element by element (fr_ad_elem.cuh): one FP32 residual at q
+// leaves the traces and face gradients that the other side of every face contributes,
+// then one kernel differentiates each element's residual in all its degrees of freedom
+static int elem_blocks_ad_local(fr_ctx *C, int l, const float *q, double shift, float *M, cudaStream_t s) {
+    TRY(ensure_levels32(C));
+    TRY(ensure_blk_tmp<float>(C));
+    if (!C->ad_nt) {
+        TRY(dalloc_t(C, &C->ad_nt, (size_t)frkad_elem_nt_floats(C->L32[0])));
+        TRY(dalloc_t(C, &C->ad_bck, (size_t)C->L32[0].nfp * C->E));
+    }
+    FrLevel32 &F = C->L32[l];
+    TRY(residual_t<float>(C, l, q, pbuf<float>(C).blk_R0, s));
+    if (frkad_elem_blocks(F, C->ph, q, F.qf, F.Qf, C->ad_nt, C->ad_bck, shift, M, s) != 0)
+        return fail(FR_ERR_UNIMPLEMENTED, "no kernel for d=%d p=%d", C->d, F.p);
+    CKLAUNCH();
+    return FR_OK;
+}
+
+// FP32 blocks of level l by colours: one forward-mode residual of the whole level per
+// (colour, batch of FR_AD_K columns), seeds in those degrees of freedom of the colour's
+// elements.  The element-local kernel above gives the same blocks to FP32 rounding; this
+// path serves meshes where a face joins an element to itself.
+static int elem_blocks_ad_colour(fr_ctx *C, int l, const float *q, double shift, float *M, cudaStream_t s) {
     TRY(ensure_levelsAD(C));
     FrLevelAD &A = C->LA[l];
     frkad_init(A.ndof, q, C->qd, s);
@@ -524,9 +549,22 @@ static int elem_blocks_ad(fr_ctx *C, int l, const float *q, double shift, float 
 // come from forward-mode differentiation instead of differences
 template <typename T>
 static int elem_blocks_t(fr_ctx *C, int l, const T *q, double shift, T *M, cudaStream_t s);
+static int elem_blocks_ad(fr_ctx *C, int l, const float *q, double shift, float *M, cudaStream_t s) {
+    return C->self_face ? elem_blocks_ad_colour(C, l, q, shift, M, s) : elem_blocks_ad_local(C, l, q, shift, M, s);
+}
 template <>
 int elem_blocks_t<float>(fr_ctx *C, int l, const float *q, double shift, float *M, cudaStream_t s) {
     return elem_blocks_ad(C, l, q, shift, M, s);
+}
+
+extern "C" int fr_elem_blocks_f32(fr_ctx *C, int l, const float *q, double shift, float *M, int method, void *stream) {
+    if (!C || l < 0 || l >= C->nlev || !q || !M) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    if (method < 0 || method > 1) return fail(FR_ERR_INVALID_ARG, "method must be 0 (element-local) or 1 (colours)");
+    if (method == 0 && C->self_face)
+        return fail(FR_ERR_INVALID_ARG, "a face joins an element to itself: only the colouring method applies");
+    cudaStream_t s = S_(stream);
+    TRY(ensure_levels32(C));
+    return method == 0 ? elem_blocks_ad_local(C, l, q, shift, M, s) : elem_blocks_ad_colour(C, l, q, shift, M, s);
 }
 template <>
 int elem_blocks_t<double>(fr_ctx *C, int l, const double *q, double shift, double *M, cudaStream_t s) {
@@ -1735,6 +1773,7 @@ static int tune_level(fr_ctx *C, int l, int prec, int reps, char *rep, size_t re
     int rc = time_residual<T>(C, l, q, R, reps, e0, e1, &t0);
     best = t0;
     for (int k = 0; rc == FR_OK && k < 8; ++k) {
+        if (k == 5) continue;          // no kernel in this slot
         short keep = L.tile[k];
         for (short c : cand) {
             L.tile[k] = c;
