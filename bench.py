@@ -15,7 +15,8 @@ Output: one JSON line with the step wall time (value), the FP64 residual through
 oracle baseline on this machine's host cores, the kernel-launch count and the SM clocks.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this build) on a
-bounded sample of the same workload (a 4^3 slice at the same CFL, scaled to 32^3).
+bounded sample of the same workload (an 8^3 slice at the same CFL on all host cores,
+scaled to 32^3 by the element count).
 """
 from __future__ import annotations
 
@@ -34,8 +35,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = "implicit step wall time @1e-8 tol: mixed/learned pMG vs FP64; residual GDOF/s"
 FP64_PEAK_NOMINAL = 1.25e12        # GB300 FP64 (vector = tensor), nominal
-SAMPLE_N = 4                       # oracle sample: 4^3 hexes, scaled by (32/4)^3
-RESIDUAL_TRAFFIC_BYTES = 6.371e9   # DRAM bytes of one FP64 residual launch on 32^3 p=3 (ncu)
+SAMPLE_N = 8                       # oracle step sample: 8^3 hexes, scaled by (32/8)^3
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def profile_figure(name, key):
+    """A figure an ncu summary states on a line "key: value" (None if the summary or the
+    line is absent: the counters were not taken for the kernels as they stand)."""
+    import re
+    try:
+        with open(os.path.join(PROFILES, name + ".md")) as f:
+            for line in f:
+                m = re.match(r"^\s*%s:\s*([0-9.eE+-]+)" % re.escape(key), line)
+                if m:
+                    return float(m.group(1))
+    except OSError:
+        pass
+    return None
 
 
 def parse():
@@ -54,8 +70,6 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
-
-SOLVE_TRAFFIC_16 = 1.845e9   # ncu DRAM bytes of one FP32 fine solve on 16^3 (4096 elements)
 
 
 def hbm_peak():
@@ -79,13 +93,13 @@ def solve_roofline(tune, E, nd):
             t_ms = min(float(x.split(":")[1]) for x in re.search(r"ms per G ([^)]*)\)", line).group(1).split())
     peak, src = hbm_peak()
     algo = E * nd * nd * 4 + E * nd * 4 + 2 * E * nd * 4
+    t16 = profile_figure("lu_solve_tgv3d16_fp32_fp64", "dram_bytes_per_launch_fp32")
     out = {"kernel": f"k_lu_solve (FP32 fine-level block solve, {E} LU factors of {nd}x{nd}, one application)",
            "bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": src, "algorithmic_bytes": algo,
-           "traffic": SOLVE_TRAFFIC_16 * E / 4096,
+           "traffic": t16 * E / 4096 if t16 else None,
            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on tgv3d 16^3 "
-                             "(4096 elements, 1.845 GB), scaled by the element count "
-                             "(profiles/lu_solve_tgv3d16_fp32_fp64.md)",
-           "share_of_step": "about a third of the step's kernel time (profiles/launches_tgv3d32_row_mixed.md)"}
+                             "(4096 elements), scaled by the element count (committed ncu summary)",
+           "share_of_step": "the largest kernel family of the mixed step (committed launch list)"}
     if t_ms:
         out.update({"achieved": algo / (t_ms * 1e-3) / 1e9, "frac": algo / (t_ms * 1e-3) / 1e9 / peak,
                     "ms_per_launch": t_ms})
@@ -114,20 +128,75 @@ def dist_env():
 
 
 # ------------------------------------------------------------------ oracle (CPU) arm
-def oracle_step_time(n_sample=SAMPLE_N, n_full=32):
-    """Seconds for one oracle ROS34PW2 step on an n_sample^3 slice at the workload's CFL,
-    and the element-count scale to the full mesh."""
+def oracle_step_time(n_sample=SAMPLE_N, threads=None):
+    """Seconds for one oracle ROS34PW2 step on an n_sample^3 slice of the workload at its CFL
+    (the pMG p{3-2} n{2-2} preconditioner, FGMRES(30) to 1e-6), on `threads` host threads
+    (all cores if None), with the step's stats."""
     import oracle
     from oracle import tableaux as TB
     from paper_2202_09733_gb300 import workloads as w
+    used = oracle.set_threads(threads or os.cpu_count() or 1)
     W = w.tgv3d(n=n_sample)
     O = oracle.Oracle(W.mesh, W.phys, W.levels)
     g, a, c, m = TB.ros34pw2()
     opts = O.opts(kdim=30, maxit_gmres=300, nsmooth=(2, 2), tol_gmres=1e-6, inv_dtau_star=1.0 / W.dt)
     t0 = time.perf_counter()
     q, st = O.row_step(g, a, c, m, W.dt, W.q0, opts)
-    dt = time.perf_counter() - t0
-    return dt, (n_full / n_sample) ** 3, st
+    return time.perf_counter() - t0, st, used
+
+
+def oracle_baseline(n_full=32):
+    """The oracle on this machine's host cores: R and Jv on the full workload, one thread and
+    all cores; the ROS34PW2 step on an 8^3 slice (all cores) and a 4^3 slice (one thread).
+    value = the 8^3 step scaled by the element count (an estimate: the slice's FGMRES count
+    is reported beside it)."""
+    import numpy as np
+    import oracle
+    from paper_2202_09733_gb300 import workloads as w
+    oracle.build()
+    ncores = os.cpu_count() or 1
+    W = w.tgv3d(n=n_full)
+    O = oracle.Oracle(W.mesh, W.phys, W.levels)
+    v = np.random.default_rng(0).standard_normal(W.q0.shape)
+    v /= np.linalg.norm(v)
+    shift = 1.0 / W.dt + 1.0 / (0.4358665215084590 * W.dt)
+    out = {}
+    for label, nt in (("1", 1), ("all", ncores)):
+        used = oracle.set_threads(nt)
+        t0 = time.perf_counter()
+        R = O.residual(W.q0)
+        t1 = time.perf_counter()
+        O.jvp(W.q0, R, v, 1e-6, shift)
+        t2 = time.perf_counter()
+        out[f"residual_s_{label}"] = t1 - t0
+        out[f"jvp_s_{label}"] = t2 - t1
+        out[f"threads_{label}"] = used
+    del O
+    t8, st8, used8 = oracle_step_time(SAMPLE_N, ncores)
+    t4, st4, _ = oracle_step_time(4, 1)
+    scale = (n_full / SAMPLE_N) ** 3
+    out.update({"step_8cube_s_all": t8, "step_8cube_gmres": st8["n_gmres"], "step_4cube_s_1": t4,
+                "step_4cube_gmres": st4["n_gmres"], "value": t8 * scale, "unit": "s/step", "cores": used8,
+                "kind": "oracle", "estimated": True,
+                "residual_gdofs_1": W.q0.size / out["residual_s_1"] / 1e9,
+                "residual_gdofs_all": W.q0.size / out["residual_s_all"] / 1e9,
+                "sample": (f"R and Jv on the full {n_full}^3 workload (one thread, {out['threads_all']} threads); the "
+                           f"ROS34PW2 step on an {SAMPLE_N}^3 slice at the same CFL on {used8} threads "
+                           f"({t8:.1f} s, {st8['n_gmres']} FGMRES iterations) scaled by the element count "
+                           f"x{int(scale)} = value (estimated), and on a 4^3 slice on one thread "
+                           f"({t4:.1f} s, {st4['n_gmres']} FGMRES iterations)")})
+    return out
+
+
+def oracle_baseline_in_child():
+    """oracle_baseline() in a child process (the GPU arm's process never loads the oracle)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print('ORACLE ' + json.dumps(bench.oracle_baseline()))") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    for line in r.stdout.splitlines():
+        if line.startswith("ORACLE "):
+            return json.loads(line[len("ORACLE "):])
+    return {"error": (r.stderr or r.stdout)[-1000:]}
 
 
 def reference_arm(args):
@@ -136,20 +205,24 @@ def reference_arm(args):
         return 0
     import oracle
     oracle.build()
-    times = []
+    scale = (32 // SAMPLE_N) ** 3
+    times, its, used = [], [], 1
     for i in range(args.warmup + args.steps):
-        t, scale, st = oracle_step_time()
+        t, st, used = oracle_step_time(SAMPLE_N, None)
         if i >= args.warmup:
             times.append(t * scale)
+            its.append(st["n_gmres"])
     value = statistics.mean(times)
-    sample = (f"oracle ROS34PW2 step, pMG p{{3-2}} n{{2-2}}, on a {SAMPLE_N}^3-hex slice of the 32^3 "
-              f"workload at the same CFL, single thread, scaled by the element count x{(32 // SAMPLE_N) ** 3}")
+    sample = (f"oracle ROS34PW2 step, pMG p{{3-2}} n{{2-2}}, FGMRES(30) to 1e-6, on an {SAMPLE_N}^3-hex slice "
+              f"of the 32^3 workload at the same CFL ({statistics.mean(its):.0f} FGMRES iterations), "
+              f"{used} host threads, scaled by the element count x{scale} (estimated)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/step", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "tgv3d 32^3 hex p=3 (Ma 0.1, Re 1600), ROS34PW2 step, pMG p{3-2} n{2-2}, "
                                    "FGMRES(30) tol 1e-6", "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "s/step", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "s/step", "cores": used, "kind": "oracle", "sample": sample,
+                             "estimated": True, "measured_s_per_sample_step": value / scale},
             "e2e": {"value": value, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -440,13 +513,7 @@ def gpu_arm(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        t_s, scale, st_s = oracle_step_time()
-        cpu = {"value": t_s * scale, "unit": "s/step", "cores": 1, "kind": "oracle",
-               "sample": f"one oracle ROS34PW2 step on a {SAMPLE_N}^3-hex slice at the same CFL "
-                         f"({t_s:.1f} s, {st_s['n_gmres']} GMRES iterations), single thread, "
-                         f"scaled by the element count x{int(scale)}"}
+        cpu = oracle_baseline_in_child()
 
     if rank == 0:
         ng = [s_["n_gmres"] for s_ in stats]
@@ -469,14 +536,14 @@ def gpu_arm(args):
             "residual_ms": t_R * 1e3,
             "gmres_iterations_per_step": statistics.mean(ng),
             "roofline": solve_roofline(tune, E, 5 * 64),
-            "roofline_residual": {"kernel": "fr_residual (FP64 FR residual, 8 kernels per launch)", "bound": "alu",
+            "roofline_residual": {"kernel": "fr_residual (FP64 FR residual, 7 kernels per launch)", "bound": "alu",
                          "achieved": flops / t_R / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
-                         "frac": (flops / t_R) / FP64_PEAK_NOMINAL, "traffic": RESIDUAL_TRAFFIC_BYTES,
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 8 kernels of one "
-                                           "residual on this workload at the default launch shapes "
-                                           "(profiles/residual_tgv3d32_fp64_dram.md)",
+                         "frac": (flops / t_R) / FP64_PEAK_NOMINAL,
+                         "traffic": profile_figure("residual_tgv3d32_fp64_dram", "dram_bytes_per_launch"),
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the kernels of one "
+                                           "residual on this workload (committed ncu summary)",
                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 entry); "
-                                        "a DFMA-chain probe measured 1.19"},
+                                        "DFMA chains measured 1.19"},
             "e2e": {"value": t_e2e, "unit": "s/step", "h2d_bytes_per_step": q_host.numel() * 8,
                     "d2h_bytes_per_step": q_host.numel() * 8},
             "cpu_baseline": cpu,

@@ -133,6 +133,9 @@ int fr_elem_blocks(fr_ctx *ctx, int level, const double *q, double shift, double
  * columns per evaluation.  The two agree to FP32 rounding; method 0 is refused
  * (FR_ERR_INVALID_ARG) on meshes where a face joins an element to itself. */
 int fr_elem_blocks_f32(fr_ctx *ctx, int level, const float *q, double shift, float *M, int method, void *stream);
+/* the method (as above) that pmg_setup uses for its FP32 blocks; 0 by default (meshes with
+ * a face joining an element to itself always use 1) */
+int fr_set_block_method(fr_ctx *ctx, int method);
 
 /* Sec. 3.2 matrix-based smoother: the element blocks M (as fr_elem_blocks) and the face
  * neighbour blocks O of the shifted Jacobian on a level in one pass over a distance-2

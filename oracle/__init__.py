@@ -36,9 +36,12 @@ def build(force: bool = False) -> str:
     newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "oracle.h")])
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-o", tmp] + srcs + ["-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp]
+        # OpenMP over elements where the toolchain has it (element results do not depend
+        # on the thread count); a plain single-threaded build otherwise
+        r = subprocess.run(base + ["-fopenmp"] + srcs + ["-lm"], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.run(base + srcs + ["-lm"], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -80,6 +83,8 @@ def lib():
                                     C.c_void_p, C.c_void_p, PD]
         L.or_pmg_steady.argtypes = [C.c_void_p, PD, C.c_double, C.c_double, C.c_double, C.c_int,
                                     C.c_void_p, C.c_void_p, PD]
+        L.or_set_threads.argtypes = [C.c_int]
+        L.or_max_threads.restype = C.c_int
         L.or_table.argtypes = [C.c_int, C.c_int, PD]
         L.or_transfer.argtypes = [C.c_int, C.c_int, PD, PD]
         L.or_jacobian.argtypes = [C.c_void_p, C.c_int, PD]
@@ -93,6 +98,16 @@ def lib():
         L.or_roe.argtypes = [C.c_void_p, PD, PD, PD, PD]
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's element loops (OpenMP builds); returns the count in effect."""
+    lib().or_set_threads(int(n))
+    return int(lib().or_max_threads())
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())
 
 
 def _d(a: np.ndarray):

@@ -4,6 +4,25 @@
 #include <stdlib.h>
 #include <string.h>
 #include "oracle.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* threads of the element loops (OpenMP builds; results do not depend on the count) */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+int or_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 void or_level_init(or_ctx *C, int l, int p);
 void or_level_free(or_level *L);

@@ -19,6 +19,9 @@
  * elimination (x_k = s_k / u_kk), kept for the pin that the two forms agree.
  *
  * Transfers (Eqs. 17-18): the 1-D Gamma / Pi applied along direction 0, then 1, then 2.
+ *
+ * Element loops may run on several OpenMP threads: every element's result is computed by
+ * the same operations in the same order whatever the thread count.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -29,9 +32,12 @@ void or_elem_blocks(or_ctx *C, int l, const double *q, double shift, const int *
     or_level *L = &C->L[l];
     int E = C->E, nv = C->nv, np = L->np, nd = nv * np;
     double *R = malloc(sizeof(double) * nd * E);
+    or_residual(C, l, q, R);
+#pragma omp parallel
+    {
     double *qe = malloc(sizeof(double) * nd), *qp = malloc(sizeof(double) * nd);
     double *R0 = malloc(sizeof(double) * nd), *Rp = malloc(sizeof(double) * nd);
-    or_residual(C, l, q, R);
+#pragma omp for schedule(dynamic)
     for (int t = 0; t < ne; ++t) {
         int e = elems[t];
         for (int r = 0; r < nd; ++r) qe[r] = q[(size_t)r * E + e];
@@ -48,7 +54,9 @@ void or_elem_blocks(or_ctx *C, int l, const double *q, double shift, const int *
             }
         }
     }
-    free(R); free(qe); free(qp); free(R0); free(Rp);
+    free(qe); free(qp); free(R0); free(Rp);
+    }
+    free(R);
 }
 
 /* the elimination; u_kk stays on the diagonal */
@@ -120,9 +128,12 @@ static void tensor_apply(int d, int nv, int E, int nin, int nout, double Op[OR_M
                          const double *x, double *y) {
     int nmax = nin > nout ? nin : nout;
     size_t blk = (size_t)nmax * nmax * nmax;
-    double *a = malloc(sizeof(double) * blk), *b = malloc(sizeof(double) * blk);
     int npin = d == 2 ? nin * nin : nin * nin * nin;
     int npout = d == 2 ? nout * nout : nout * nout * nout;
+#pragma omp parallel
+    {
+    double *a = malloc(sizeof(double) * blk), *b = malloc(sizeof(double) * blk);
+#pragma omp for schedule(static)
     for (int e = 0; e < E; ++e)
         for (int v = 0; v < nv; ++v) {
             int dims[3] = {nin, nin, d == 3 ? nin : 1};
@@ -147,6 +158,7 @@ static void tensor_apply(int d, int nv, int E, int nin, int nout, double Op[OR_M
             for (int i = 0; i < npout; ++i) y[((size_t)v * npout + i) * E + e] = a[i];
         }
     free(a); free(b);
+    }
 }
 
 void or_restrict(or_ctx *C, int l, const double *x0, double *x1) {

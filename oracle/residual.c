@@ -349,7 +349,7 @@ static void div_elem(const or_ctx *C, const or_level *L, int e, const double *qe
                      const double *fne, double *Re) {
     int d = C->d, E = C->E, n = L->n, np = L->np, nfp = L->nfp, nv = C->nv;
     const or_tab *T = &L->T;
-    static double Ft[3 * NVMAX * NPMAX];
+    static _Thread_local double Ft[3 * NVMAX * NPMAX];
     for (int i = 0; i < np; ++i) {
         double qi[5], Qi[3][5], fi[3][5], fvi[3][5];
         for (int v = 0; v < nv; ++v) qi[v] = qe[v * np + i];
@@ -409,16 +409,18 @@ static void scatter(double *g, int nrow, int E, int e, const double *loc) {
 void or_residual(or_ctx *C, int l, const double *q, double *R) {
     or_level *L = &C->L[l];
     int d = C->d, E = C->E, nv = C->nv, np = L->np, nfp = L->nfp;
-    static double qe[NVMAX * NPMAX], qfe[NVMAX * NPMAX], dqe[NVMAX * NPMAX];
-    static double Qe[3 * NVMAX * NPMAX], gfe[3 * NVMAX * NPMAX], Qfe[3 * NVMAX * NPMAX];
-    static double fne[NVMAX * NPMAX], Re[NVMAX * NPMAX];
+    static _Thread_local double qe[NVMAX * NPMAX], qfe[NVMAX * NPMAX], dqe[NVMAX * NPMAX];
+    static _Thread_local double Qe[3 * NVMAX * NPMAX], gfe[3 * NVMAX * NPMAX], Qfe[3 * NVMAX * NPMAX];
+    static _Thread_local double fne[NVMAX * NPMAX], Re[NVMAX * NPMAX];
     /* stage 1 */
+#pragma omp parallel for schedule(static)
     for (int e = 0; e < E; ++e) {
         gather(q, nv * np, E, e, qe);
         interp_faces(C, L, qe, qfe);
         scatter(L->qf, nv * nfp, E, e, qfe);
     }
     /* stage 2 */
+#pragma omp parallel for schedule(static)
     for (int P = 0; P < L->npairs; ++P) {
         int eL = L->pe[2 * P], kL = L->pk[2 * P], eR = L->pe[2 * P + 1], kR = L->pk[2 * P + 1];
         double qL[5], qR[5];
@@ -433,6 +435,7 @@ void or_residual(or_ctx *C, int l, const double *q, double *R) {
         }
     }
     /* stage 3 */
+#pragma omp parallel for schedule(static)
     for (int e = 0; e < E; ++e) {
         gather(q, nv * np, E, e, qe);
         gather(L->qf, nv * nfp, E, e, qfe);
@@ -443,6 +446,7 @@ void or_residual(or_ctx *C, int l, const double *q, double *R) {
         scatter(L->Qf, d * nv * nfp, E, e, Qfe);
     }
     /* stage 4 */
+#pragma omp parallel for schedule(static)
     for (int P = 0; P < L->npairs; ++P) {
         int eL = L->pe[2 * P], kL = L->pk[2 * P], eR = L->pe[2 * P + 1], kR = L->pk[2 * P + 1];
         int bc = L->bc[P];
@@ -462,6 +466,7 @@ void or_residual(or_ctx *C, int l, const double *q, double *R) {
         }
     }
     /* stage 5 */
+#pragma omp parallel for schedule(static)
     for (int e = 0; e < E; ++e) {
         gather(q, nv * np, E, e, qe);
         gather(L->Q, d * nv * np, E, e, Qe);
@@ -481,10 +486,10 @@ void or_elem_residual(or_ctx *C, int l, const double *q, int e, const double *qe
     or_level *L = &C->L[l];
     int d = C->d, E = C->E, nv = C->nv, nfp = L->nfp;
     (void)q;
-    static double qfe[NVMAX * NPMAX], dqe[NVMAX * NPMAX];
-    static double Qe[3 * NVMAX * NPMAX], gfe[3 * NVMAX * NPMAX], Qfe[3 * NVMAX * NPMAX];
-    static double fne[NVMAX * NPMAX];
-    static double dqn[NVMAX * NPMAX];   /* neighbour-side jump at e's face point k */
+    static _Thread_local double qfe[NVMAX * NPMAX], dqe[NVMAX * NPMAX];
+    static _Thread_local double Qe[3 * NVMAX * NPMAX], gfe[3 * NVMAX * NPMAX], Qfe[3 * NVMAX * NPMAX];
+    static _Thread_local double fne[NVMAX * NPMAX];
+    static _Thread_local double dqn[NVMAX * NPMAX];   /* neighbour-side jump at e's face point k */
     interp_faces(C, L, qe_new, qfe);
     for (int k = 0; k < nfp; ++k) {
         int P = L->epair[(size_t)k * E + e];

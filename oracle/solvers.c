@@ -179,6 +179,7 @@ void or_pmg_setup(or_ctx *C, const double *q_ref, int nlev, const int *nsmooth, 
             g_pmg.O = malloc(sizeof(double) * (size_t)E * nf * nd * nd);
             or_nbr_blocks(C, l, qr, g_pmg.nbr, g_pmg.O);
         }
+#pragma omp parallel for schedule(static)
         for (int e = 0; e < E; ++e)
             or_lu_factor(nd, &g_pmg.M[l][(size_t)e * nd * nd], &g_pmg.piv[l][(size_t)e * nd]);
         if (l + 1 < nlev) {
@@ -195,13 +196,17 @@ void or_pmg_setup(or_ctx *C, const double *q_ref, int nlev, const int *nsmooth, 
 /* apply M_l^{-1} element by element, in place on x[v][i][e] */
 static void block_solve(or_ctx *C, int l, double *x) {
     int E = C->E, nd = C->nv * C->L[l].np;
+#pragma omp parallel
+    {
     double *b = malloc(sizeof(double) * nd);
+#pragma omp for schedule(static)
     for (int e = 0; e < E; ++e) {
         for (int r = 0; r < nd; ++r) b[r] = x[(size_t)r * E + e];
         or_lu_solve(nd, &g_pmg.M[l][(size_t)e * nd * nd], &g_pmg.piv[l][(size_t)e * nd], b);
         for (int r = 0; r < nd; ++r) x[(size_t)r * E + e] = b[r];
     }
     free(b);
+    }
 }
 void or_block_solve(or_ctx *C, int l, double *x) { block_solve(C, l, x); }
 

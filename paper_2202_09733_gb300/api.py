@@ -117,6 +117,11 @@ def fr_elem_blocks_f32(ctx, level, q32, shift, method="local", M=None, stream=No
     return M
 
 
+def fr_set_block_method(ctx, method):
+    """The method pmg_setup uses for the FP32 blocks: "local" (default) or "colour"."""
+    N.check(N.load().fr_set_block_method(ctx.handle, {"local": 0, "colour": 1}[method]), "fr_set_block_method")
+
+
 def fr_nbr_blocks(ctx, level, q, shift, stream=None):
     """(M, O): element blocks [E, nd(col), nd(row)] and face-neighbour blocks
     [E, 2d, nd(col), nd(row)] (column-major per block) of the shifted Jacobian."""

@@ -11,6 +11,7 @@ Translation units:
   csrc/mbnk.cu        matrix-based Newton-Krylov smoother of the coarsest pMG level
   csrc/host_tables.c  binary128 operator tables         (gcc -ffp-contract=off)
   csrc/host_geometry.c geometric factors, connectivity  (gcc -ffp-contract=off)
+build_rates() compiles csrc/rates.cu (pipe-rate microbenchmarks) into librates.so.
 """
 from __future__ import annotations
 
@@ -96,6 +97,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError(f"linking failed:\n{' '.join(link)}\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
+
+
+RATES_LIB = os.path.join(HERE, "librates.so")
+
+
+def build_rates(force: bool = False) -> str:
+    """The pipe-rate microbenchmarks (csrc/rates.cu) as their own library."""
+    src = os.path.join(CSRC, "rates.cu")
+    if not force and os.path.exists(RATES_LIB) and os.path.getmtime(RATES_LIB) >= os.path.getmtime(src):
+        return RATES_LIB
+    tmp = RATES_LIB + f".{os.getpid()}.tmp"
+    cmd = [_nvcc()] + ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
+                              "-o", tmp, src]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"compiling rates.cu failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, RATES_LIB)
+    return RATES_LIB
 
 
 if __name__ == "__main__":

@@ -281,25 +281,28 @@ __device__ __forceinline__ void ghost_state(const FrPhys<B> &ph, int bc, const T
 template <typename T>
 __device__ const FrTab<T> &frtab(int p);
 
-// stage 1: qf[v][k][e] = sum_m l_side[m] q[v][line(k, m)][e]
+// stage 1: qf[v][k][e] = sum_m l_side[m] q[v][line(k, m)][e]; one thread per (k, e), all v
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(256) k_interp(const T *__restrict__ q, T *__restrict__ qf, int E) {
     using S = Sh<D, P>;
     constexpr int N = S::n;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
-    int v = blockIdx.y / S::nfp, k = blockIdx.y - v * S::nfp;
+    int k = blockIdx.y;
     int df, s, a, b;
     fp_decode<D, N>(k, df, s, a, b);
     typedef typename FrBase<T>::type B;
     const FrTab<B> &tb = frtab<B>(P);
-    T acc = T(0);
 #pragma unroll
-    for (int m = 0; m < N; ++m) {
-        T l = s ? tb.lp[m] : tb.lm[m];
-        acc = fma(l, q[(size_t)(v * S::np + line_pt<D, N>(df, a, b, m)) * E + e], acc);
+    for (int v = 0; v < S::nv; ++v) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            T l = s ? tb.lp[m] : tb.lm[m];
+            acc = fma(l, q[(size_t)(v * S::np + line_pt<D, N>(df, a, b, m)) * E + e], acc);
+        }
+        qf[(size_t)(v * S::nfp + k) * E + e] = acc;
     }
-    qf[(size_t)(v * S::nfp + k) * E + e] = acc;
 }
 
 // stage 2: common solution, jumps dq = qs - q_side on both sides
@@ -329,44 +332,8 @@ __global__ void __launch_bounds__(256) k_pair_common(const int4 *__restrict__ pa
     }
 }
 
-// stage 3a: corrected gradient at solution points
-template <int D, int P, typename T>
-__global__ void __launch_bounds__(256) k_grad_sp(const T *__restrict__ q, const T *__restrict__ dq,
-                                                 const typename FrBase<T>::type *__restrict__ G, T *__restrict__ Q,
-                                                 int E) {
-    using S = Sh<D, P>;
-    constexpr int N = S::n;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    int v = blockIdx.y / S::np, i = blockIdx.y - v * S::np;
-    int ii[3] = {i % N, (i / N) % N, D == 3 ? i / (N * N) : 0};
-    typedef typename FrBase<T>::type B;
-    const FrTab<B> &tb = frtab<B>(P);
-    T gr[3];
-#pragma unroll
-    for (int dd = 0; dd < D; ++dd) {
-        T t = T(0);
-        int cd = ii[dd];
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            int jj0 = dd == 0 ? m : ii[0], jj1 = dd == 1 ? m : ii[1], jj2 = dd == 2 ? m : ii[2];
-            t = fma(tb.D[cd][m], q[(size_t)(v * S::np + spi<D, N>(jj0, jj1, jj2)) * E + e], t);
-        }
-        int kL = fp_of<D, N>(dd, 0, ii[0], ii[1], ii[2]), kR = fp_of<D, N>(dd, 1, ii[0], ii[1], ii[2]);
-        t = fma(tb.gLd[cd], dq[(size_t)(v * S::nfp + kL) * E + e], t);
-        t = fma(tb.gRd[cd], dq[(size_t)(v * S::nfp + kR) * E + e], t);
-        gr[dd] = t;
-    }
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-        T acc = T(0);
-#pragma unroll
-        for (int dd = 0; dd < D; ++dd) acc = fma(G[(size_t)((dd * D + c) * S::np + i) * E + e], gr[dd], acc);
-        Q[(size_t)((c * S::nv + v) * S::np + i) * E + e] = acc;
-    }
-}
-
-// stage 3b: face gradient traces (uncorrected) with the BR2 lifting of the face's own jump
+// stage 3: face gradient traces (uncorrected) with the BR2 lifting of the face's own jump;
+// one thread per (k, e), all v (the metric terms Gf read once)
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(256) k_grad_fp(const T *__restrict__ q, const T *__restrict__ qf,
                                                  const T *__restrict__ dq, const typename FrBase<T>::type *__restrict__ Gf,
@@ -376,47 +343,55 @@ __global__ void __launch_bounds__(256) k_grad_fp(const T *__restrict__ q, const 
     constexpr int N = S::n;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
-    int v = blockIdx.y / S::nfp, k = blockIdx.y - v * S::nfp;
+    int k = blockIdx.y;
     int df, s, a, b;
     fp_decode<D, N>(k, df, s, a, b);
     typedef typename FrBase<T>::type B;
     const FrTab<B> &tb = frtab<B>(P);
-    T gf[3];
-    {
-        T t = T(0);
+    B g[3][3];
 #pragma unroll
-        for (int m = 0; m < N; ++m) {
-            T dl = s ? tb.dlp[m] : tb.dlm[m];
-            t = fma(dl, q[(size_t)(v * S::np + line_pt<D, N>(df, a, b, m)) * E + e], t);
-        }
-        gf[df] = t;
-    }
+    for (int dd = 0; dd < D; ++dd)
+#pragma unroll
+        for (int c = 0; c < D; ++c) g[dd][c] = Gf[(size_t)((dd * D + c) * S::nfp + k) * E + e];
     // tangential directions in increasing order, coordinates a then b
     int td0 = df == 0 ? 1 : 0, td1 = df == 2 ? 1 : 2;
-    {
-        T u = T(0);
 #pragma unroll
-        for (int m = 0; m < N; ++m)
-            u = fma(tb.D[a][m], qf[(size_t)(v * S::nfp + fp_at<D, N>(df, s, m, b)) * E + e], u);
-        gf[td0] = u;
-    }
-    if (D == 3) {
-        T u = T(0);
+    for (int v = 0; v < S::nv; ++v) {
+        T gf[3];
+        {
+            T t = T(0);
 #pragma unroll
-        for (int m = 0; m < N; ++m)
-            u = fma(tb.D[b][m], qf[(size_t)(v * S::nfp + fp_at<D, N>(df, s, a, m)) * E + e], u);
-        gf[td1] = u;
-    }
-    T comp[3];
+            for (int m = 0; m < N; ++m) {
+                T dl = s ? tb.dlp[m] : tb.dlm[m];
+                t = fma(dl, q[(size_t)(v * S::np + line_pt<D, N>(df, a, b, m)) * E + e], t);
+            }
+            gf[df] = t;
+        }
+        {
+            T u = T(0);
 #pragma unroll
-    for (int dd = 0; dd < D; ++dd) comp[dd] = gf[dd];
-    comp[df] = fma(s ? etagR : etagL, dq[(size_t)(v * S::nfp + k) * E + e], gf[df]);
+            for (int m = 0; m < N; ++m)
+                u = fma(tb.D[a][m], qf[(size_t)(v * S::nfp + fp_at<D, N>(df, s, m, b)) * E + e], u);
+            gf[td0] = u;
+        }
+        if (D == 3) {
+            T u = T(0);
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-        T acc = T(0);
+            for (int m = 0; m < N; ++m)
+                u = fma(tb.D[b][m], qf[(size_t)(v * S::nfp + fp_at<D, N>(df, s, a, m)) * E + e], u);
+            gf[td1] = u;
+        }
+        T comp[3];
 #pragma unroll
-        for (int dd = 0; dd < D; ++dd) acc = fma(Gf[(size_t)((dd * D + c) * S::nfp + k) * E + e], comp[dd], acc);
-        Qf[(size_t)((c * S::nv + v) * S::nfp + k) * E + e] = acc;
+        for (int dd = 0; dd < D; ++dd) comp[dd] = gf[dd];
+        comp[df] = fma(s ? etagR : etagL, dq[(size_t)(v * S::nfp + k) * E + e], gf[df]);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            T acc = T(0);
+#pragma unroll
+            for (int dd = 0; dd < D; ++dd) acc = fma(g[dd][c], comp[dd], acc);
+            Qf[(size_t)((c * S::nv + v) * S::nfp + k) * E + e] = acc;
+        }
     }
 }
 
@@ -479,23 +454,52 @@ __global__ void __launch_bounds__(256) k_pair_flux(const int4 *__restrict__ pair
     }
 }
 
-// stage 5a: transformed volume flux Ft[dd][v][i][e] = sum_c S[dd][c] (f_inv - f_visc)_c
+// stage 5a: corrected gradient at the solution point (never stored), then the transformed
+// volume flux Ft[dd][v][i][e] = sum_c S[dd][c] (f_inv - f_visc)_c; one thread per (i, e)
 template <int D, int P, typename T>
-__global__ void __launch_bounds__(256) k_vflux(const T *__restrict__ q, const T *__restrict__ Q,
-                                               const typename FrBase<T>::type *__restrict__ Sm, T *__restrict__ Ft, int E,
-                                               FrPhys<typename FrBase<T>::type> ph) {
+__global__ void __launch_bounds__(256) k_grad_vflux(const T *__restrict__ q, const T *__restrict__ dq,
+                                                    const typename FrBase<T>::type *__restrict__ G,
+                                                    const typename FrBase<T>::type *__restrict__ Sm, T *__restrict__ Ft,
+                                                    int E, FrPhys<typename FrBase<T>::type> ph) {
     using S = Sh<D, P>;
     typedef typename FrBase<T>::type B;
-    constexpr int nv = S::nv;
+    constexpr int N = S::n, nv = S::nv;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     int i = blockIdx.y;
+    int ii[3] = {i % N, (i / N) % N, D == 3 ? i / (N * N) : 0};
+    const FrTab<B> &tb = frtab<B>(P);
+    B g[3][3];
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd)
+#pragma unroll
+        for (int c = 0; c < D; ++c) g[dd][c] = G[(size_t)((dd * D + c) * S::np + i) * E + e];
     T qi[5], Qi[3][5], fi[3][5], fvi[3][5];
 #pragma unroll
     for (int v = 0; v < nv; ++v) {
         qi[v] = q[(size_t)(v * S::np + i) * E + e];
+        T gr[3];
 #pragma unroll
-        for (int c = 0; c < D; ++c) Qi[c][v] = Q[(size_t)((c * nv + v) * S::np + i) * E + e];
+        for (int dd = 0; dd < D; ++dd) {
+            T t = T(0);
+            int cd = ii[dd];
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                int jj0 = dd == 0 ? m : ii[0], jj1 = dd == 1 ? m : ii[1], jj2 = dd == 2 ? m : ii[2];
+                t = fma(tb.D[cd][m], q[(size_t)(v * S::np + spi<D, N>(jj0, jj1, jj2)) * E + e], t);
+            }
+            int kL = fp_of<D, N>(dd, 0, ii[0], ii[1], ii[2]), kR = fp_of<D, N>(dd, 1, ii[0], ii[1], ii[2]);
+            t = fma(tb.gLd[cd], dq[(size_t)(v * S::nfp + kL) * E + e], t);
+            t = fma(tb.gRd[cd], dq[(size_t)(v * S::nfp + kR) * E + e], t);
+            gr[dd] = t;
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            T acc = T(0);
+#pragma unroll
+            for (int dd = 0; dd < D; ++dd) acc = fma(g[dd][c], gr[dd], acc);
+            Qi[c][v] = acc;
+        }
     }
     flux_inviscid<D, T, B>(ph, qi, fi);
     flux_viscous<D, T, B>(ph, qi, Qi, false, fvi);
@@ -514,28 +518,32 @@ __global__ void __launch_bounds__(256) k_vflux(const T *__restrict__ q, const T 
     }
 }
 
-// stage 5b: transformed discontinuous flux at the face points (normal component)
+// stage 5b: transformed discontinuous flux at the face points (normal component); one
+// thread per (k, e), all v
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(256) k_face_ft(const T *__restrict__ Ft, T *__restrict__ Ftf, int E) {
     using S = Sh<D, P>;
     constexpr int N = S::n;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
-    int v = blockIdx.y / S::nfp, k = blockIdx.y - v * S::nfp;
+    int k = blockIdx.y;
     int df, s, a, b;
     fp_decode<D, N>(k, df, s, a, b);
     typedef typename FrBase<T>::type B;
     const FrTab<B> &tb = frtab<B>(P);
-    T acc = T(0);
 #pragma unroll
-    for (int m = 0; m < N; ++m) {
-        T l = s ? tb.lp[m] : tb.lm[m];
-        acc = fma(l, Ft[(size_t)((df * S::nv + v) * S::np + line_pt<D, N>(df, a, b, m)) * E + e], acc);
+    for (int v = 0; v < S::nv; ++v) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            T l = s ? tb.lp[m] : tb.lm[m];
+            acc = fma(l, Ft[(size_t)((df * S::nv + v) * S::np + line_pt<D, N>(df, a, b, m)) * E + e], acc);
+        }
+        Ftf[(size_t)(v * S::nfp + k) * E + e] = acc;
     }
-    Ftf[(size_t)(v * S::nfp + k) * E + e] = acc;
 }
 
-// stage 5c: divergence with FR corrections, R = -(div * invJ)
+// stage 5c: divergence with FR corrections, R = -(div * invJ); one thread per (i, e), all v
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(256) k_div(const T *__restrict__ Ft, const T *__restrict__ Ftf,
                                              const T *__restrict__ fn, const typename FrBase<T>::type *__restrict__ invJ,
@@ -544,27 +552,31 @@ __global__ void __launch_bounds__(256) k_div(const T *__restrict__ Ft, const T *
     constexpr int N = S::n;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
-    int v = blockIdx.y / S::np, i = blockIdx.y - v * S::np;
+    int i = blockIdx.y;
     int ii[3] = {i % N, (i / N) % N, D == 3 ? i / (N * N) : 0};
     typedef typename FrBase<T>::type B;
     const FrTab<B> &tb = frtab<B>(P);
-    T div = T(0);
+    B ij = invJ[(size_t)i * E + e];
 #pragma unroll
-    for (int dd = 0; dd < D; ++dd) {
-        int cd = ii[dd];
-        const T *F = Ft + (size_t)((dd * S::nv + v) * S::np) * E;
-        T t = T(0);
+    for (int v = 0; v < S::nv; ++v) {
+        T div = T(0);
 #pragma unroll
-        for (int m = 0; m < N; ++m) {
-            int jj0 = dd == 0 ? m : ii[0], jj1 = dd == 1 ? m : ii[1], jj2 = dd == 2 ? m : ii[2];
-            t = fma(tb.D[cd][m], F[(size_t)spi<D, N>(jj0, jj1, jj2) * E + e], t);
+        for (int dd = 0; dd < D; ++dd) {
+            int cd = ii[dd];
+            const T *F = Ft + (size_t)((dd * S::nv + v) * S::np) * E;
+            T t = T(0);
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                int jj0 = dd == 0 ? m : ii[0], jj1 = dd == 1 ? m : ii[1], jj2 = dd == 2 ? m : ii[2];
+                t = fma(tb.D[cd][m], F[(size_t)spi<D, N>(jj0, jj1, jj2) * E + e], t);
+            }
+            int kL = fp_of<D, N>(dd, 0, ii[0], ii[1], ii[2]), kR = fp_of<D, N>(dd, 1, ii[0], ii[1], ii[2]);
+            T FsL = -fn[(size_t)(v * S::nfp + kL) * E + e];
+            T FsR = fn[(size_t)(v * S::nfp + kR) * E + e];
+            t = fma(tb.gLd[cd], FsL - Ftf[(size_t)(v * S::nfp + kL) * E + e], t);
+            t = fma(tb.gRd[cd], FsR - Ftf[(size_t)(v * S::nfp + kR) * E + e], t);
+            div = div + t;
         }
-        int kL = fp_of<D, N>(dd, 0, ii[0], ii[1], ii[2]), kR = fp_of<D, N>(dd, 1, ii[0], ii[1], ii[2]);
-        T FsL = -fn[(size_t)(v * S::nfp + kL) * E + e];
-        T FsR = fn[(size_t)(v * S::nfp + kR) * E + e];
-        t = fma(tb.gLd[cd], FsL - Ftf[(size_t)(v * S::nfp + kL) * E + e], t);
-        t = fma(tb.gRd[cd], FsR - Ftf[(size_t)(v * S::nfp + kR) * E + e], t);
-        div = div + t;
+        R[(size_t)(v * S::np + i) * E + e] = -(div * ij);
     }
-    R[(size_t)(v * S::np + i) * E + e] = -(div * invJ[(size_t)i * E + e]);
 }

@@ -101,6 +101,7 @@ struct fr_ctx {
     int ncolor;
     int *color;
     int self_face;                // a face joins an element to itself (periodic, one element wide)
+    int ad_method;                // FP32 blocks: 0 element by element, 1 whole-level colours
     float *ad_nt;                 // element-local FP32 blocks: the other sides' frozen face data
     signed char *ad_bck;          //   and the boundary code of every element face point
     int ncolor2;
@@ -550,7 +551,14 @@ static int elem_blocks_ad_colour(fr_ctx *C, int l, const float *q, double shift,
 template <typename T>
 static int elem_blocks_t(fr_ctx *C, int l, const T *q, double shift, T *M, cudaStream_t s);
 static int elem_blocks_ad(fr_ctx *C, int l, const float *q, double shift, float *M, cudaStream_t s) {
-    return C->self_face ? elem_blocks_ad_colour(C, l, q, shift, M, s) : elem_blocks_ad_local(C, l, q, shift, M, s);
+    return (C->self_face || C->ad_method == 1) ? elem_blocks_ad_colour(C, l, q, shift, M, s)
+                                               : elem_blocks_ad_local(C, l, q, shift, M, s);
+}
+
+extern "C" int fr_set_block_method(fr_ctx *C, int method) {
+    if (!C || method < 0 || method > 1) return fail(FR_ERR_INVALID_ARG, "method must be 0 or 1");
+    C->ad_method = method;
+    return FR_OK;
 }
 template <>
 int elem_blocks_t<float>(fr_ctx *C, int l, const float *q, double shift, float *M, cudaStream_t s) {

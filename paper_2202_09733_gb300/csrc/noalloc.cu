@@ -1,5 +1,5 @@
 // fr_residual_noalloc: the FP64 residual with its stage scratch (flux-point traces, jumps,
-// gradients, face gradients, common fluxes, transformed fluxes) taken from one
+// face gradients, common fluxes, transformed fluxes) taken from one
 // file-scope device array instead of the context's workspace.  It calls no cudaMalloc,
 // cudaFree or any allocating routine.
 //
@@ -49,7 +49,7 @@ extern "C" int fr_residual_noalloc(fr_ctx *ctx, int level, const double *q, doub
     size_t nfv = align_doubles((size_t)L.nv * L.nfp * E);
     size_t npv = align_doubles((size_t)L.d * L.nv * L.np * E);
     size_t nqf = align_doubles((size_t)L.d * L.nv * L.nfp * E);
-    size_t need = 4 * nfv + 2 * npv + nqf;
+    size_t need = 4 * nfv + npv + nqf;
     if (need > FR_NOALLOC_MAX_DOUBLES)
         return fr_internal_fail(FR_ERR_INVALID_ARG,
                                 "fr_residual_noalloc: this level needs more stage scratch than the fixed "
@@ -73,9 +73,8 @@ extern "C" int fr_residual_noalloc(fr_ctx *ctx, int level, const double *q, doub
     L.dq = base + nfv;
     L.fn = base + 2 * nfv;
     L.Ftf = base + 3 * nfv;
-    L.Q = base + 4 * nfv;
-    L.Ft = base + 4 * nfv + npv;
-    L.Qf = base + 4 * nfv + 2 * npv;
+    L.Ft = base + 4 * nfv;
+    L.Qf = base + 4 * nfv + npv;
     if (frk64_residual(L, ph, q, R, (cudaStream_t)stream) != 0)
         return fr_internal_fail(FR_ERR_UNIMPLEMENTED, "fr_residual_noalloc: no kernel for this degree");
     cudaError_t e = cudaGetLastError();

@@ -259,11 +259,14 @@ def test_row_step_converged_state_at_larger_fd_step(eps):
 
 # ----------------------------------------------------------------- mixed precision
 # The mixed preconditioner (FP32 cycle, FP32 FD blocks and LU) against the FP64 oracle.
-# Same input scaling on both sides (the library scales X so that ||Y||_inf ~ 1e-3
-# ||q||_inf, i.e. s = 1e-3 ||q||_inf (c + 1/dtau*) / ||X||_inf); the difference is then the
-# FP32 arithmetic: FD truncation of the FP32 blocks (step 3e-4 max(1,|q|), relative error
-# ~3e-4), FP32 rounding of R amplified by 1/1e-3 (~6e-5), through n{2-2} smoothing
-# steps: tolerance 5e-3 on the max-norm relative error.
+# Same input scaling on both sides; the difference is then the FP32 arithmetic: rounding of
+# R(qh) - R(q) at the input scale 1e-2 (about 2.5e-3 through n{2-2} smoothing steps) and the
+# FP32 factor and solve of each element block, whose forward error grows with the block's
+# condition number.  Well-conditioned blocks (periodic boxes, kappa <= 2e2): 5e-3.  The
+# stretched O-mesh's wall blocks reach kappa ~ 5e6 (p = 3) and 5e5 (p = 4) in the
+# conservative variables, where an FP32 LU is only bounded by kappa n u ~ 0.1-1 relative;
+# two FP32 block assemblies that agree to 1e-6 (element-local and whole-level, see
+# test_gpu_ad_blocks) give 2.6e-3 and 6.4e-3 there: 1.5e-2.
 def test_pmg_precondition_mixed_vs_fp64_oracle(case):
     O, G, q = case["O"], case["G"], case["q"]
     if case["mesh"]["E"] > 128:
@@ -294,7 +297,8 @@ def test_pmg_precondition_mixed_vs_fp64_oracle(case):
     Y_or = Y_or / s
     api.pmg_setup(G, dev(q), nsm, c, 1.0 / dt, precision="mixed")
     Y_gpu = api.pmg_precondition(G, dev(q), dev(Rq), dev(X))
-    assert relerr(Y_gpu, Y_or) <= 5e-3
+    tol = 1.5e-2 if case["name"].startswith("omesh") else 5e-3
+    assert relerr(Y_gpu, Y_or) <= tol
 
 
 def test_esdirk_step_mixed_converged_state():
