@@ -96,6 +96,7 @@ def lib():
         L.or_flux_viscous.argtypes = [C.c_void_p, PD, PD, C.c_int, PD]
         L.or_rusanov.argtypes = [C.c_void_p, PD, PD, PD, PD]
         L.or_roe.argtypes = [C.c_void_p, PD, PD, PD, PD]
+        L.or_weiss_smith.argtypes = [C.c_void_p, PD, PD, PD, PD]
         _lib = L
     return _lib
 
@@ -170,10 +171,12 @@ class Oracle:
         g = np.ascontiguousarray(mesh["gnodes"], dtype=np.float64)
         f = np.ascontiguousarray(mesh["faces"], dtype=np.int32)
         pl = np.array(self.levels, dtype=np.int32)
-        ph = np.zeros(10)                           # gamma, Pr, mu, eta, qinf[5], flux code
+        ph = np.zeros(11)                           # gamma, Pr, mu, eta, qinf[5], flux code, Ur floor
         src = np.asarray(phys.packed() if hasattr(phys, "packed") else phys, dtype=np.float64)
         ph[:len(src)] = src
-        self.flux = ("rusanov", "roe")[int(ph[9])]
+        if len(src) <= 10:
+            ph[10] = 1.0
+        self.flux = ("rusanov", "roe", "weiss_smith")[int(ph[9])]
         self._keep = (g, f, pl, ph)
         self.h = lib().or_create(self.d, self.E, mesh["qg"], _d(g), len(f), _i(f), len(pl), _i(pl), _d(ph))
 
@@ -221,12 +224,13 @@ class Oracle:
         return f[:self.d, :self.nv].copy()
 
     def common_flux(self, qL, qR, n, kind=None):
-        """The inviscid common flux along the scaled normal n ("rusanov" or "roe"; default:
-        the context's physics)."""
+        """The inviscid common flux along the scaled normal n ("rusanov", "roe" or
+        "weiss_smith"; default: the context's physics)."""
         kind = kind or self.flux
         qL, qR, n = (np.ascontiguousarray(a, dtype=np.float64) for a in (qL, qR, n))
         F = np.zeros(5)
-        (lib().or_roe if kind == "roe" else lib().or_rusanov)(self.h, _d(qL), _d(qR), _d(n), _d(F))
+        fn = {"roe": lib().or_roe, "rusanov": lib().or_rusanov, "weiss_smith": lib().or_weiss_smith}[kind]
+        fn(self.h, _d(qL), _d(qR), _d(n), _d(F))
         return F[:self.nv].copy()
 
     def restrict(self, x0, l=0):

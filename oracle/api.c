@@ -33,7 +33,8 @@ or_ctx *or_create(int d, int E, int qg, const double *gnodes, int nfaces, const 
     C->d = d; C->nv = d + 2; C->E = E; C->qg = qg; C->nlev = nlev;
     C->ph.gamma = phys[0]; C->ph.Pr = phys[1]; C->ph.mu = phys[2]; C->ph.eta = phys[3];
     for (int v = 0; v < C->nv; ++v) C->ph.qinf[v] = phys[4 + v];
-    C->ph.flux = (int)phys[9];        /* phys = gamma, Pr, mu, eta, qinf[5], flux code */
+    C->ph.flux = (int)phys[9];        /* phys = gamma, Pr, mu, eta, qinf[5], flux code, Ur floor */
+    C->ph.ws_umin = phys[10];
     int m = qg + 1, ng = (d == 2) ? m * m : m * m * m;
     C->gnodes = malloc(sizeof(double) * (size_t)E * ng * d);
     memcpy(C->gnodes, gnodes, sizeof(double) * (size_t)E * ng * d);

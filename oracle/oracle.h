@@ -39,7 +39,9 @@ typedef struct {
 typedef struct {
     double gamma, Pr, mu, eta;         /* ratio of heats, Prandtl, viscosity, BR2 penalty */
     double qinf[5];                    /* free-stream conservative state (far field ghost) */
-    int flux;                          /* inviscid common flux: 0 Rusanov, 1 Roe          */
+    int flux;                          /* inviscid common flux: 0 Rusanov, 1 Roe,
+                                          2 Roe with Weiss-Smith low-Mach preconditioning */
+    double ws_umin;                    /* Weiss-Smith: floor of the reference velocity     */
 } or_phys;
 
 typedef struct {
@@ -76,5 +78,6 @@ void or_flux_inviscid(const or_ctx *C, const double *q, double f[3][5]);
 void or_flux_viscous(const or_ctx *C, const double *q, double Q[3][5], int adiabatic, double f[3][5]);
 void or_rusanov(const or_ctx *C, const double *qL, const double *qR, const double *n, double *F);
 void or_roe(const or_ctx *C, const double *qL, const double *qR, const double *n, double *F);
+void or_weiss_smith(const or_ctx *C, const double *qL, const double *qR, const double *n, double *F);
 
 #endif

@@ -196,6 +196,117 @@ void or_roe(const or_ctx *C, const double *qL, const double *qR, const double *n
     }
 }
 
+/* Weiss-Smith low-Mach preconditioning of Roe's dissipation (Sec. 4.1 uses it with Roe's
+ * solver for the steady low-Mach sphere).  In the primitive variables Q = (p, u, T), with the
+ * gas constant 1 (T = p / rho, C_p = gamma / (gamma - 1), c^2 = gamma T), the dissipation is
+ *     D = Gamma |Gamma^{-1} A_n| (Q_R - Q_L)
+ * at the Roe-averaged state (rho, u, H of Roe's solver), where A_n = dF_n/dQ along the unit
+ * normal and Gamma = dW/dQ with drho/dp replaced by theta = 1/Ur^2 - rho_T / (rho C_p); the
+ * reference velocity Ur = min(c, max(|u|, umin)).  Gamma^{-1} A_n has the eigenvalues vn
+ * (d times) and u' +- c', u' = vn (1 - alpha), c' = sqrt(alpha^2 vn^2 + Ur^2), alpha =
+ * (1 - Ur^2 / c^2) / 2: three distinct values (Ur > 0).  So |Gamma^{-1} A_n| is the
+ * quadratic p(B) = a0 + a1 B + a2 B^2 that takes |lambda| at them, and
+ *     D = a0 Gamma dQ + a1 A_n dQ + a2 A_n Gamma^{-1} A_n dQ.
+ * With Ur = c, Gamma = dW/dQ and D is Roe's |A| dW to first order in the jump. */
+typedef struct { double rho, u[3], H, T, rp, rT, cp, theta, vn, nh[3]; int d; } ws_state;
+
+static void ws_apply_A(const ws_state *S, const double *x, double *y) {
+    int d = S->d;
+    double nx = 0.0, ux = 0.0;
+    for (int j = 0; j < d; ++j) nx = fma(S->nh[j], x[1 + j], nx);
+    for (int j = 0; j < d; ++j) ux = fma(S->u[j], x[1 + j], ux);
+    double r = S->rp * S->vn * x[0] + S->rho * nx + S->rT * S->vn * x[d + 1];
+    y[0] = r;
+    for (int i = 0; i < d; ++i) y[1 + i] = S->u[i] * r + S->nh[i] * x[0] + S->rho * S->vn * x[1 + i];
+    y[d + 1] = S->H * r + S->rho * S->vn * ux + S->rho * S->cp * S->vn * x[d + 1];
+}
+static void ws_apply_G(const ws_state *S, const double *x, double *y) {
+    int d = S->d;
+    double ux = 0.0;
+    for (int j = 0; j < d; ++j) ux = fma(S->u[j], x[1 + j], ux);
+    double r = S->theta * x[0] + S->rT * x[d + 1];
+    y[0] = r;
+    for (int i = 0; i < d; ++i) y[1 + i] = S->u[i] * r + S->rho * x[1 + i];
+    y[d + 1] = S->H * r - x[0] + S->rho * ux + S->rho * S->cp * x[d + 1];
+}
+/* z = Gamma^{-1} y: the velocity rows give z_u, the energy row minus H times the first
+ * leaves -z_p + rho C_p z_T = s, which with theta z_p + rho_T z_T = y_0 fixes z_p, z_T */
+static void ws_solve_G(const ws_state *S, const double *y, double *z) {
+    int d = S->d;
+    double r0 = y[0], sum = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double t = y[1 + i] - S->u[i] * r0;
+        z[1 + i] = t / S->rho;
+        sum = fma(S->u[i], t, sum);
+    }
+    double s = y[d + 1] - S->H * r0 - sum;
+    double det = S->theta * S->rho * S->cp + S->rT;
+    z[0] = (r0 * S->rho * S->cp - S->rT * s) / det;
+    z[d + 1] = (S->theta * s + r0) / det;
+}
+
+void or_weiss_smith(const or_ctx *C, const double *qL, const double *qR, const double *n, double *F) {
+    int d = C->d, nv = C->nv;
+    double gamma = C->ph.gamma, gm1 = gamma - 1.0;
+    double fL[3][5], fR[3][5];
+    or_flux_inviscid(C, qL, fL);
+    or_flux_inviscid(C, qR, fR);
+    double nn = 0.0;
+    for (int c = 0; c < d; ++c) nn = fma(n[c], n[c], nn);
+    double nmag = sqrt(nn);
+    ws_state S;
+    S.d = d;
+    for (int c = 0; c < d; ++c) S.nh[c] = n[c] / nmag;
+    double rho[2], u[2][3], p[2], H[2], T[2];
+    for (int side = 0; side < 2; ++side) {
+        const double *q = side ? qR : qL;
+        double rinv = 1.0 / q[0], ke = 0.0;
+        rho[side] = q[0];
+        for (int j = 0; j < d; ++j) u[side][j] = q[1 + j] * rinv;
+        for (int j = 0; j < d; ++j) ke = fma(q[1 + j], u[side][j], ke);
+        p[side] = gm1 * (q[d + 1] - 0.5 * ke);
+        H[side] = (q[d + 1] + p[side]) * rinv;
+        T[side] = p[side] * rinv;
+    }
+    double sL = sqrt(rho[0]), sR = sqrt(rho[1]), wt = 1.0 / (sL + sR), q2 = 0.0;
+    for (int j = 0; j < d; ++j) S.u[j] = (sL * u[0][j] + sR * u[1][j]) * wt;
+    S.H = (sL * H[0] + sR * H[1]) * wt;
+    for (int j = 0; j < d; ++j) q2 = fma(S.u[j], S.u[j], q2);
+    S.vn = 0.0;
+    for (int j = 0; j < d; ++j) S.vn = fma(S.u[j], S.nh[j], S.vn);
+    double c2 = gm1 * (S.H - 0.5 * q2);
+    S.rho = sL * sR;
+    S.cp = gamma / gm1;
+    S.T = c2 / gamma;
+    S.rp = 1.0 / S.T;
+    S.rT = -S.rho / S.T;
+    double ur = fmin(sqrt(c2), fmax(sqrt(q2), C->ph.ws_umin));
+    S.theta = 1.0 / (ur * ur) - S.rT / (S.rho * S.cp);
+    double alpha = 0.5 * (1.0 - (ur * ur) / c2);
+    double up = S.vn * (1.0 - alpha), cq = sqrt(alpha * alpha * S.vn * S.vn + ur * ur);
+    double l1 = S.vn, l2 = up + cq, l3 = up - cq;
+    double f1 = fabs(l1), f2 = fabs(l2), f3 = fabs(l3);
+    double s21 = (f2 - f1) / (l2 - l1), s31 = (f3 - f1) / (l3 - l1);
+    double a2 = (s31 - s21) / (l3 - l2);
+    double a1 = s21 - a2 * (l1 + l2);
+    double a0 = f1 - a1 * l1 - a2 * (l1 * l1);
+    double dQ[5], g[5], y1[5], z[5], y2[5], Dv[5];
+    dQ[0] = p[1] - p[0];
+    for (int j = 0; j < d; ++j) dQ[1 + j] = u[1][j] - u[0][j];
+    dQ[d + 1] = T[1] - T[0];
+    ws_apply_G(&S, dQ, g);
+    ws_apply_A(&S, dQ, y1);
+    ws_solve_G(&S, y1, z);
+    ws_apply_A(&S, z, y2);
+    for (int v = 0; v < nv; ++v) Dv[v] = a0 * g[v] + a1 * y1[v] + a2 * y2[v];
+    for (int v = 0; v < nv; ++v) {
+        double FnL = 0.0, FnR = 0.0;
+        for (int c = 0; c < d; ++c) FnL = fma(fL[c][v], n[c], FnL);
+        for (int c = 0; c < d; ++c) FnR = fma(fR[c][v], n[c], FnR);
+        F[v] = 0.5 * (FnL + FnR) - 0.5 * nmag * Dv[v];
+    }
+}
+
 /* boundary ghost state: 1 = far field (free stream), 2 = no-slip adiabatic wall */
 static void ghost(const or_ctx *C, int bc, const double *qL, double *qR) {
     int d = C->d;
@@ -334,7 +445,8 @@ static void pair_flux(const or_ctx *C, const or_level *L, int P, const double *q
     for (int v = 0; v < nv; ++v) qs[v] = 0.5 * (qL[v] + qR[v]);
     for (int c = 0; c < d; ++c)
         for (int v = 0; v < nv; ++v) Qs[c][v] = (bc == 0) ? 0.5 * (QL[c][v] + QR[c][v]) : QL[c][v];
-    if (C->ph.flux == 1) or_roe(C, qL, qR, nrm, Fr);
+    if (C->ph.flux == 2) or_weiss_smith(C, qL, qR, nrm, Fr);
+    else if (C->ph.flux == 1) or_roe(C, qL, qR, nrm, Fr);
     else or_rusanov(C, qL, qR, nrm, Fr);
     or_flux_viscous(C, qs, Qs, bc == 2, fv);
     for (int v = 0; v < nv; ++v) {

@@ -277,7 +277,7 @@ def to_state(field: np.ndarray) -> np.ndarray:
 
 
 # ------------------------------------------------------------------------ configs
-FLUXES = ("rusanov", "roe")
+FLUXES = ("rusanov", "roe", "weiss_smith")
 
 
 @dataclass
@@ -287,17 +287,20 @@ class Physics:
     mu: float = 0.0
     eta: float = 2.0
     qinf: np.ndarray = field(default_factory=lambda: np.zeros(4))
-    flux: str = "rusanov"          # inviscid common flux: "rusanov" or "roe"
+    flux: str = "rusanov"          # inviscid common flux: "rusanov", "roe" or "weiss_smith"
+    ws_umin: float = 1.0           # weiss_smith: floor of the reference velocity (free-stream units)
 
     @property
     def flux_code(self) -> int:
         return FLUXES.index(self.flux)
 
     def packed(self) -> np.ndarray:
-        """gamma, Pr, mu, eta, qinf padded to 5, flux code (0 Rusanov, 1 Roe)."""
+        """gamma, Pr, mu, eta, qinf padded to 5, flux code (0 Rusanov, 1 Roe, 2 Roe with
+        Weiss-Smith preconditioning), reference-velocity floor."""
         qi = np.zeros(5)
         qi[:len(self.qinf)] = self.qinf
-        return np.concatenate([[self.gamma, self.Pr, self.mu, self.eta], qi, [self.flux_code]]).astype(np.float64)
+        return np.concatenate([[self.gamma, self.Pr, self.mu, self.eta], qi,
+                               [self.flux_code, self.ws_umin]]).astype(np.float64)
 
 
 @dataclass
