@@ -378,6 +378,44 @@ def batched_step(api, w, T, np, torch, N):
     return out
 
 
+def steady_lowmach(api, w, np, torch, max_it=100):
+    """The steady low-Mach cylinder (O-mesh 64 x 128, stretched to aspect ratio 1e3 at the
+    wall, p{4-2-1} n{2-2-5}, Ma 1e-3, Re 40, Rusanov, impulsive start): pseudo-transient
+    continuation with SER from dtau = 0.1 h_min / (|u| + c), FGMRES(30) to 1e-3 in at most 60
+    iterations per pseudo step, with the FP64 and with the mixed (FP32 cycle, blocks, LU)
+    preconditioner; per precision the relative residual reached after max_it pseudo steps,
+    the pseudo steps and seconds to reach drops of 1e-2 / 1e-3 / 1e-4, and the iteration
+    counts (CUDA events around the whole march)."""
+    W = w.cylinder_steady()
+    mach = 1e-3
+    dtau0 = 0.1 * W.mesh["h_min"] / (1.0 + 1.0 / mach)
+    out = {"workload": "cylinder_steady 64x128 O-mesh p{4-2-1} n{2-2-5} (Ma 1e-3, Re 40, Rusanov), PTC + SER, "
+                       f"FGMRES(30) tol 1e-3 maxit 60, {max_it} pseudo steps", "precisions": {}}
+    for prec in ("fp64", "mixed"):
+        G = api.fr_create(W.mesh, W.phys, W.levels)
+        o = api.solve_opts(kdim=30, maxit_gmres=60, nsmooth=(2, 2, 5), tol_gmres=1e-3, inv_dtau_star=-1.0,
+                           precision=prec)
+        q = torch.from_numpy(np.ascontiguousarray(W.q0)).cuda()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        st = api.ptc_steady(G, q, dtau0, 1e6, 1e-10, max_it, o)
+        e1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        h = np.asarray(st["hist"])
+        rel = h / h[0]
+        reach = {}
+        for tol in (1e-2, 1e-3, 1e-4):
+            k = int(np.argmax(rel <= tol)) if np.any(rel <= tol) else None
+            reach[f"{tol:g}"] = {"pseudo_steps": k, "s": (wall * k / max(1, len(h) - 1)) if k else None}
+        out["precisions"][prec] = {"relative_residual": float(rel[-1]), "pseudo_steps": int(st["n_ptc"]),
+                                   "gmres_total": int(st["n_gmres"]), "s": e0.elapsed_time(e1) / 1e3,
+                                   "converged_1e-10": bool(st["converged"]), "fp64_switch_at": st["prec_switch_it"],
+                                   "reached": reach}
+    return out
+
+
 def run_extras_in_child():
     """The ESDIRK guess comparison and the batched step, in a child process of their own
     (a clean library state, and a failure there cannot take the main measurement down)."""
@@ -385,7 +423,8 @@ def run_extras_in_child():
             "from paper_2202_09733_gb300 import api, workloads as w, tableaux as T, _native as N; "
             "torch.cuda.set_device(0); "
             "out = {'esdirk_cylinder': bench.esdirk_guess_compare(api, w, T, np, torch), "
-            "'batched_vortex': bench.batched_step(api, w, T, np, torch, N)}; "
+            "'batched_vortex': bench.batched_step(api, w, T, np, torch, N), "
+            "'steady_lowmach_cylinder': bench.steady_lowmach(api, w, np, torch)}; "
             "print('EXTRAS ' + json.dumps(out))") % ROOT
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
     for line in r.stdout.splitlines():
@@ -414,8 +453,17 @@ def gpu_arm(args):
     lib = N.load()
 
     W = w.tgv3d(n=args.n)
-    ctx = api.fr_create(W.mesh, W.phys, W.levels)
-    q0 = torch.from_numpy(W.q0).cuda()
+    part = None
+    if ws > 1:
+        # the mesh split over the ranks (one GPU each): ghosts exchanged and inner products
+        # summed over NCCL by the library's communicator
+        from paper_2202_09733_gb300.distributed import PartitionedContext, TorchDistTransport
+        part = PartitionedContext(W.mesh, W.phys, W.levels, rank, ws, TorchDistTransport())
+        ctx = part.ctx
+        q0 = part.local_state(W.q0)
+    else:
+        ctx = api.fr_create(W.mesh, W.phys, W.levels)
+        q0 = torch.from_numpy(W.q0).cuda()
     q = q0.clone()
     g, a, c, m = T.ros34pw2()
     opts = api.solve_opts(kdim=30, maxit_gmres=300, nsmooth=(2, 2), tol_gmres=1e-6, inv_dtau_star=1.0 / W.dt,
@@ -429,7 +477,7 @@ def gpu_arm(args):
         return api.row_step(ctx, g, a, c, m, W.dt, q, o)
 
     tune = None
-    if not args.no_autotune:
+    if not args.no_autotune and part is None:     # every rank would have to tune in lockstep
         # launch shapes of this GPU for the residual kernels; G of the block solves after
         # one step has factored the blocks (no result bit depends on either)
         step()
@@ -473,7 +521,7 @@ def gpu_arm(args):
         st64 = step(opts64)
         f1.record(stream)
         torch.cuda.synchronize()
-        t_fp64 = f0.elapsed_time(f1) / 1e3
+        t_fp64 = max_over_ranks(f0.elapsed_time(f1) / 1e3, ws, "cuda")
         dq = float(((q_mixed - q).abs().max() / q.abs().max()).item())
 
     # ---- residual throughput and roofline (same stream, CUDA events)
@@ -488,8 +536,9 @@ def gpu_arm(args):
     e1.record(stream)
     torch.cuda.synchronize()
     t_R = e0.elapsed_time(e1) / 1e3 / nrep
+    t_R = max_over_ranks(t_R, ws, "cuda")
     E = W.mesh["E"]
-    ndof = q0.numel()
+    ndof = int(W.q0.size)
     flops = PM.residual_flops(3, 3) * E
     gdofs = ndof / t_R / 1e9
 
@@ -504,7 +553,7 @@ def gpu_arm(args):
         api.row_step(ctx, g, a, c, m, W.dt, q, opts)
         out_host.copy_(q, non_blocking=True)
     torch.cuda.synchronize()
-    t_e2e = (time.perf_counter() - t0) / args.steps
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps, ws, "cuda")
     barrier()
 
     extras = {}
@@ -519,7 +568,8 @@ def gpu_arm(args):
         ng = [s_["n_gmres"] for s_ in stats]
         line = {
             "metric": METRIC, "value": t_step, "unit": "s/step", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+            "scaling": "strong" if ws > 1 else "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
             "data": "synthetic",
             "config": {"workload": f"tgv3d {args.n}^3 hex p=3 (Ma 0.1, Re 1600), ROS34PW2 step dt=20x explicit, "
@@ -527,7 +577,9 @@ def gpu_arm(args):
                        "precision": ("FP64 throughout" if args.precision == "fp64" else
                                      "mixed: FP64 residual, Jv, Gram-Schmidt, update; FP32 pMG cycle, blocks, LU"),
                        "ndof": ndof, "elements": E, "l2": "inputs larger than L2 (state 84 MB, blocks 31 GB): no flush",
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+                       "parallelism": (f"element partition over {ws} GPUs (recursive bisection, one ghost "
+                                       "layer; ghost exchange and inner-product sums over NCCL)") if ws > 1
+                                      else "single GPU"},
             "fp64_step_s": t_fp64,
             "speedup_vs_fp64_step": (t_fp64 / t_step) if t_fp64 else None,
             "fp64_step_gmres_iterations": st64["n_gmres"] if st64 else None,

@@ -72,12 +72,17 @@ typedef struct {
 /* gamma, Prandtl number, dynamic viscosity (1/Re in the dimensionless set-up of Sec. 2.2),
  * BR2 penalty, free-stream conservative state (nv values) used by far-field faces, and the
  * inviscid common flux: 0 Rusanov (local Lax-Friedrichs), 1 Roe (the original Roe solver
- * the paper uses in Sec. 4.2: |A| of the Roe-averaged state, no entropy fix).  Any other
- * flux value is FR_ERR_INVALID_ARG. */
+ * the paper uses in Sec. 4.2: |A| of the Roe-averaged state, no entropy fix), 2 Roe with
+ * the Weiss-Smith low-Mach preconditioning of its dissipation (Sec. 4.1, the steady
+ * low-Mach case): Gamma |Gamma^{-1} A_n| dQ in the primitive variables (p, u, T), Gamma =
+ * dW/dQ with drho/dp replaced by 1/Ur^2 - rho_T/(rho C_p), reference velocity
+ * Ur = min(c, max(|u|, ws_umin)) at the Roe-averaged state (ws_umin > 0, used with flux 2
+ * only).  Any other flux value is FR_ERR_INVALID_ARG. */
 typedef struct {
     double gamma, prandtl, mu, eta;
     double qinf[5];
     int flux;
+    double ws_umin;
 } fr_physics;
 
 /* Create a context: operator tables, geometric factors of every level, connectivity and
@@ -398,6 +403,48 @@ int fr_kernel_timeouts(int clear);
  * 4096 polls) so that callers can check that it reports through fr_kernel_timeouts and
  * leaves the context usable; synchronises the device */
 int fr_selftest_wait_timeout(void);
+
+/* ------------------------------------------------------------------ element partition
+ * One process per GPU, each solving its part of one mesh (the paper's runs split the mesh
+ * over four MPI processes, Sec. 4; the interface is this library's).  A process's context
+ * is created on its local mesh: its owned elements first (0 .. n_owned-1), then ghost
+ * copies of the other processes' elements that share a face with an owned element, in
+ * the order the communicator delivers them.  A ghost's faces towards elements that are
+ * neither owned nor ghost enter as far-field faces: they change only the ghost's own
+ * residual, which nothing reads.  With a communicator set on the context:
+ *  - before every residual evaluation of a state whose ghosts may be stale (fr_residual,
+ *    the Jacobian-vector product, every pMG level, the steppers), the library packs the
+ *    owned elements send_idx[0 .. nsend) of that level vector into send_buf (element by
+ *    element: nv Np_level values of the level's precision each, concatenated in send_idx
+ *    order) and calls halo(user, level, precision, elem_bytes, stream) with the stream
+ *    synchronised; on return recv_buf must hold the E - n_owned ghost elements' values
+ *    (ghost order, elem_bytes each), which the library copies into the ghosts.  A finite
+ *    difference column of the element blocks exchanges nothing (each process perturbs
+ *    its own elements only);
+ *  - every inner product and norm runs over the owned elements and is summed over the
+ *    processes by allreduce(user, buf, n, 0) on a host buffer; the FP32 cycle's maxima
+ *    by allreduce(.., 1) (max); RMS norms divide by the global unknown count
+ *    (n_owned_total elements); fr_set_comm itself communicates nothing;
+ *  - so each process's owned values follow the single-process computation step for step;
+ *    results differ from it only in the summation order of inner products.
+ * fr_residual and fr_jvp overwrite the ghost entries of their state inputs with the
+ * owners' values.  A non-zero return from a callback fails the call with FR_ERR_CUDA.
+ * Refused while a communicator is set: the network guess and its training (guess 2,
+ * train_iters > 0), the matrix-based coarse smoother, fr_residual_noalloc.
+ * send_buf and recv_buf: device memory of the caller, at least nsend (and E - n_owned)
+ * elements of nv Np_0 doubles. */
+typedef struct {
+    int n_owned;
+    long long n_owned_total;  /* owned elements over all processes (RMS norms divide by it) */
+    int nsend;
+    const int *send_idx;      /* host, nsend owned element indices (copied by the call) */
+    void *send_buf, *recv_buf;
+    int (*halo)(void *user, int level, int precision, long long elem_bytes, void *stream);
+    int (*allreduce)(void *user, double *buf, int n, int op);
+    void *user;
+} fr_comm;
+/* comm NULL: single process again */
+int fr_set_comm(fr_ctx *ctx, const fr_comm *comm);
 
 /* ------------------------------------------------------------------ batches
  * Many independent problems advanced together (not in the paper: a throughput mode).

@@ -19,7 +19,7 @@ ERRORS = {-1: "FR_ERR_INVALID_ARG", -2: "FR_ERR_CUDA", -3: "FR_ERR_OOM", -4: "FR
 # every symbol the header declares
 EXPORTS = ["fr_create", "fr_destroy", "fr_last_error", "fr_kernel_launches", "fr_level_info", "fr_num_colors", "fr_residual",
            "fr_residual_noalloc", "fr_jvp",
-           "fr_elem_blocks", "fr_elem_blocks_f32", "fr_set_block_method", "fr_nbr_blocks", "fr_neighbour_table", "fr_mbnk_last", "fr_mbnk_operator", "fr_block_factor", "fr_block_solve", "fr_restrict", "fr_prolong", "pmg_setup",
+           "fr_elem_blocks", "fr_elem_blocks_f32", "fr_set_block_method", "fr_set_comm", "fr_nbr_blocks", "fr_neighbour_table", "fr_mbnk_last", "fr_mbnk_operator", "fr_block_factor", "fr_block_solve", "fr_restrict", "fr_prolong", "pmg_setup",
            "pmg_precondition", "gmres_solve", "esdirk_step", "row_step", "ptc_steady",
            "mlp_create", "mlp_destroy", "mlp_get_params", "mlp_forward", "mlp_train_step", "fr_mlp_dims",
            "fr_set_mlp", "fr_reset_history", "fr_guess_features", "fr_batch_create", "fr_batch_destroy",
@@ -36,13 +36,22 @@ class MeshDesc(C.Structure):
 
 class Physics(C.Structure):
     _fields_ = [("gamma", C.c_double), ("prandtl", C.c_double), ("mu", C.c_double), ("eta", C.c_double),
-                ("qinf", C.c_double * 5), ("flux", C.c_int)]
+                ("qinf", C.c_double * 5), ("flux", C.c_int), ("ws_umin", C.c_double)]
 
 
 class PmgOpts(C.Structure):
     _fields_ = [("nlevels", C.c_int), ("nsmooth", C.c_int * 4), ("c", C.c_double), ("inv_dtau_star", C.c_double),
                 ("precision", C.c_int), ("coarse_smoother", C.c_int), ("mbnk_maxit", C.c_int),
                 ("mbnk_tol", C.c_double)]
+
+
+HaloFn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_longlong, C.c_void_p)
+AllreduceFn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_int)
+
+
+class Comm(C.Structure):
+    _fields_ = [("n_owned", C.c_int), ("n_owned_total", C.c_longlong), ("nsend", C.c_int), ("send_idx", PI), ("send_buf", VP), ("recv_buf", VP),
+                ("halo", HaloFn), ("allreduce", AllreduceFn), ("user", VP)]
 
 
 class GmresOpts(C.Structure):
@@ -103,6 +112,7 @@ def load(path: str = LIB_PATH):
         "fr_elem_blocks": ([VP, C.c_int, VP, C.c_double, VP, VP], C.c_int),
         "fr_elem_blocks_f32": ([VP, C.c_int, VP, C.c_double, VP, C.c_int, VP], C.c_int),
         "fr_set_block_method": ([VP, C.c_int], C.c_int),
+        "fr_set_comm": ([VP, C.POINTER(Comm)], C.c_int),
         "fr_nbr_blocks": ([VP, C.c_int, VP, C.c_double, VP, VP, VP], C.c_int),
         "fr_neighbour_table": ([VP, PI], C.c_int),
         "fr_mbnk_last": ([VP, PI, PD], C.c_int),

@@ -78,6 +78,7 @@ def fr_create(mesh: dict, phys, levels) -> Context:
     for v, x in enumerate(phys.qinf):
         ph.qinf[v] = float(x)
     ph.flux = int(getattr(phys, "flux_code", 0))
+    ph.ws_umin = float(getattr(phys, "ws_umin", 1.0))
     h = C.c_void_p()
     N.check(lib.fr_create(C.byref(h), C.byref(md), C.byref(ph)), "fr_create")
     return Context(h, mesh["d"], mesh["E"], list(levels), mesh["d"] + 2)
@@ -469,6 +470,7 @@ class Batch:
         for v, x in enumerate(phys.qinf):
             ph.qinf[v] = float(x)
         ph.flux = int(getattr(phys, "flux_code", 0))
+        ph.ws_umin = float(getattr(phys, "ws_umin", 1.0))
         h = C.c_void_p()
         N.check(lib.fr_batch_create(C.byref(h), len(problems), descs, C.byref(ph)), "fr_batch_create")
         self.handle = h

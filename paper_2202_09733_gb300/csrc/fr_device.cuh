@@ -34,7 +34,8 @@ struct FrPhys {
     T gamma, gm1, mu, kappa, c23;
     T qinf[5];
     T etagL, etagR;   // eta * g_L'(-1), eta * g_R'(+1) of the level
-    int flux;         // inviscid common flux: 0 Rusanov, 1 Roe
+    int flux;         // inviscid common flux: 0 Rusanov, 1 Roe, 2 Roe + Weiss-Smith
+    T ws_umin;        // Weiss-Smith: floor of the reference velocity
 };
 
 template <int D, int P>
@@ -262,6 +263,131 @@ __device__ __forceinline__ void roe(const FrPhys<B> &ph, const T *qL, const T *q
     }
 }
 
+// Roe's solver with the Weiss-Smith low-Mach preconditioning of its dissipation: in the
+// primitive variables Q = (p, u, T) (gas constant 1, C_p = gamma/(gamma-1)) the dissipation is
+// Gamma |Gamma^{-1} A_n| dQ at the Roe-averaged state, Gamma = dW/dQ with drho/dp replaced by
+// theta = 1/Ur^2 - rho_T/(rho C_p), Ur = min(c, max(|u|, umin)); Gamma^{-1} A_n has the three
+// distinct eigenvalues vn, u' +- c' (u' = vn (1 - alpha), c' = sqrt(alpha^2 vn^2 + Ur^2),
+// alpha = (1 - Ur^2/c^2)/2), so |Gamma^{-1} A_n| is the quadratic through |lambda| at them:
+// D = a0 Gamma dQ + a1 A_n dQ + a2 A_n Gamma^{-1} A_n dQ.
+template <int D, typename T, typename B>
+struct WsState {
+    T rho, u[3], H, T_, rp, rT, cp, theta, vn;
+    B nh[3];
+};
+template <int D, typename T, typename B>
+__device__ __forceinline__ void ws_apply_A(const WsState<D, T, B> &S, const T *x, T *y) {
+    T nx = T(0), ux = T(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) nx = fma(S.nh[j], x[1 + j], nx);
+#pragma unroll
+    for (int j = 0; j < D; ++j) ux = fma(S.u[j], x[1 + j], ux);
+    T r = S.rp * S.vn * x[0] + S.rho * nx + S.rT * S.vn * x[D + 1];
+    y[0] = r;
+#pragma unroll
+    for (int i = 0; i < D; ++i) y[1 + i] = S.u[i] * r + S.nh[i] * x[0] + S.rho * S.vn * x[1 + i];
+    y[D + 1] = S.H * r + S.rho * S.vn * ux + S.rho * S.cp * S.vn * x[D + 1];
+}
+template <int D, typename T, typename B>
+__device__ __forceinline__ void ws_apply_G(const WsState<D, T, B> &S, const T *x, T *y) {
+    T ux = T(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) ux = fma(S.u[j], x[1 + j], ux);
+    T r = S.theta * x[0] + S.rT * x[D + 1];
+    y[0] = r;
+#pragma unroll
+    for (int i = 0; i < D; ++i) y[1 + i] = S.u[i] * r + S.rho * x[1 + i];
+    y[D + 1] = S.H * r - x[0] + S.rho * ux + S.rho * S.cp * x[D + 1];
+}
+// z = Gamma^{-1} y (the velocity rows, then the 2 x 2 system of the first and energy rows)
+template <int D, typename T, typename B>
+__device__ __forceinline__ void ws_solve_G(const WsState<D, T, B> &S, const T *y, T *z) {
+    T r0 = y[0], sum = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        T t = y[1 + i] - S.u[i] * r0;
+        z[1 + i] = t / S.rho;
+        sum = fma(S.u[i], t, sum);
+    }
+    T s = y[D + 1] - S.H * r0 - sum;
+    T det = S.theta * S.rho * S.cp + S.rT;
+    z[0] = (r0 * S.rho * S.cp - S.rT * s) / det;
+    z[D + 1] = (S.theta * s + r0) / det;
+}
+
+template <int D, typename T, typename B>
+__device__ __forceinline__ void weiss_smith(const FrPhys<B> &ph, const T *qL, const T *qR, const B *n, T *F) {
+    constexpr int nv = D + 2;
+    T fL[3][5], fR[3][5];
+    flux_inviscid<D, T, B>(ph, qL, fL);
+    flux_inviscid<D, T, B>(ph, qR, fR);
+    B nn = B(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) nn = fma(n[c], n[c], nn);
+    B nmag = sqrt(nn);
+    WsState<D, T, B> S;
+#pragma unroll
+    for (int c = 0; c < D; ++c) S.nh[c] = n[c] / nmag;
+    T rho[2], u[2][3], p[2], H[2], Tt[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const T *q = side ? qR : qL;
+        T rinv = T(1) / q[0], ke = T(0);
+        rho[side] = q[0];
+#pragma unroll
+        for (int j = 0; j < D; ++j) u[side][j] = q[1 + j] * rinv;
+#pragma unroll
+        for (int j = 0; j < D; ++j) ke = fma(q[1 + j], u[side][j], ke);
+        p[side] = ph.gm1 * (q[D + 1] - T(0.5) * ke);
+        H[side] = (q[D + 1] + p[side]) * rinv;
+        Tt[side] = p[side] * rinv;
+    }
+    T sL = sqrt(rho[0]), sR = sqrt(rho[1]), wt = T(1) / (sL + sR), q2 = T(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) S.u[j] = (sL * u[0][j] + sR * u[1][j]) * wt;
+    S.H = (sL * H[0] + sR * H[1]) * wt;
+#pragma unroll
+    for (int j = 0; j < D; ++j) q2 = fma(S.u[j], S.u[j], q2);
+    S.vn = T(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) S.vn = fma(S.u[j], S.nh[j], S.vn);
+    T c2 = ph.gm1 * (S.H - T(0.5) * q2);
+    S.rho = sL * sR;
+    S.cp = T(ph.gamma / ph.gm1);
+    S.T_ = c2 / T(ph.gamma);
+    S.rp = T(1) / S.T_;
+    S.rT = -S.rho / S.T_;
+    T ur = fmin(sqrt(c2), fmax(sqrt(q2), T(ph.ws_umin)));
+    S.theta = T(1) / (ur * ur) - S.rT / (S.rho * S.cp);
+    T alpha = T(0.5) * (T(1) - (ur * ur) / c2);
+    T up = S.vn * (T(1) - alpha), cq = sqrt(alpha * alpha * S.vn * S.vn + ur * ur);
+    T l1 = S.vn, l2 = up + cq, l3 = up - cq;
+    T f1 = fabs(l1), f2 = fabs(l2), f3 = fabs(l3);
+    T s21 = (f2 - f1) / (l2 - l1), s31 = (f3 - f1) / (l3 - l1);
+    T a2 = (s31 - s21) / (l3 - l2);
+    T a1 = s21 - a2 * (l1 + l2);
+    T a0 = f1 - a1 * l1 - a2 * (l1 * l1);
+    T dQ[5], g[5], y1[5], z[5], y2[5];
+    dQ[0] = p[1] - p[0];
+#pragma unroll
+    for (int j = 0; j < D; ++j) dQ[1 + j] = u[1][j] - u[0][j];
+    dQ[D + 1] = Tt[1] - Tt[0];
+    ws_apply_G<D, T, B>(S, dQ, g);
+    ws_apply_A<D, T, B>(S, dQ, y1);
+    ws_solve_G<D, T, B>(S, y1, z);
+    ws_apply_A<D, T, B>(S, z, y2);
+#pragma unroll
+    for (int v = 0; v < nv; ++v) {
+        T Dv = a0 * g[v] + a1 * y1[v] + a2 * y2[v];
+        T FnL = T(0), FnR = T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) FnL = fma(fL[c][v], n[c], FnL);
+#pragma unroll
+        for (int c = 0; c < D; ++c) FnR = fma(fR[c][v], n[c], FnR);
+        F[v] = T(0.5) * (FnL + FnR) - T(0.5) * nmag * Dv;
+    }
+}
+
 template <int D, typename T, typename B>
 __device__ __forceinline__ void ghost_state(const FrPhys<B> &ph, int bc, const T *qL, T *qR) {
     if (bc == 1) {
@@ -440,7 +566,8 @@ __global__ void __launch_bounds__(256) k_pair_flux(const int4 *__restrict__ pair
 #pragma unroll
     for (int v = 0; v < nv; ++v) qs[v] = T(0.5) * (qL[v] + qR[v]);
     T Fr[5], fv[3][5];
-    if (ph.flux == 1) roe<D, T, B>(ph, qL, qR, nrm, Fr);
+    if (ph.flux == 2) weiss_smith<D, T, B>(ph, qL, qR, nrm, Fr);
+    else if (ph.flux == 1) roe<D, T, B>(ph, qL, qR, nrm, Fr);
     else rusanov<D, T, B>(ph, qL, qR, nrm, Fr);
     flux_viscous<D, T, B>(ph, qs, Qs, bc == 2, fv);
 #pragma unroll

@@ -79,6 +79,7 @@ FR_DN DualN<K> sqrt(DualN<K> a) {
 }
 FR_DN DualN<K> fabs(DualN<K> a) { return a.v < 0.f ? -a : a; }
 FR_DN DualN<K> fmax(DualN<K> a, DualN<K> b) { return a.v >= b.v ? a : b; }
+FR_DN DualN<K> fmin(DualN<K> a, DualN<K> b) { return a.v <= b.v ? a : b; }
 #undef FR_EACH
 #undef FR_DN
 

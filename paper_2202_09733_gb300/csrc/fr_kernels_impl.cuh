@@ -47,6 +47,7 @@ static FrPhys<FRT> to_phys(const FrPhysH &h, const FrLevelT<FRT> &L) {
     for (int v = 0; v < 5; ++v) p.qinf[v] = (FRT)h.qinf[v];
     p.etagL = (FRT)L.etagL; p.etagR = (FRT)L.etagR;
     p.flux = h.flux;
+    p.ws_umin = (FRT)h.ws_umin;
     return p;
 }
 
@@ -85,6 +86,35 @@ int FRK(residual)(const FrLevelT<FRT> &L, const FrPhysH &h, const FRT *q, FRT *R
         }
     }
     return -1;
+}
+
+// -------------------------------------------------------------- element partition
+// Ghost exchange of a [rows][E] level vector: pack the owned elements idx[0..nsend) into
+// buf[slot][rows] (slot-major, so every peer's slots are one contiguous chunk), and unpack
+// buf[j][rows] into the ghost elements n_owned + j (j < nrecv).
+__global__ void k_halo_pack(int rows, long long E, int nsend, const int *idx, const FRT *x, FRT *buf) {
+    long long n = (long long)rows * nsend;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        int slot = (int)(t / rows), r = (int)(t - (long long)slot * rows);
+        buf[t] = x[(size_t)r * E + idx[slot]];
+    }
+}
+__global__ void k_halo_unpack(int rows, long long E, int n_owned, int nrecv, const FRT *buf, FRT *x) {
+    long long n = (long long)rows * nrecv;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        int j = (int)(t / rows), r = (int)(t - (long long)j * rows);
+        x[(size_t)r * E + n_owned + j] = buf[t];
+    }
+}
+void FRK(halo_pack)(int rows, long long E, int nsend, const int *idx, const FRT *x, FRT *buf, cudaStream_t s) {
+    long long n = (long long)rows * nsend;
+    if (n == 0) return;
+    CNT(); k_halo_pack<<<(int)std::min<long long>((n + 255) / 256, 152LL * 16), 256, 0, s>>>(rows, E, nsend, idx, x, buf);
+}
+void FRK(halo_unpack)(int rows, long long E, int n_owned, int nrecv, const FRT *buf, FRT *x, cudaStream_t s) {
+    long long n = (long long)rows * nrecv;
+    if (n == 0) return;
+    CNT(); k_halo_unpack<<<(int)std::min<long long>((n + 255) / 256, 152LL * 16), 256, 0, s>>>(rows, E, n_owned, nrecv, buf, x);
 }
 
 // ------------------------------------------------------------------- elementwise

@@ -34,7 +34,8 @@ typedef FrLevelT<DualT> FrLevelAD;
 
 struct FrPhysH {
     double gamma, gm1, mu, kappa, c23, qinf[5];
-    int flux;   // 0 Rusanov, 1 Roe
+    int flux;   // 0 Rusanov, 1 Roe, 2 Roe with Weiss-Smith preconditioning
+    double ws_umin;   // Weiss-Smith: floor of the reference velocity
 };
 
 // tables: per degree p (0..5) and transfers per (p0, p1)
@@ -63,7 +64,9 @@ struct FrTabH {
     int P##_lu_solve_error(int clear);                                                                      \
     void P##_wait_selftest(int limit, cudaStream_t s);                                                      \
     int P##_transfer(const FrLevelT<T> &Lf, const FrLevelT<T> &Lc, bool restrict_, const T *x, T *y,       \
-                     cudaStream_t s);
+                     cudaStream_t s);                                                                       \
+    void P##_halo_pack(int rows, long long E, int nsend, const int *idx, const T *x, T *buf, cudaStream_t s);  \
+    void P##_halo_unpack(int rows, long long E, int n_owned, int nrecv, const T *buf, T *x, cudaStream_t s);
 
 FRK_DECLARE(frk64, double)
 FRK_DECLARE(frk32, float)
@@ -81,7 +84,11 @@ void frk64_lincomb(long long n, int m, const double *coef_host, const double *co
 void frk64_stage_F(long long n, const double *q, const double *sv, double adt, const double *R, double *F,
                    cudaStream_t s);                                                    // F = (q - sv)/adt - R
 void frk64_add_div(long long n, const double *a, const double *acc, double dt, double *y, cudaStream_t s);
-int frk64_multidot(long long n, int m, const double *w, const double *const *V, double *out_dev, cudaStream_t s);
+// out_dev[j] = w . V_j over rows x n_owned entries of [rows][E] vectors (n_owned = E: all);
+// partial: frk64_multidot_scratch(rows * n_owned) doubles of the caller's
+long long frk64_multidot_scratch(long long n);
+int frk64_multidot(long long rows, long long E, long long n_owned, int m, const double *w, const double *const *V,
+                   double *out_dev, double *partial, cudaStream_t s);
 void frk64_multi_axpy(long long n, int m, const double *h_dev, const double *const *V, double *w, cudaStream_t s);
 void frk64_update_x(long long n, int m, const double *y_host, const double *const *Z, double *x, cudaStream_t s);
 
@@ -92,6 +99,12 @@ void frk32_d2f_scaled(long long n, const double *x, const double *xmax_dev, doub
 int frk32_absmax_var(int nv, long long per, const double *x, double *out_dev, cudaStream_t s);
 int frk32_absmax_var_f(int nv, long long per, const float *x, double *out_dev, cudaStream_t s);
 int frk32_absmax(long long n, const double *x, double *out_dev, cudaStream_t s);
+// the same over the owned elements (first n_owned of E) of [rows][E] vectors
+int frk32_absmax_owned(long long rows, long long E, long long n_owned, const double *x, double *out_dev, cudaStream_t s);
+int frk32_absmax_var_owned(int nv, long long np, long long E, long long n_owned, const double *x, double *out_dev,
+                           cudaStream_t s);
+int frk32_absmax_var_owned_f(int nv, long long np, long long E, long long n_owned, const float *x, double *out_dev,
+                             cudaStream_t s);
 void frk32_f2d_unscale(long long n, const float *x, const double *xmax_dev, double target, double *y, cudaStream_t s);
 
 void frk32_d2f_scaled_dev(long long n, const double *x, const double *xmax_dev, const double *target_dev, float *y,

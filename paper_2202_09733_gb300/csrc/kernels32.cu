@@ -54,6 +54,40 @@ int frk32_absmax_var(int nv, long long per, const double *x, double *out_dev, cu
 int frk32_absmax_var_f(int nv, long long per, const float *x, double *out_dev, cudaStream_t s) {
     return absmax_var<float>(nv, per, x, out_dev, s);
 }
+// the same maxima over the owned elements only (index t -> row t / n_owned, element
+// t % n_owned of a [rows][E] vector); per variable: rows = np per variable
+template <typename S>
+__global__ void k_absmax_owned(long long n, long long E, long long n_owned, long long rows_per_out, const S *x,
+                               unsigned long long *out) {
+    int v = blockIdx.y;
+    const S *xv = x + (size_t)v * rows_per_out * E;
+    double m = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, fabs((double)xv[(t / n_owned) * E + t % n_owned]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + v, (unsigned long long)__double_as_longlong(m));
+}
+template <typename S>
+static int absmax_owned(int nout, long long rows_per_out, long long E, long long n_owned, const S *x, double *out_dev,
+                        cudaStream_t s) {
+    if (cudaMemsetAsync(out_dev, 0, sizeof(double) * nout, s) != cudaSuccess) return -1;
+    long long n = rows_per_out * n_owned;
+    int gx = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 4));
+    CNT(); k_absmax_owned<S><<<dim3(gx, nout), 256, 0, s>>>(n, E, n_owned, rows_per_out, x, (unsigned long long *)out_dev);
+    return 0;
+}
+int frk32_absmax_owned(long long rows, long long E, long long n_owned, const double *x, double *out_dev, cudaStream_t s) {
+    return absmax_owned<double>(1, rows, E, n_owned, x, out_dev, s);
+}
+int frk32_absmax_var_owned(int nv, long long np, long long E, long long n_owned, const double *x, double *out_dev,
+                           cudaStream_t s) {
+    return absmax_owned<double>(nv, np, E, n_owned, x, out_dev, s);
+}
+int frk32_absmax_var_owned_f(int nv, long long np, long long E, long long n_owned, const float *x, double *out_dev,
+                             cudaStream_t s) {
+    return absmax_owned<float>(nv, np, E, n_owned, x, out_dev, s);
+}
+
 // y = double(x) * (max / target): undoes the input scaling of the FP32 cycle
 __global__ void k_f2d_unscale(long long n, const float *x, const double *xmax, double target, double *y) {
     double m = *xmax;

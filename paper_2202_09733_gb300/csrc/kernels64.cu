@@ -72,12 +72,16 @@ static inline int red_blocks(long long n) {
     return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 8));
 }
 
+// w . V_j over the owned part of level vectors: index i -> (row i / n_owned, element
+// i % n_owned) of a [rows][E] vector (n_owned = E: the whole vector, in the same order)
 template <int M>
-__global__ void __launch_bounds__(RED_THREADS) k_multidot_partial(long long n, const double *w, Ptr8 V, double *partial) {
+__global__ void __launch_bounds__(RED_THREADS) k_multidot_partial(long long n, long long E, long long n_owned,
+                                                                  const double *w, Ptr8 V, double *partial) {
     double acc[M];
 #pragma unroll
     for (int j = 0; j < M; ++j) acc[j] = 0.0;
-    GRID_STRIDE(i, n) {
+    GRID_STRIDE(t, n) {
+        long long i = n_owned == E ? t : (t / n_owned) * E + t % n_owned;
         double wi = w[i];
 #pragma unroll
         for (int j = 0; j < M; ++j) acc[j] = fma(wi, V.p[j][i], acc[j]);
@@ -98,39 +102,65 @@ __global__ void __launch_bounds__(RED_THREADS) k_multidot_partial(long long n, c
     }
 }
 
-__global__ void k_multidot_final(int nb, int m, const double *partial, double *out) {
-    int j = threadIdx.x;
-    if (j >= m) return;
-    double t = 0.0;
-    for (int b = 0; b < nb; ++b) t = t + partial[(size_t)b * 8 + j];
-    out[j] = t;
+// one CTA of RED_THREADS threads: thread t sums the partials t, t + RED_THREADS, ... of
+// every column j in that order, then a fixed shuffle tree and the warp sums in warp order
+// (the same order for a given nb on every call)
+template <int M>
+__global__ void __launch_bounds__(RED_THREADS) k_multidot_final(int nb, const double *partial, double *out) {
+    double acc[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) acc[j] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += RED_THREADS)
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc[j] = acc[j] + partial[(size_t)b * 8 + j];
+    __shared__ double sh[RED_THREADS / 32][M];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        double v = acc[j];
+        for (int o = 16; o > 0; o >>= 1) v = v + __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[wid][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < M) {
+        double t = 0.0;
+        for (int k = 0; k < RED_THREADS / 32; ++k) t = t + sh[k][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
 }
 
-static double *g_partial = nullptr;
-static int g_partial_n = 0;
+long long frk64_multidot_scratch(long long n) { return (long long)red_blocks(n) * 8; }
 
-int frk64_multidot(long long n, int m, const double *w, const double *const *V, double *out, cudaStream_t s) {
+// out[j] = w . V_j (j < m) over the owned elements (rows x n_owned of [rows][E] vectors;
+// n_owned = E for whole vectors); partial: frk64_multidot_scratch(rows * n_owned) doubles
+int frk64_multidot(long long rows, long long E, long long n_owned, int m, const double *w, const double *const *V,
+                   double *out, double *partial, cudaStream_t s) {
+    long long n = rows * n_owned;
     int nb = red_blocks(n);
-    if (g_partial_n < nb * 8) {
-        if (g_partial) cudaFree(g_partial);
-        if (cudaMalloc(&g_partial, sizeof(double) * nb * 8) != cudaSuccess) { g_partial = nullptr; g_partial_n = 0; return -1; }
-        g_partial_n = nb * 8;
-    }
     for (int j0 = 0; j0 < m; j0 += 8) {
         int mm = std::min(8, m - j0);
         Ptr8 P;
         for (int j = 0; j < 8; ++j) { P.p[j] = j < mm ? V[j0 + j] : nullptr; P.c[j] = 0.0; }
         switch (mm) {
-            case 1: { CNT(); k_multidot_partial<1><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
-            case 2: { CNT(); k_multidot_partial<2><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
-            case 3: { CNT(); k_multidot_partial<3><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
-            case 4: { CNT(); k_multidot_partial<4><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
-            case 5: { CNT(); k_multidot_partial<5><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
-            case 6: { CNT(); k_multidot_partial<6><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
-            case 7: { CNT(); k_multidot_partial<7><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
-            default: { CNT(); k_multidot_partial<8><<<nb, RED_THREADS, 0, s>>>(n, w, P, g_partial); break; }
+            case 1: { CNT(); k_multidot_partial<1><<<nb, RED_THREADS, 0, s>>>(n, E, n_owned, w, P, partial); break; }
+            case 2: { CNT(); k_multidot_partial<2><<<nb, RED_THREADS, 0, s>>>(n, E, n_owned, w, P, partial); break; }
+            case 3: { CNT(); k_multidot_partial<3><<<nb, RED_THREADS, 0, s>>>(n, E, n_owned, w, P, partial); break; }
+            case 4: { CNT(); k_multidot_partial<4><<<nb, RED_THREADS, 0, s>>>(n, E, n_owned, w, P, partial); break; }
+            case 5: { CNT(); k_multidot_partial<5><<<nb, RED_THREADS, 0, s>>>(n, E, n_owned, w, P, partial); break; }
+            case 6: { CNT(); k_multidot_partial<6><<<nb, RED_THREADS, 0, s>>>(n, E, n_owned, w, P, partial); break; }
+            case 7: { CNT(); k_multidot_partial<7><<<nb, RED_THREADS, 0, s>>>(n, E, n_owned, w, P, partial); break; }
+            default: { CNT(); k_multidot_partial<8><<<nb, RED_THREADS, 0, s>>>(n, E, n_owned, w, P, partial); break; }
         }
-        CNT(); k_multidot_final<<<1, 32, 0, s>>>(nb, mm, g_partial, out + j0);
+        switch (mm) {
+            case 1: { CNT(); k_multidot_final<1><<<1, RED_THREADS, 0, s>>>(nb, partial, out + j0); break; }
+            case 2: { CNT(); k_multidot_final<2><<<1, RED_THREADS, 0, s>>>(nb, partial, out + j0); break; }
+            case 3: { CNT(); k_multidot_final<3><<<1, RED_THREADS, 0, s>>>(nb, partial, out + j0); break; }
+            case 4: { CNT(); k_multidot_final<4><<<1, RED_THREADS, 0, s>>>(nb, partial, out + j0); break; }
+            case 5: { CNT(); k_multidot_final<5><<<1, RED_THREADS, 0, s>>>(nb, partial, out + j0); break; }
+            case 6: { CNT(); k_multidot_final<6><<<1, RED_THREADS, 0, s>>>(nb, partial, out + j0); break; }
+            case 7: { CNT(); k_multidot_final<7><<<1, RED_THREADS, 0, s>>>(nb, partial, out + j0); break; }
+            default: { CNT(); k_multidot_final<8><<<1, RED_THREADS, 0, s>>>(nb, partial, out + j0); break; }
+        }
     }
     return 0;
 }

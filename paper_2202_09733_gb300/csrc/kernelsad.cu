@@ -50,6 +50,7 @@ int frkad_residual(const FrLevelAD &L, const FrPhysH &h, const DualT *q, DualT *
     for (int v = 0; v < 5; ++v) ph.qinf[v] = (float)h.qinf[v];
     ph.etagL = (float)L.etagL; ph.etagR = (float)L.etagR;
     ph.flux = h.flux;
+    ph.ws_umin = (float)h.ws_umin;
     if (L.d == 2) {
         switch (L.p) {
             case 1: residual_ad<2, 1>(L, ph, q, R, s); return 0;
@@ -157,6 +158,7 @@ static FrPhys<float> ad_phys(const FrPhysH &h, const FrLevel32 &L) {
     for (int v = 0; v < 5; ++v) ph.qinf[v] = (float)h.qinf[v];
     ph.etagL = (float)L.etagL; ph.etagR = (float)L.etagR;
     ph.flux = h.flux;
+    ph.ws_umin = (float)h.ws_umin;
     return ph;
 }
 

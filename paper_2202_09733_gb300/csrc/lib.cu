@@ -140,6 +140,12 @@ struct fr_ctx {
     unsigned short *Xf, *ringX;
     float *Yf, *Tf, *ringT;
     int ring_cap, ring_n, ring_head, train_cursor;
+    // element partition (fr_set_comm): ghosts are elements n_owned .. E-1
+    int has_comm;
+    fr_comm comm;
+    int *send_idx_dev;
+    double ndof_rms;              // unknowns the RMS norms divide by (over all processes)
+    double *partial;              // this context's reduction partials
 };
 
 static int dalloc(fr_ctx *C, void **p, size_t bytes) {
@@ -273,7 +279,8 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
     }
     if (!(ph->gamma > 1.0) || !(ph->prandtl > 0.0) || !(ph->mu >= 0.0) || !(ph->eta >= 0.0))
         return fail(FR_ERR_INVALID_ARG, "invalid physical parameters");
-    if (ph->flux != 0 && ph->flux != 1) return fail(FR_ERR_INVALID_ARG, "flux must be 0 (Rusanov) or 1 (Roe)");
+    if (ph->flux < 0 || ph->flux > 2) return fail(FR_ERR_INVALID_ARG, "flux must be 0 (Rusanov), 1 (Roe) or 2 (Weiss-Smith)");
+    if (ph->flux == 2 && !(ph->ws_umin > 0.0)) return fail(FR_ERR_INVALID_ARG, "Weiss-Smith needs a positive ws_umin");
     fr_ctx *C = new fr_ctx();
     C->d = m->dim; C->nv = m->dim + 2; C->E = m->nelem; C->qg = m->qg; C->nlev = m->nlevels;
     C->eta = ph->eta;
@@ -284,6 +291,7 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
     C->ph.c23 = 2.0 / 3.0;
     for (int v = 0; v < 5; ++v) C->ph.qinf[v] = v < C->nv ? ph->qinf[v] : 0.0;
     C->ph.flux = ph->flux;
+    C->ph.ws_umin = ph->flux == 2 ? ph->ws_umin : 1.0;
     int rc = upload_tables();
     for (int l = 0; rc == FR_OK && l < m->nlevels; ++l) rc = setup_level(C, l, m->plevels[l], m);
     for (int F = 0; F < m->nfaces; ++F)
@@ -311,6 +319,8 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
     long long n0 = C->L[0].ndof;
     if (rc == FR_OK) rc = dalloc_t(C, &C->info, 1);
     if (rc == FR_OK) rc = dalloc_t(C, &C->dots, 64);
+    if (rc == FR_OK) rc = dalloc_t(C, &C->partial, (size_t)frk64_multidot_scratch(C->L[0].ndof));
+    C->ndof_rms = (double)C->L[0].ndof;
     if (rc == FR_OK) rc = dalloc_t(C, &C->jv_qp, n0);
     if (rc == FR_OK) rc = dalloc_t(C, &C->jv_Rp, n0);
     if (rc != FR_OK) { fr_destroy(C); return rc; }
@@ -353,9 +363,17 @@ int fr_internal_level(const fr_ctx *C, int l, FrLevel *out, FrPhysH *ph) {
     return FR_OK;
 }
 int fr_internal_fail(int code, const char *msg) { return fail(code, "%s", msg); }
+int fr_internal_has_comm(const fr_ctx *C) { return C->has_comm; }
 
 // ------------------------------------------------------------------ residual, Jv
+// ---------------------------------------------------------- element partition
+// the ghost elements of the level-l vector x take their owners' values (no-op without a
+// communicator); x is the caller's state: only its ghost entries change
+static int halo64(fr_ctx *C, int l, const double *x, cudaStream_t s);
+static int halo32(fr_ctx *C, int l, const float *x, cudaStream_t s);
+
 static int residual(fr_ctx *C, int l, const double *q, double *R, cudaStream_t s) {
+    TRY(halo64(C, l, q, s));
     if (frk64_residual(C->L[l], C->ph, q, R, s) != 0)
         return fail(FR_ERR_UNIMPLEMENTED, "no kernel for d=%d p=%d", C->d, C->L[l].p);
     CKLAUNCH();
@@ -439,11 +457,83 @@ template <typename T> static PmgBuf<T> &pbuf(fr_ctx *C);
 template <> PmgBuf<double> &pbuf<double>(fr_ctx *C) { return C->p64; }
 template <> PmgBuf<float> &pbuf<float>(fr_ctx *C) { return C->p32; }
 
+static int halo_t(fr_ctx *C, int l, const double *x, cudaStream_t s) { return halo64(C, l, x, s); }
+static int halo_t(fr_ctx *C, int l, const float *x, cudaStream_t s) { return halo32(C, l, x, s); }
+
+// exchange = false: a finite-difference column, whose perturbation stays on this process
 template <typename T>
-static int residual_t(fr_ctx *C, int l, const T *q, T *R, cudaStream_t s) {
+static int residual_t(fr_ctx *C, int l, const T *q, T *R, cudaStream_t s, bool exchange = true) {
+    if (exchange) TRY(halo_t(C, l, q, s));
     if (Kn<T>::residual(levels<T>(C)[l], C->ph, q, R, s) != 0)
         return fail(FR_ERR_UNIMPLEMENTED, "no kernel for d=%d p=%d", C->d, C->L[l].p);
     CKLAUNCH();
+    return FR_OK;
+}
+
+template <typename T>
+static int halo_impl(fr_ctx *C, int l, const T *x, int prec, cudaStream_t s,
+                     void (*pack)(int, long long, int, const int *, const T *, T *, cudaStream_t),
+                     void (*unpack)(int, long long, int, int, const T *, T *, cudaStream_t)) {
+    if (!C->has_comm) return FR_OK;
+    const FrLevel &L = C->L[l];
+    int rows = L.nv * L.np, nrecv = C->E - C->comm.n_owned;
+    T *xm = const_cast<T *>(x);   // only the ghost entries are written
+    pack(rows, C->E, C->comm.nsend, C->send_idx_dev, x, (T *)C->comm.send_buf, s);
+    CKLAUNCH();
+    CK(cudaStreamSynchronize(s));
+    if (C->comm.halo(C->comm.user, l, prec, (long long)rows * (long long)sizeof(T), (void *)s) != 0)
+        return fail(FR_ERR_CUDA, "ghost exchange failed (level %d)", l);
+    unpack(rows, C->E, C->comm.n_owned, nrecv, (const T *)C->comm.recv_buf, xm, s);
+    CKLAUNCH();
+    return FR_OK;
+}
+static int halo64(fr_ctx *C, int l, const double *x, cudaStream_t s) {
+    return halo_impl<double>(C, l, x, 0, s, frk64_halo_pack, frk64_halo_unpack);
+}
+static int halo32(fr_ctx *C, int l, const float *x, cudaStream_t s) {
+    return halo_impl<float>(C, l, x, 1, s, frk32_halo_pack, frk32_halo_unpack);
+}
+
+// maxima or sums of n device doubles over the processes (in place; no-op alone)
+static int allreduce_dev(fr_ctx *C, double *dev, int n, int op, cudaStream_t s) {
+    if (!C->has_comm) return FR_OK;
+    double h[64];
+    if (n > 64) return fail(FR_ERR_INVALID_ARG, "allreduce of more than 64 values");
+    CK(cudaMemcpyAsync(h, dev, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (C->comm.allreduce(C->comm.user, h, n, op) != 0) return fail(FR_ERR_CUDA, "allreduce failed");
+    CK(cudaMemcpyAsync(dev, h, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return FR_OK;
+}
+
+extern "C" int fr_set_comm(fr_ctx *C, const fr_comm *m) {
+    if (!C) return fail(FR_ERR_INVALID_ARG, "NULL context");
+    if (!m) {
+        C->has_comm = 0;
+        C->ndof_rms = (double)C->L[0].ndof;
+        return FR_OK;
+    }
+    int nrecv = C->E - m->n_owned;
+    if (m->n_owned < 1 || m->n_owned > C->E || m->nsend < 0)
+        return fail(FR_ERR_INVALID_ARG, "n_owned must be 1..E and nsend >= 0");
+    if (!m->halo || !m->allreduce) return fail(FR_ERR_INVALID_ARG, "both callbacks are needed");
+    if ((m->nsend > 0 && (!m->send_idx || !m->send_buf)) || (nrecv > 0 && !m->recv_buf))
+        return fail(FR_ERR_INVALID_ARG, "send list or exchange buffers missing");
+    for (int i = 0; i < m->nsend; ++i)
+        if (m->send_idx[i] < 0 || m->send_idx[i] >= m->n_owned)
+            return fail(FR_ERR_INVALID_ARG, "send_idx[%d] = %d is not an owned element", i, m->send_idx[i]);
+    if (C->mbnk) return fail(FR_ERR_INVALID_ARG, "the matrix-based coarse smoother is not partitioned");
+    int *dev = nullptr;
+    TRY(dalloc_t(C, &dev, (size_t)(m->nsend > 0 ? m->nsend : 1)));
+    if (m->nsend > 0) CK(cudaMemcpy(dev, m->send_idx, sizeof(int) * m->nsend, cudaMemcpyHostToDevice));
+    if (C->send_idx_dev) dfree(C, C->send_idx_dev);
+    C->send_idx_dev = dev;
+    C->comm = *m;
+    C->comm.send_idx = nullptr;
+    if (m->n_owned_total < m->n_owned) return fail(FR_ERR_INVALID_ARG, "n_owned_total below n_owned");
+    C->ndof_rms = (double)C->L[0].nv * C->L[0].np * (double)m->n_owned_total;
+    C->has_comm = 1;
     return FR_OK;
 }
 
@@ -585,7 +675,7 @@ int elem_blocks_t<double>(fr_ctx *C, int l, const double *q, double shift, doubl
     for (int col = 0; col < C->ncolor; ++col)
         for (int j = 0; j < L.nd; ++j) {
             Kn<T>::perturb(L, C->color, col, j, q, P.blk_qp, Kn<T>::epsrel, s);
-            TRY(residual_t<T>(C, l, P.blk_qp, P.blk_Rp, s));
+            TRY(residual_t<T>(C, l, P.blk_qp, P.blk_Rp, s, false));
             Kn<T>::column(L, C->color, col, j, q, P.blk_R0, P.blk_Rp, shift, Kn<T>::epsrel, M, s);
             Kn<T>::restore(L, C->color, col, j, q, P.blk_qp, s);
         }
@@ -630,7 +720,7 @@ int elem_blocks_mbnk_t<double>(fr_ctx *C, int l, const double *q, double shift, 
     for (int col = 0; col < C->ncolor2; ++col)
         for (int j = 0; j < L.nd; ++j) {
             Kn<T>::perturb(L, C->color2, col, j, q, P.blk_qp, Kn<T>::epsrel, s);
-            TRY(residual_t<T>(C, l, P.blk_qp, P.blk_Rp, s));
+            TRY(residual_t<T>(C, l, P.blk_qp, P.blk_Rp, s, false));
             Kn<T>::column(L, C->color2, col, j, q, P.blk_R0, P.blk_Rp, shift, Kn<T>::epsrel, M, s);
             frmb_nbr_column(L.E, L.nd, nf, C->nbr, C->color2, col, j, q, P.blk_R0, P.blk_Rp, Kn<T>::epsrel, O, s);
             Kn<T>::restore(L, C->color2, col, j, q, P.blk_qp, s);
@@ -788,6 +878,8 @@ static int pmg_setup_(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, cuda
     C->pmg_c = o->c;
     C->pmg_ids = o->inv_dtau_star;
     C->pmg_prec = o->precision;
+    if (C->has_comm && o->coarse_smoother == 1)
+        return fail(FR_ERR_INVALID_ARG, "the matrix-based coarse smoother is not partitioned");
     C->mbnk = o->coarse_smoother == 1;
     C->mbnk_maxit = o->mbnk_maxit;
     C->mbnk_tol = o->mbnk_tol;
@@ -800,7 +892,10 @@ static int pmg_setup_(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, cuda
         TRY(pmg_alloc_t<float>(C, o->nlevels));
         long long n = C->L[0].ndof;
         if (!C->ymax) TRY(dalloc_t(C, &C->ymax, 5));
-        if (frk32_absmax_var(C->nv, n / C->nv, q_ref, C->ymax, s) != 0) return fail(FR_ERR_CUDA, "absmax");
+        int rc_m = C->has_comm ? frk32_absmax_var_owned(C->nv, C->L[0].np, C->E, C->comm.n_owned, q_ref, C->ymax, s)
+                               : frk32_absmax_var(C->nv, n / C->nv, q_ref, C->ymax, s);
+        if (rc_m != 0) return fail(FR_ERR_CUDA, "absmax");
+        TRY(allreduce_dev(C, C->ymax, C->nv, 1, s));
         CK(cudaMemcpyAsync(C->pmg_qref, C->ymax, sizeof(double) * C->nv, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         // per-variable magnitudes of the reference state, floored at 1e-3 of the largest
@@ -953,7 +1048,10 @@ static int pmg_apply(fr_ctx *C, const double *q, const double *Rq, const double 
         return FR_OK;
     }
     PmgBuf<float> &P = C->p32;
-    if (frk32_absmax(n, X, C->xmax, s) != 0) return fail(FR_ERR_CUDA, "absmax");
+    int rc_x = C->has_comm ? frk32_absmax_owned(n / C->E, C->E, C->comm.n_owned, X, C->xmax, s)
+                           : frk32_absmax(n, X, C->xmax, s);
+    if (rc_x != 0) return fail(FR_ERR_CUDA, "absmax");
+    TRY(allreduce_dev(C, C->xmax, 1, 1, s));
     if (C->q32_of != q) {
         frk32_d2f(n, q, C->q32, s);
         TRY(residual_t<float>(C, 0, C->q32, C->Rq32, s));
@@ -965,7 +1063,10 @@ static int pmg_apply(fr_ctx *C, const double *q, const double *Rq, const double 
         frk32_copy(n, C->q32, P.qh[0], s);
         TRY(vcycle_t<float>(C, 0, C->q32, C->Rq32, C->x32, P.qh[0], s));
         frk32_sub(n, P.qh[0], C->q32, C->y32, s);
-        if (frk32_absmax_var_f(C->nv, n / C->nv, C->y32, C->ymax, s) != 0) return fail(FR_ERR_CUDA, "absmax");
+        int rc_y = C->has_comm ? frk32_absmax_var_owned_f(C->nv, C->L[0].np, C->E, C->comm.n_owned, C->y32, C->ymax, s)
+                               : frk32_absmax_var_f(C->nv, n / C->nv, C->y32, C->ymax, s);
+        if (rc_y != 0) return fail(FR_ERR_CUDA, "absmax");
+        TRY(allreduce_dev(C, C->ymax, C->nv, 1, s));
         double yv[5], ym = 0.0;
         CK(cudaMemcpyAsync(yv, C->ymax, sizeof(double) * C->nv, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -987,11 +1088,18 @@ extern "C" int pmg_precondition(fr_ctx *C, const double *q, const double *Rq, co
 }
 
 // ------------------------------------------------------------------------ FGMRES
+// w . V_j on the finest level's [nv Np][E] vectors: over the owned elements, summed over
+// the processes; the sums are left in C->dots on the device too (CGS2 reads them there)
 static int dots(fr_ctx *C, long long n, int m, const double *w, const double *const *V, double *host, cudaStream_t s) {
-    if (frk64_multidot(n, m, w, V, C->dots, s) != 0) return fail(FR_ERR_OOM, "reduction scratch");
+    long long E = C->E, rows = n / E, own = C->has_comm ? C->comm.n_owned : E;
+    if (frk64_multidot(rows, E, own, m, w, V, C->dots, C->partial, s) != 0) return fail(FR_ERR_OOM, "reduction");
     CKLAUNCH();
     CK(cudaMemcpyAsync(host, C->dots, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (C->has_comm) {
+        if (C->comm.allreduce(C->comm.user, host, m, 0) != 0) return fail(FR_ERR_CUDA, "allreduce failed");
+        CK(cudaMemcpyAsync(C->dots, host, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    }
     return FR_OK;
 }
 static int norm2(fr_ctx *C, long long n, const double *w, double *out, cudaStream_t s) {
@@ -1050,7 +1158,7 @@ static int gmres_(fr_ctx *C, const double *q, const double *Rq, const double *b,
     if (!isfinite(bnorm)) return fail(FR_ERR_NONFINITE, "non-finite right-hand side");
     std::vector<const double *> Zp(K);
     for (;;) {
-        frk64_div_scalar(n, r, beta, C->V[0], s);
+        frk64_scale(n, 1.0 / beta, r, C->V[0], s);   // FP64 division is slow: one reciprocal
         for (int j = 0; j <= K; ++j) g[j] = 0.0;
         g[0] = beta;
         int jj = 0;
@@ -1062,7 +1170,7 @@ static int gmres_(fr_ctx *C, const double *q, const double *Rq, const double *b,
                 double zn;
                 TRY(norm2(C, n, C->Z[j], &zn, s));
                 if (!(zn > 0.0) || !isfinite(zn)) return fail(FR_ERR_NONFINITE, "preconditioner output norm %g", zn);
-                frk64_div_scalar(n, C->Z[j], zn, C->Z[j], s);
+                frk64_scale(n, 1.0 / zn, C->Z[j], C->Z[j], s);
                 zj = C->Z[j];
             } else {
                 zj = C->V[j];
@@ -1080,7 +1188,7 @@ static int gmres_(fr_ctx *C, const double *q, const double *Rq, const double *b,
             TRY(norm2(C, n, w, &hn, s));
             if (!isfinite(hn)) return fail(FR_ERR_NONFINITE, "non-finite Arnoldi vector");
             H[(size_t)(j + 1) * K + j] = hn;
-            if (hn > 0.0) frk64_div_scalar(n, w, hn, C->V[j + 1], s);
+            if (hn > 0.0) frk64_scale(n, 1.0 / hn, w, C->V[j + 1], s);
             for (int i = 0; i < j; ++i) {
                 double a = H[(size_t)i * K + j], bb = H[(size_t)(i + 1) * K + j];
                 H[(size_t)i * K + j] = cs[i] * a + sn[i] * bb;
@@ -1107,7 +1215,7 @@ static int gmres_(fr_ctx *C, const double *q, const double *Rq, const double *b,
         double xn;
         TRY(norm2(C, n, x, &xn, s));
         if (xn > 0.0) {
-            frk64_div_scalar(n, x, xn, r, s);
+            frk64_scale(n, 1.0 / xn, x, r, s);
             TRY(jvp(C, q, Rq, r, o->eps, o->shift, w, s));
             frk64_scale(n, xn, w, C->gtmp, s);
             frk64_sub(n, b, C->gtmp, r, s);
@@ -1257,7 +1365,7 @@ static int stage_rms(fr_ctx *C, const double *qc, const double *sv, double adt, 
     frk64_stage_F(n, qc, sv, adt, C->Rtmp, C->Ftmp, s);
     double fn;
     TRY(norm2(C, n, C->Ftmp, &fn, s));
-    *rms = fabs(adt) * fn / sqrt((double)n);
+    *rms = fabs(adt) * fn / sqrt(C->ndof_rms);
     if (!isfinite(*rms)) *rms = INFINITY;
     return FR_OK;
 }
@@ -1300,6 +1408,8 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
     TRY(check_solve_opts(C, o));
     if (o->guess < 0 || o->guess > 2) return fail(FR_ERR_INVALID_ARG, "guess must be 0, 1 or 2");
     if ((o->guess == 2 || o->train_iters > 0) && !C->mlp) return fail(FR_ERR_NOT_READY, "no network attached (fr_set_mlp)");
+    if ((o->guess == 2 || o->train_iters > 0) && C->has_comm)
+        return fail(FR_ERR_INVALID_ARG, "the network guess is not partitioned (its feature scales sum over all elements)");
     cudaStream_t s = S_(stream);
     int ns = tab->stages;
     TRY(stepper_alloc(C, ns + 5));
@@ -1398,7 +1508,7 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
             frk64_stage_F(n, q, sv, adt, Rk, F, s);
             double fn;
             TRY(norm2(C, n, F, &fn, s));
-            res = fabs(adt) * fn / sqrt((double)n);
+            res = fabs(adt) * fn / sqrt(C->ndof_rms);
             if (!isfinite(res)) return fail(FR_ERR_NONFINITE, "non-finite stage residual (stage %d, iteration %d)", i, k);
             if (res <= o->tol_newton) { conv = 1; break; }
             if (k == o->max_ptc) break;

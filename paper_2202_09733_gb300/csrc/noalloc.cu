@@ -35,6 +35,7 @@ static std::mutex g_scratch_mutex;
 // access to the context's level data (defined in lib.cu)
 extern "C++" int fr_internal_level(const fr_ctx *ctx, int level, FrLevel *out, FrPhysH *ph);
 extern "C++" int fr_internal_fail(int code, const char *msg);
+extern "C++" int fr_internal_has_comm(const fr_ctx *ctx);
 
 static size_t align_doubles(size_t n) { return (n + 31) & ~(size_t)31; }   // 256-byte multiples
 
@@ -43,6 +44,8 @@ extern "C" int fr_residual_noalloc(fr_ctx *ctx, int level, const double *q, doub
     FrPhysH ph;
     if (!ctx || !q || !R) return fr_internal_fail(FR_ERR_INVALID_ARG, "fr_residual_noalloc: NULL argument");
     if (q == R) return fr_internal_fail(FR_ERR_INVALID_ARG, "fr_residual_noalloc: q and R must not alias");
+    if (fr_internal_has_comm(ctx))
+        return fr_internal_fail(FR_ERR_INVALID_ARG, "fr_residual_noalloc: not with an element partition (fr_set_comm)");
     if (fr_internal_level(ctx, level, &L, &ph) != FR_OK)
         return fr_internal_fail(FR_ERR_INVALID_ARG, "fr_residual_noalloc: bad level");
     size_t E = (size_t)L.E;
