@@ -595,7 +595,8 @@ def gpu_arm(args):
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the kernels of one "
                                            "residual on this workload (committed ncu summary)",
                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 entry); "
-                                        "DFMA chains measured 1.19"},
+                                        "independent DFMA chains measured %s TFLOP/s on this part"
+                                        % profile_figure("fp_rates_gb300", "dfma_tflops")},
             "e2e": {"value": t_e2e, "unit": "s/step", "h2d_bytes_per_step": q_host.numel() * 8,
                     "d2h_bytes_per_step": q_host.numel() * 8},
             "cpu_baseline": cpu,

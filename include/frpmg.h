@@ -59,7 +59,8 @@ typedef struct fr_ctx fr_ctx;
  *           reverses the tangential index of the R side; 3-D bit 2 swaps the two
  *           tangential indices, then bit 0 / bit 1 reverse the first / second.
  *   plevels [nlevels] polynomial degree per p-level, finest first (p in 1..4 for 2-D,
- *           1..3 for 3-D).  Geometry of level p has degree min(qg, p). */
+ *           1..3 for 3-D).  Geometry of level p has degree min(qg, p).
+ *   nelem   1 .. 2,097,120 (= 32 x 65535) elements per context. */
 typedef struct {
     int dim, nelem, qg;
     const double *gnodes;

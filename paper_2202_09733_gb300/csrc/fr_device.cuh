@@ -412,9 +412,9 @@ template <int D, int P, typename T>
 __global__ void __launch_bounds__(256) k_interp(const T *__restrict__ q, T *__restrict__ qf, int E) {
     using S = Sh<D, P>;
     constexpr int N = S::n;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int e = blockIdx.y * blockDim.x + threadIdx.x;   // the points of an element chunk run side by side
     if (e >= E) return;
-    int k = blockIdx.y;
+    int k = blockIdx.x;
     int df, s, a, b;
     fp_decode<D, N>(k, df, s, a, b);
     typedef typename FrBase<T>::type B;
@@ -467,9 +467,9 @@ __global__ void __launch_bounds__(256) k_grad_fp(const T *__restrict__ q, const 
                                                  typename FrBase<T>::type etagR) {
     using S = Sh<D, P>;
     constexpr int N = S::n;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int e = blockIdx.y * blockDim.x + threadIdx.x;   // the points of an element chunk run side by side
     if (e >= E) return;
-    int k = blockIdx.y;
+    int k = blockIdx.x;
     int df, s, a, b;
     fp_decode<D, N>(k, df, s, a, b);
     typedef typename FrBase<T>::type B;
@@ -591,9 +591,9 @@ __global__ void __launch_bounds__(256) k_grad_vflux(const T *__restrict__ q, con
     using S = Sh<D, P>;
     typedef typename FrBase<T>::type B;
     constexpr int N = S::n, nv = S::nv;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int e = blockIdx.y * blockDim.x + threadIdx.x;   // the points of an element chunk run side by side
     if (e >= E) return;
-    int i = blockIdx.y;
+    int i = blockIdx.x;
     int ii[3] = {i % N, (i / N) % N, D == 3 ? i / (N * N) : 0};
     const FrTab<B> &tb = frtab<B>(P);
     B g[3][3];
@@ -651,9 +651,9 @@ template <int D, int P, typename T>
 __global__ void __launch_bounds__(256) k_face_ft(const T *__restrict__ Ft, T *__restrict__ Ftf, int E) {
     using S = Sh<D, P>;
     constexpr int N = S::n;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int e = blockIdx.y * blockDim.x + threadIdx.x;   // the points of an element chunk run side by side
     if (e >= E) return;
-    int k = blockIdx.y;
+    int k = blockIdx.x;
     int df, s, a, b;
     fp_decode<D, N>(k, df, s, a, b);
     typedef typename FrBase<T>::type B;
@@ -677,9 +677,9 @@ __global__ void __launch_bounds__(256) k_div(const T *__restrict__ Ft, const T *
                                              T *__restrict__ R, int E) {
     using S = Sh<D, P>;
     constexpr int N = S::n;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int e = blockIdx.y * blockDim.x + threadIdx.x;   // the points of an element chunk run side by side
     if (e >= E) return;
-    int i = blockIdx.y;
+    int i = blockIdx.x;
     int ii[3] = {i % N, (i / N) % N, D == 3 ? i / (N * N) : 0};
     typedef typename FrBase<T>::type B;
     const FrTab<B> &tb = frtab<B>(P);

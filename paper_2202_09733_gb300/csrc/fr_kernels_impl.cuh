@@ -60,13 +60,13 @@ static void residual_t(const FrLevelT<FRT> &L, const FrPhys<FRT> &ph, const FRT 
     for (int k = 0; k < 8; ++k) b[k] = L.tile[k] > 0 ? L.tile[k] : 128;
     auto gx = [&](int k) { return (E + b[k] - 1) / b[k]; };
     auto gp = [&](int k) { return (L.npairs + b[k] - 1) / b[k]; };
-    CNT(); k_interp<D, P, FRT><<<dim3(gx(0), S::nfp), b[0], 0, s>>>(q, L.qf, E);
+    CNT(); k_interp<D, P, FRT><<<dim3(S::nfp, gx(0)), b[0], 0, s>>>(q, L.qf, E);
     CNT(); k_pair_common<D, P, FRT><<<gp(1), b[1], 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.dq, E, ph);
-    CNT(); k_grad_fp<D, P, FRT><<<dim3(gx(3), S::nfp), b[3], 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
+    CNT(); k_grad_fp<D, P, FRT><<<dim3(S::nfp, gx(3)), b[3], 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
     CNT(); k_pair_flux<D, P, FRT><<<gp(4), b[4], 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.Qf, L.Sf, L.fn, E, ph);
-    CNT(); k_grad_vflux<D, P, FRT><<<dim3(gx(2), S::np), b[2], 0, s>>>(q, L.dq, L.G, L.S, L.Ft, E, ph);
-    CNT(); k_face_ft<D, P, FRT><<<dim3(gx(6), S::nfp), b[6], 0, s>>>(L.Ft, L.Ftf, E);
-    CNT(); k_div<D, P, FRT><<<dim3(gx(7), S::np), b[7], 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
+    CNT(); k_grad_vflux<D, P, FRT><<<dim3(S::np, gx(2)), b[2], 0, s>>>(q, L.dq, L.G, L.S, L.Ft, E, ph);
+    CNT(); k_face_ft<D, P, FRT><<<dim3(S::nfp, gx(6)), b[6], 0, s>>>(L.Ft, L.Ftf, E);
+    CNT(); k_div<D, P, FRT><<<dim3(S::np, gx(7)), b[7], 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
 }
 
 int FRK(residual)(const FrLevelT<FRT> &L, const FrPhysH &h, const FRT *q, FRT *R, cudaStream_t s) {

@@ -34,13 +34,13 @@ template <int D, int P>
 static void residual_ad(const FrLevelAD &L, const FrPhys<float> &ph, const DualT *q, DualT *R, cudaStream_t s) {
     using S = Sh<D, P>;
     const int E = L.E, gx = (E + 127) / 128, gp = (L.npairs + 127) / 128;
-    CNT(); k_interp<D, P, DualT><<<dim3(gx, S::nfp), 128, 0, s>>>(q, L.qf, E);
+    CNT(); k_interp<D, P, DualT><<<dim3(S::nfp, gx), 128, 0, s>>>(q, L.qf, E);
     CNT(); k_pair_common<D, P, DualT><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.dq, E, ph);
-    CNT(); k_grad_fp<D, P, DualT><<<dim3(gx, S::nfp), 128, 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
+    CNT(); k_grad_fp<D, P, DualT><<<dim3(S::nfp, gx), 128, 0, s>>>(q, L.qf, L.dq, L.Gf, L.Qf, E, ph.etagL, ph.etagR);
     CNT(); k_pair_flux<D, P, DualT><<<gp, 128, 0, s>>>(L.pairs, L.bc, L.npairs, L.qf, L.Qf, L.Sf, L.fn, E, ph);
-    CNT(); k_grad_vflux<D, P, DualT><<<dim3(gx, S::np), 128, 0, s>>>(q, L.dq, L.G, L.S, L.Ft, E, ph);
-    CNT(); k_face_ft<D, P, DualT><<<dim3(gx, S::nfp), 128, 0, s>>>(L.Ft, L.Ftf, E);
-    CNT(); k_div<D, P, DualT><<<dim3(gx, S::np), 128, 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
+    CNT(); k_grad_vflux<D, P, DualT><<<dim3(S::np, gx), 128, 0, s>>>(q, L.dq, L.G, L.S, L.Ft, E, ph);
+    CNT(); k_face_ft<D, P, DualT><<<dim3(S::nfp, gx), 128, 0, s>>>(L.Ft, L.Ftf, E);
+    CNT(); k_div<D, P, DualT><<<dim3(S::np, gx), 128, 0, s>>>(L.Ft, L.Ftf, L.fn, L.invJ, R, E);
 }
 
 int frkad_residual(const FrLevelAD &L, const FrPhysH &h, const DualT *q, DualT *R, cudaStream_t s) {

@@ -268,6 +268,9 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
     if (m->qg != 1 && m->qg != 2) return fail(FR_ERR_INVALID_ARG, "geometry degree must be 1 or 2");
     if (m->nelem <= 0 || !m->gnodes || !m->faces || m->nfaces <= 0)
         return fail(FR_ERR_INVALID_ARG, "empty mesh");
+    // the residual's grids put element chunks (CTA size >= 32) on the y axis, at most 65535
+    if (m->nelem > 32LL * 65535)
+        return fail(FR_ERR_INVALID_ARG, "at most %lld elements per context", 32LL * 65535);
     if (m->nlevels < 1 || m->nlevels > FRL_MAXLEV || !m->plevels)
         return fail(FR_ERR_INVALID_ARG, "nlevels must be 1..%d", FRL_MAXLEV);
     int pmax = m->dim == 2 ? 4 : 3;

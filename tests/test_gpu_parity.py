@@ -352,11 +352,11 @@ def test_ptc_steady_converged_state():
     precisions level off between 1e-7 and 2e-7 (the march reaches the floor of the
     finite-difference products of Eq. 8 with the fixed eps: the FGMRES solves of the last
     pseudo steps are limited by it, and which side of 1e-7 a run lands on depends on the
-    rounding path of its inner products), so both GPU runs are held to 1e-6.  A 1e-7 drop
-    from ||R(q0)|| ~ 2e8 still leaves ||R|| ~ 20 on 2.6e-4-thick wall cells, so two
-    converged paths differ by ~1e-3 in the state: FP64 to 5e-3 of the oracle's state.
-    The mixed preconditioner's FP32 cycle stalls the march early and hands over to the
-    FP64 cycle; its state is held to 5e-2."""
+    rounding path of its inner products), so both GPU runs are held to 1e-6.  A 1e-6 drop
+    from ||R(q0)|| ~ 2e8 still leaves ||R|| ~ 200 on 2.6e-4-thick wall cells, so a run
+    stopped there differs from the oracle's 1e-7 state by up to ~1e-2 (measured 6.5e-3):
+    FP64 to 2e-2.  The mixed preconditioner's FP32 cycle stalls the march early and hands
+    over to the FP64 cycle; its state is held to 5e-2."""
     W = w.cylinder_steady(nr=6, nt=12, p=2, levels=[2, 1], mach=0.2, re=40)
     O = oracle.Oracle(W.mesh, W.phys, W.levels)
     G = api.fr_create(W.mesh, W.phys, W.levels)
@@ -365,7 +365,7 @@ def test_ptc_steady_converged_state():
     q_or, st_or = O.ptc_steady(W.q0, dtau0, 1e6, 1e-7, 80, oo)
     assert st_or["converged"]
     r0 = np.linalg.norm(O.residual(W.q0))
-    for prec, tol, state_tol in (("fp64", 1e-6, 5e-3), ("mixed", 1e-6, 5e-2)):
+    for prec, tol, state_tol in (("fp64", 1e-6, 2e-2), ("mixed", 1e-6, 5e-2)):
         go = api.solve_opts(kdim=30, maxit_gmres=60, nsmooth=(2, 2), tol_gmres=1e-3, inv_dtau_star=-1.0,
                             precision=prec)
         qg = dev(W.q0)
