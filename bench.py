@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ESDIRK3 initial-guess comparison (cylinder) and the batched step")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--lu-storage", default="fp32", choices=["fp32", "half"],
+                    help="mixed preconditioner: the smoother's block solves read FP32 factors or half-width ones")
     return ap.parse_args()
 
 
@@ -464,6 +466,7 @@ def gpu_arm(args):
     else:
         ctx = api.fr_create(W.mesh, W.phys, W.levels)
         q0 = torch.from_numpy(W.q0).cuda()
+    api.fr_set_lu_storage(ctx, args.lu_storage)
     q = q0.clone()
     g, a, c, m = T.ros34pw2()
     opts = api.solve_opts(kdim=30, maxit_gmres=300, nsmooth=(2, 2), tol_gmres=1e-6, inv_dtau_star=1.0 / W.dt,

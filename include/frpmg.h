@@ -172,6 +172,40 @@ int fr_block_factor(fr_ctx *ctx, int level, double *M, int *perm, void *stream);
 /* x <- M_e^{-1} x for every element using the factors of fr_block_factor.
  * x: device [nv][Np][E], overwritten. */
 int fr_block_solve(fr_ctx *ctx, int level, const double *M, const int *perm, double *x, void *stream);
+/* The same factorisation of FP32 blocks (those of fr_elem_blocks_f32, which the mixed
+ * preconditioner factors in pmg_setup): M device FP32, E nd^2 values column-major per
+ * element, factored in place (L, U, 1/u_kk as above); perm as above.  method 0: the
+ * tensor-core factorisation where the block size allows it (65 <= nd <= 384), else the
+ * CUDA-core kernels; 1: the CUDA-core kernels (FP32 fma, one block per CTA); 2: the
+ * tensor-core factorisation (FR_ERR_UNIMPLEMENTED outside 65..384).  The tensor-core path
+ * eliminates in 32-column panels with the same pivot rule; its trailing updates
+ * A22 - L21 U12 run as tcgen05 TF32 products of split operands (x = hi + lo, three
+ * products), which keeps them at FP32 accuracy, so its factors differ from method 1's
+ * by rounding only.  Synchronises the stream; FR_ERR_BREAKDOWN on a zero pivot;
+ * FR_ERR_CUDA if a bounded wait for the tensor cores ran out. */
+int fr_block_factor_f32(fr_ctx *ctx, int level, float *M, int *perm, int method, void *stream);
+/* x <- M_e^{-1} x with FP32 factors of fr_block_factor_f32; x device FP32 [nv][Np][E]. */
+int fr_block_solve_f32(fr_ctx *ctx, int level, const float *M, const int *perm, float *x, void *stream);
+/* the FP32 factorisation pmg_setup uses for the mixed preconditioner's blocks: 0 (the
+ * default) as method 0 above, 1 the CUDA-core kernels */
+int fr_set_lu_method(fr_ctx *ctx, int method);
+/* Factors stored at half width for the FP32 block solves (not in the paper: a storage
+ * format of the mixed preconditioner, which the block solves read once per smoothing step
+ * and which bound them by memory bandwidth).  From FP32 factors M (fr_block_factor_f32):
+ * H device binary16 [E][nd][nd] column-major, L below the diagonal (|l| <= 1), column k of
+ * U (rows < k) divided by its largest magnitude g_k (g_k = 1 for an all-zero column),
+ * 0 on the diagonal; dg device FP32 [E][nd][2] = (1/u_kk, g_k).  binary16 keeps 10
+ * mantissa bits (TF32's): entries carry a relative error up to 2^-11 (below 2^-14 of the
+ * column's scale, an absolute one up to 2^-25 of it). */
+int fr_block_to_half(fr_ctx *ctx, int level, const float *M, void *H, float *dg, void *stream);
+/* x <- M_e^{-1} x with the half-width factors (x device FP32 [nv][Np][E]); perm as from
+ * fr_block_factor_f32 */
+int fr_block_solve_half(fr_ctx *ctx, int level, const void *H, const float *dg, const int *perm, float *x,
+                        void *stream);
+/* 1: pmg_setup also stores the mixed preconditioner's FP32 factors at half width and the
+ * smoother's block solves read those (half the bytes per solve); 0 (the default): FP32
+ * factors.  Takes effect at the next pmg_setup. */
+int fr_set_lu_storage(fr_ctx *ctx, int half);
 
 /* Eqs. (17)-(18): L2 restriction level -> level+1 and prolongation level+1 -> level,
  * tensor-product 1-D operators applied along direction 0, 1, 2 in turn.  Device arrays. */
@@ -398,7 +432,9 @@ int fr_autotune_load(const char *path);
 /* bounded device-side waits that ran out since the last clear (bit 0: block-solve stage
  * barriers); such a kernel records the failure and returns instead of hanging.  Bit 1:
  * the bulk-copy block solve also gave up waiting for its own copies in flight, which may
- * then land in shared memory after its CTA exited: treat the device as unusable. */
+ * then land in shared memory after its CTA exited: treat the device as unusable.  Bit 2:
+ * a trailing update of the tensor-core LU gave up waiting for its products (its block's
+ * factors are then wrong). */
 int fr_kernel_timeouts(int clear);
 /* runs the time-out path of those waits on purpose (a barrier that nothing completes,
  * 4096 polls) so that callers can check that it reports through fr_kernel_timeouts and

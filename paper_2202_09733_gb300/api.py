@@ -172,6 +172,53 @@ def fr_block_solve(ctx, level, M, perm, x, stream=None):
     return x
 
 
+LU_METHODS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
+
+
+def fr_block_factor_f32(ctx, level, M, method="auto", perm=None, stream=None):
+    """In-place LU of FP32 blocks M [E, nd, nd] (column-major per element); method "auto"
+    (tensor cores where the block size allows), "cuda_cores" or "tensor_cores"."""
+    perm = torch.empty((ctx.E, ctx.nd(level)), dtype=torch.int32, device="cuda") if perm is None else perm
+    N.check(N.load().fr_block_factor_f32(ctx.handle, level, _dev(M, torch.float32, "M"), _dev(perm, torch.int32),
+                                         LU_METHODS[method], _stream(stream)), "fr_block_factor_f32")
+    return perm
+
+
+def fr_block_solve_f32(ctx, level, M, perm, x, stream=None):
+    N.check(N.load().fr_block_solve_f32(ctx.handle, level, _dev(M, torch.float32, "M"), _dev(perm, torch.int32),
+                                        _dev(x, torch.float32, "x"), _stream(stream)), "fr_block_solve_f32")
+    return x
+
+
+def fr_set_lu_method(ctx, method):
+    """The FP32 factorisation pmg_setup uses: "auto" (default) or "cuda_cores"."""
+    N.check(N.load().fr_set_lu_method(ctx.handle, {"auto": 0, "cuda_cores": 1}[method]), "fr_set_lu_method")
+
+
+def fr_block_to_half(ctx, level, M, stream=None):
+    """(H, dg): half-width copy of FP32 factors M [E, nd, nd]: H float16 [E, nd, nd]
+    (L, column-scaled U), dg float32 [E, nd, 2] = (1/u_kk, column scale)."""
+    E, nd = M.shape[0], M.shape[1]
+    H = torch.empty((E, nd, nd), dtype=torch.float16, device="cuda")
+    dg = torch.empty((E, nd, 2), dtype=torch.float32, device="cuda")
+    N.check(N.load().fr_block_to_half(ctx.handle, level, _dev(M, torch.float32, "M"), _dev(H, torch.float16, "H"),
+                                      _dev(dg, torch.float32, "dg"), _stream(stream)), "fr_block_to_half")
+    return H, dg
+
+
+def fr_block_solve_half(ctx, level, H, dg, perm, x, stream=None):
+    N.check(N.load().fr_block_solve_half(ctx.handle, level, _dev(H, torch.float16, "H"), _dev(dg, torch.float32, "dg"),
+                                         _dev(perm, torch.int32), _dev(x, torch.float32, "x"), _stream(stream)),
+            "fr_block_solve_half")
+    return x
+
+
+def fr_set_lu_storage(ctx, storage):
+    """How pmg_setup keeps the FP32 factors for the smoother's solves: "fp32" (default) or
+    "half" (binary16 entries with per-column scales, half the bytes per solve)."""
+    N.check(N.load().fr_set_lu_storage(ctx.handle, {"fp32": 0, "half": 1}[storage]), "fr_set_lu_storage")
+
+
 def fr_restrict(ctx, level, xf, xc=None, stream=None):
     xc = ctx.empty(level + 1) if xc is None else xc
     N.check(N.load().fr_restrict(ctx.handle, level, _dev(xf), _dev(xc), _stream(stream)), "fr_restrict")

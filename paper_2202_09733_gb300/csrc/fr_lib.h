@@ -114,6 +114,17 @@ void frk32_f2d_unscale_dev(long long n, const float *x, const double *xmax_dev, 
 void frk32_next_target(int nv, const double *ymax_dev, const double *qref_dev, double want, double *target_dev,
                        cudaStream_t s);
 
+// tensor-core LU of FP32 element blocks (lu_tc.cu): supported block sizes, the factor
+// (same layout and permutation as P##_lu_factor), its time-out flag (4 if set)
+unsigned long long frktc_launch_count();
+int frktc_lu_supported(int nd);
+int frktc_lu_factor(int E, int nd, float *M, int *perm, int *info, cudaStream_t s);
+int frktc_lu_error(int clear);
+// half-width factors for the solves: binary16 L and column-scaled U, per column (1/u_kk, g_k)
+int frktc_lu_to_half(int E, int nd, const float *M, void *H, float *dg, cudaStream_t s);
+int frktc_lu_solve_half(int E, int nd, int g, const void *H, const float *dg, const int *perm, float *x,
+                        cudaStream_t s);
+
 // segmented vector kernels of the batched solver (batch_kernels.cu)
 unsigned long long frkb_launch_count();
 int frkb_segdots(int rows, int E, int nitems, const int4 *items, int nprob, const int *item_off, const double *w,

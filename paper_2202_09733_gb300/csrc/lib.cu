@@ -87,6 +87,12 @@ struct PmgBuf {
     // blocks, Krylov basis (FRMB_MAXIT + 1 vectors), two work vectors; capacities in T
     T *Md, *O, *V, *mz, *mw;
     size_t Md_cap, O_cap, V_cap, w_cap;
+    // FP32 factors also stored at half width for the solves (binary16 entries, per-column
+    // (1/u_kk, g_k) in FP32) when the context asks for it; half_ok[l]: current for M[l]
+    void *H[FRL_MAXLEV];
+    float *dg[FRL_MAXLEV];
+    size_t H_cap[FRL_MAXLEV];
+    int half_ok[FRL_MAXLEV];
 };
 
 struct fr_ctx {
@@ -102,6 +108,8 @@ struct fr_ctx {
     int *color;
     int self_face;                // a face joins an element to itself (periodic, one element wide)
     int ad_method;                // FP32 blocks: 0 element by element, 1 whole-level colours
+    int lu_method;                // FP32 LU: 0 tensor cores where the block size allows, 1 CUDA cores
+    int lu_half;                  // FP32 block solves from half-width factors (pmg_setup converts)
     float *ad_nt;                 // element-local FP32 blocks: the other sides' frozen face data
     signed char *ad_bck;          //   and the boundary code of every element face point
     int ncolor2;
@@ -180,7 +188,7 @@ static std::atomic<unsigned long long> g_capture_kernels{0};  // launch-counter 
 
 extern "C" unsigned long long fr_kernel_launches(void) {
     return frk64_launch_count() + frk32_launch_count() + frkad_launch_count() + frkmlp_launch_count() +
-           frkb_launch_count() + frmb_launch_count() - g_capture_kernels + g_graph_kernels;
+           frkb_launch_count() + frmb_launch_count() + frktc_launch_count() - g_capture_kernels + g_graph_kernels;
 }
 
 // ---------------------------------------------------------------- context set-up
@@ -335,7 +343,7 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
 }
 
 extern "C" int fr_kernel_timeouts(int clear) {
-    return frk64_lu_solve_error(clear) | frk32_lu_solve_error(clear);
+    return frk64_lu_solve_error(clear) | frk32_lu_solve_error(clear) | frktc_lu_error(clear);
 }
 
 extern "C" int fr_selftest_wait_timeout(void) {
@@ -748,10 +756,55 @@ extern "C" int fr_elem_blocks(fr_ctx *C, int l, const double *q, double shift, d
     return elem_blocks_t<double>(C, l, q, shift, M, S_(stream));
 }
 
+// FP32 blocks go to the tensor-core factorisation where its block size allows it and the
+// context's LU method is 0; FP64 blocks always take the CUDA-core kernels (their fma
+// order is the oracle's)
+static bool use_tc_lu(fr_ctx *C, int l, const float *) { return C->lu_method == 0 && frktc_lu_supported(C->L32[l].nd); }
+static bool use_tc_lu(fr_ctx *, int, const double *) { return false; }
+static void tc_factor(fr_ctx *C, int l, float *M, int *perm, cudaStream_t s) {
+    frktc_lu_factor(C->L32[l].E, C->L32[l].nd, M, perm, C->info, s);
+}
+static void tc_factor(fr_ctx *, int, double *, int *, cudaStream_t) {}
+
+// half-width copy of level l's FP32 factors for the solves (FP64 factors: nothing)
+static int half_factors(fr_ctx *C, int l, const float *M, cudaStream_t s) {
+    PmgBuf<float> &P = C->p32;
+    P.half_ok[l] = 0;
+    if (!C->lu_half) return FR_OK;
+    const FrLevel32 &L = C->L32[l];
+    size_t need = (size_t)L.E * L.nd * L.nd;
+    if (!P.H[l] || P.H_cap[l] < need) {
+        dfree(C, P.H[l]);
+        dfree(C, P.dg[l]);
+        P.H[l] = nullptr; P.dg[l] = nullptr; P.H_cap[l] = 0;
+        TRY(dalloc(C, &P.H[l], 2 * need));
+        TRY(dalloc_t(C, &P.dg[l], (size_t)2 * L.E * L.nd));
+        P.H_cap[l] = need;
+    }
+    frktc_lu_to_half(L.E, L.nd, M, P.H[l], P.dg[l], s);
+    P.half_ok[l] = 1;
+    return FR_OK;
+}
+static int half_factors(fr_ctx *, int, const double *, cudaStream_t) { return FR_OK; }
+// the block solve of the smoother on level l with the factors pmg_setup stored
+static int smoother_solve(fr_ctx *C, int l, float *x, cudaStream_t s) {
+    PmgBuf<float> &P = C->p32;
+    const FrLevel32 &L = C->L32[l];
+    if (P.half_ok[l]) return frktc_lu_solve_half(L.E, L.nd, L.lu_g, P.H[l], P.dg[l], P.perm[l], x, s) == 0
+                                 ? FR_OK : fail(FR_ERR_UNIMPLEMENTED, "block size %d", L.nd);
+    return Kn<float>::solve(L, P.M[l], P.perm[l], x, s) == 0 ? FR_OK : fail(FR_ERR_UNIMPLEMENTED, "block size %d", L.nd);
+}
+static int smoother_solve(fr_ctx *C, int l, double *x, cudaStream_t s) {
+    PmgBuf<double> &P = C->p64;
+    return Kn<double>::solve(C->L[l], P.M[l], P.perm[l], x, s) == 0 ? FR_OK
+                                                                       : fail(FR_ERR_UNIMPLEMENTED, "block size %d", C->L[l].nd);
+}
+
 template <typename T>
 static int block_factor_t(fr_ctx *C, int l, T *M, int *perm, cudaStream_t s) {
     CK(cudaMemsetAsync(C->info, 0, sizeof(int), s));
-    Kn<T>::factor(levels<T>(C)[l], M, perm, C->info, s);
+    if (use_tc_lu(C, l, M)) tc_factor(C, l, M, perm, s);
+    else Kn<T>::factor(levels<T>(C)[l], M, perm, C->info, s);
     CKLAUNCH();
     return FR_OK;
 }
@@ -764,6 +817,67 @@ extern "C" int fr_block_factor(fr_ctx *C, int l, double *M, int *perm, void *str
     CK(cudaMemcpyAsync(&info, C->info, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (info) return fail(FR_ERR_BREAKDOWN, "zero pivot in an element block");
+    return FR_OK;
+}
+
+extern "C" int fr_set_lu_method(fr_ctx *C, int method) {
+    if (!C || method < 0 || method > 1) return fail(FR_ERR_INVALID_ARG, "method must be 0 or 1");
+    C->lu_method = method;
+    return FR_OK;
+}
+
+extern "C" int fr_set_lu_storage(fr_ctx *C, int half) {
+    if (!C || half < 0 || half > 1) return fail(FR_ERR_INVALID_ARG, "half must be 0 or 1");
+    C->lu_half = half;
+    return FR_OK;
+}
+
+extern "C" int fr_block_to_half(fr_ctx *C, int l, const float *M, void *H, float *dg, void *stream) {
+    if (!C || l < 0 || l >= C->nlev || !M || !H || !dg) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    TRY(ensure_levels32(C));
+    frktc_lu_to_half(C->L32[l].E, C->L32[l].nd, M, H, dg, S_(stream));
+    CKLAUNCH();
+    return FR_OK;
+}
+
+extern "C" int fr_block_solve_half(fr_ctx *C, int l, const void *H, const float *dg, const int *perm, float *x,
+                                   void *stream) {
+    if (!C || l < 0 || l >= C->nlev || !H || !dg || !perm || !x) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    TRY(ensure_levels32(C));
+    const FrLevel32 &L = C->L32[l];
+    if (frktc_lu_solve_half(L.E, L.nd, L.lu_g, H, dg, perm, x, S_(stream)) != 0)
+        return fail(FR_ERR_UNIMPLEMENTED, "block size %d", L.nd);
+    CKLAUNCH();
+    return FR_OK;
+}
+
+extern "C" int fr_block_factor_f32(fr_ctx *C, int l, float *M, int *perm, int method, void *stream) {
+    if (!C || l < 0 || l >= C->nlev || !M || !perm) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    if (method < 0 || method > 2) return fail(FR_ERR_INVALID_ARG, "method must be 0, 1 or 2");
+    TRY(ensure_levels32(C));
+    cudaStream_t s = S_(stream);
+    const FrLevel32 &L = C->L32[l];
+    bool tc = method == 2 || (method == 0 && frktc_lu_supported(L.nd));
+    if (tc && !frktc_lu_supported(L.nd))
+        return fail(FR_ERR_UNIMPLEMENTED, "tensor-core LU: block size %d outside 65..384", L.nd);
+    CK(cudaMemsetAsync(C->info, 0, sizeof(int), s));
+    if (tc) frktc_lu_factor(L.E, L.nd, M, perm, C->info, s);
+    else frk32_lu_factor(L, M, perm, C->info, s);
+    CKLAUNCH();
+    int info = 0;
+    CK(cudaMemcpyAsync(&info, C->info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (frktc_lu_error(1)) return fail(FR_ERR_CUDA, "tensor-core LU: a wait for the tensor cores ran out");
+    if (info) return fail(FR_ERR_BREAKDOWN, "zero pivot in an element block");
+    return FR_OK;
+}
+
+extern "C" int fr_block_solve_f32(fr_ctx *C, int l, const float *M, const int *perm, float *x, void *stream) {
+    if (!C || l < 0 || l >= C->nlev || !M || !perm || !x) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    TRY(ensure_levels32(C));
+    if (frk32_lu_solve(C->L32[l], M, perm, x, S_(stream)) != 0)
+        return fail(FR_ERR_UNIMPLEMENTED, "block size %d", C->L32[l].nd);
+    CKLAUNCH();
     return FR_OK;
 }
 
@@ -869,6 +983,7 @@ static int pmg_factor_levels(fr_ctx *C, const T *q_ref, const fr_pmg_opts *o, cu
             TRY(elem_blocks_t<T>(C, l, qr, shift, P.M[l], s));
         }
         TRY(block_factor_t<T>(C, l, P.M[l], P.perm[l], s));
+        TRY(half_factors(C, l, P.M[l], s));
     }
     return FR_OK;
 }
@@ -946,13 +1061,13 @@ static int mbnk_solve_t(fr_ctx *C, int l, T *x, cudaStream_t s) {
     frmb_start(N, x, P.V, C->mb_partial, C->mb_gm, s);
     for (int k = 0; k < m; ++k) {
         Kn<T>::copy(N, P.V + (size_t)k * N, P.mz, s);
-        TRY(Kn<T>::solve(L, P.M[l], P.perm[l], P.mz, s));
+        TRY(smoother_solve(C, l, P.mz, s));
         frmb_bsr_mv(L.E, L.nd, nf, C->nbr, P.Md, P.O, P.mz, P.mw, s);
         frmb_arnoldi(N, m, k, P.V, P.mw, C->mb_partial, C->mb_gm, s);
     }
     frmb_small_solve(m, C->mbnk_tol, C->mb_gm, s);
     frmb_combine(N, m, P.V, C->mb_gm, x, s);
-    TRY(Kn<T>::solve(L, P.M[l], P.perm[l], x, s));
+    TRY(smoother_solve(C, l, x, s));
     return FR_OK;
 }
 
@@ -992,7 +1107,7 @@ static int smooth_t(fr_ctx *C, int l, int nsteps, const T *b, const T *Rb, const
             Kn<T>::pmg_rhs(L.ndof, C->pmg_c, d, qh, b, P.Rqh[l], Rb, P.rhs[l], s);
         }
         if (C->mbnk && l == C->pmg_nlev - 1) TRY(mbnk_solve_t<T>(C, l, P.rhs[l], s));
-        else Kn<T>::solve(L, P.M[l], P.perm[l], P.rhs[l], s);
+        else TRY(smoother_solve(C, l, P.rhs[l], s));
         Kn<T>::add(L.ndof, qh, P.rhs[l], qh, s);
     }
     CKLAUNCH();
