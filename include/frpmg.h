@@ -192,9 +192,10 @@ int fr_set_lu_method(fr_ctx *ctx, int method);
 /* Factors stored at half width for the FP32 block solves (not in the paper: a storage
  * format of the mixed preconditioner, which the block solves read once per smoothing step
  * and which bound them by memory bandwidth).  From FP32 factors M (fr_block_factor_f32):
- * H device binary16 [E][nd][nd] column-major, L below the diagonal (|l| <= 1), column k of
- * U (rows < k) divided by its largest magnitude g_k (g_k = 1 for an all-zero column),
- * 0 on the diagonal; dg device FP32 [E][nd][2] = (1/u_kk, g_k).  binary16 keeps 10
+ * H device binary16 [E][nd][ldh] column-major with ldh = nd rounded up to even (column k
+ * at H + (e nd + k) ldh; the pad row is 0), L below the diagonal (|l| <= 1), column k of U
+ * (rows < k) divided by its largest magnitude g_k (g_k = 1 for an all-zero column), 0 on
+ * the diagonal; dg device FP32 [E][nd][2] = (1/u_kk, g_k).  binary16 keeps 10
  * mantissa bits (TF32's): entries carry a relative error up to 2^-11 (below 2^-14 of the
  * column's scale, an absolute one up to 2^-25 of it). */
 int fr_block_to_half(fr_ctx *ctx, int level, const float *M, void *H, float *dg, void *stream);
@@ -433,8 +434,9 @@ int fr_autotune_load(const char *path);
  * barriers); such a kernel records the failure and returns instead of hanging.  Bit 1:
  * the bulk-copy block solve also gave up waiting for its own copies in flight, which may
  * then land in shared memory after its CTA exited: treat the device as unusable.  Bit 2:
- * a trailing update of the tensor-core LU gave up waiting for its products (its block's
- * factors are then wrong). */
+ * a trailing update of the tensor-core LU gave up waiting for its operand copy or its
+ * products (its block's factors are then wrong); if it also gave up waiting for the copy
+ * to drain, bit 1 is set as well. */
 int fr_kernel_timeouts(int clear);
 /* runs the time-out path of those waits on purpose (a barrier that nothing completes,
  * 4096 polls) so that callers can check that it reports through fr_kernel_timeouts and

@@ -196,10 +196,11 @@ def fr_set_lu_method(ctx, method):
 
 
 def fr_block_to_half(ctx, level, M, stream=None):
-    """(H, dg): half-width copy of FP32 factors M [E, nd, nd]: H float16 [E, nd, nd]
-    (L, column-scaled U), dg float32 [E, nd, 2] = (1/u_kk, column scale)."""
+    """(H, dg): half-width copy of FP32 factors M [E, nd, nd]: H float16 [E, nd, ldh]
+    (column k of L and column-scaled U in H[e, k, :nd], ldh = nd rounded up to even), dg
+    float32 [E, nd, 2] = (1/u_kk, column scale)."""
     E, nd = M.shape[0], M.shape[1]
-    H = torch.empty((E, nd, nd), dtype=torch.float16, device="cuda")
+    H = torch.empty((E, nd, (nd + 1) // 2 * 2), dtype=torch.float16, device="cuda")
     dg = torch.empty((E, nd, 2), dtype=torch.float32, device="cuda")
     N.check(N.load().fr_block_to_half(ctx.handle, level, _dev(M, torch.float32, "M"), _dev(H, torch.float16, "H"),
                                       _dev(dg, torch.float32, "dg"), _stream(stream)), "fr_block_to_half")

@@ -118,9 +118,13 @@ void frk32_next_target(int nv, const double *ymax_dev, const double *qref_dev, d
 // (same layout and permutation as P##_lu_factor), its time-out flag (4 if set)
 unsigned long long frktc_launch_count();
 int frktc_lu_supported(int nd);
-int frktc_lu_factor(int E, int nd, float *M, int *perm, int *info, cudaStream_t s);
+// l21: scratch of frktc_lu_scratch_floats(E, nd) floats (each phase's split L21 operand)
+size_t frktc_lu_scratch_floats(int E, int nd);
+int frktc_lu_factor(int E, int nd, float *M, int *perm, int *info, float *l21, cudaStream_t s);
 int frktc_lu_error(int clear);
-// half-width factors for the solves: binary16 L and column-scaled U, per column (1/u_kk, g_k)
+// half-width factors for the solves: binary16 L and column-scaled U (columns frktc_half_ld(nd)
+// halves apart), per column (1/u_kk, g_k)
+int frktc_half_ld(int nd);
 int frktc_lu_to_half(int E, int nd, const float *M, void *H, float *dg, cudaStream_t s);
 int frktc_lu_solve_half(int E, int nd, int g, const void *H, const float *dg, const int *perm, float *x,
                         cudaStream_t s);

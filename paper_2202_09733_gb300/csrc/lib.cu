@@ -110,6 +110,8 @@ struct fr_ctx {
     int ad_method;                // FP32 blocks: 0 element by element, 1 whole-level colours
     int lu_method;                // FP32 LU: 0 tensor cores where the block size allows, 1 CUDA cores
     int lu_half;                  // FP32 block solves from half-width factors (pmg_setup converts)
+    float *lu_scr;                // tensor-core LU: each phase's split L21 operand
+    size_t lu_scr_cap;
     float *ad_nt;                 // element-local FP32 blocks: the other sides' frozen face data
     signed char *ad_bck;          //   and the boundary code of every element face point
     int ncolor2;
@@ -329,7 +331,7 @@ extern "C" int fr_create(fr_ctx **out, const fr_mesh_desc *m, const fr_physics *
     }
     long long n0 = C->L[0].ndof;
     if (rc == FR_OK) rc = dalloc_t(C, &C->info, 1);
-    if (rc == FR_OK) rc = dalloc_t(C, &C->dots, 64);
+    if (rc == FR_OK) rc = dalloc_t(C, &C->dots, 520);   // Krylov dimensions up to 512: j + 1 <= 512 sums
     if (rc == FR_OK) rc = dalloc_t(C, &C->partial, (size_t)frk64_multidot_scratch(C->L[0].ndof));
     C->ndof_rms = (double)C->L[0].ndof;
     if (rc == FR_OK) rc = dalloc_t(C, &C->jv_qp, n0);
@@ -761,10 +763,22 @@ extern "C" int fr_elem_blocks(fr_ctx *C, int l, const double *q, double shift, d
 // order is the oracle's)
 static bool use_tc_lu(fr_ctx *C, int l, const float *) { return C->lu_method == 0 && frktc_lu_supported(C->L32[l].nd); }
 static bool use_tc_lu(fr_ctx *, int, const double *) { return false; }
-static void tc_factor(fr_ctx *C, int l, float *M, int *perm, cudaStream_t s) {
-    frktc_lu_factor(C->L32[l].E, C->L32[l].nd, M, perm, C->info, s);
+static int tc_scratch(fr_ctx *C, int E, int nd) {
+    size_t need = frktc_lu_scratch_floats(E, nd);
+    if (C->lu_scr && C->lu_scr_cap >= need) return FR_OK;
+    dfree(C, C->lu_scr);
+    C->lu_scr = nullptr;
+    C->lu_scr_cap = 0;
+    TRY(dalloc_t(C, &C->lu_scr, need));
+    C->lu_scr_cap = need;
+    return FR_OK;
 }
-static void tc_factor(fr_ctx *, int, double *, int *, cudaStream_t) {}
+static int tc_factor(fr_ctx *C, int l, float *M, int *perm, cudaStream_t s) {
+    TRY(tc_scratch(C, C->L32[l].E, C->L32[l].nd));
+    frktc_lu_factor(C->L32[l].E, C->L32[l].nd, M, perm, C->info, C->lu_scr, s);
+    return FR_OK;
+}
+static int tc_factor(fr_ctx *, int, double *, int *, cudaStream_t) { return FR_OK; }
 
 // half-width copy of level l's FP32 factors for the solves (FP64 factors: nothing)
 static int half_factors(fr_ctx *C, int l, const float *M, cudaStream_t s) {
@@ -772,7 +786,7 @@ static int half_factors(fr_ctx *C, int l, const float *M, cudaStream_t s) {
     P.half_ok[l] = 0;
     if (!C->lu_half) return FR_OK;
     const FrLevel32 &L = C->L32[l];
-    size_t need = (size_t)L.E * L.nd * L.nd;
+    size_t need = (size_t)L.E * L.nd * frktc_half_ld(L.nd);
     if (!P.H[l] || P.H_cap[l] < need) {
         dfree(C, P.H[l]);
         dfree(C, P.dg[l]);
@@ -803,7 +817,7 @@ static int smoother_solve(fr_ctx *C, int l, double *x, cudaStream_t s) {
 template <typename T>
 static int block_factor_t(fr_ctx *C, int l, T *M, int *perm, cudaStream_t s) {
     CK(cudaMemsetAsync(C->info, 0, sizeof(int), s));
-    if (use_tc_lu(C, l, M)) tc_factor(C, l, M, perm, s);
+    if (use_tc_lu(C, l, M)) TRY(tc_factor(C, l, M, perm, s));
     else Kn<T>::factor(levels<T>(C)[l], M, perm, C->info, s);
     CKLAUNCH();
     return FR_OK;
@@ -860,8 +874,9 @@ extern "C" int fr_block_factor_f32(fr_ctx *C, int l, float *M, int *perm, int me
     bool tc = method == 2 || (method == 0 && frktc_lu_supported(L.nd));
     if (tc && !frktc_lu_supported(L.nd))
         return fail(FR_ERR_UNIMPLEMENTED, "tensor-core LU: block size %d outside 65..384", L.nd);
+    if (tc) TRY(tc_scratch(C, L.E, L.nd));
     CK(cudaMemsetAsync(C->info, 0, sizeof(int), s));
-    if (tc) frktc_lu_factor(L.E, L.nd, M, perm, C->info, s);
+    if (tc) frktc_lu_factor(L.E, L.nd, M, perm, C->info, C->lu_scr, s);
     else frk32_lu_factor(L, M, perm, C->info, s);
     CKLAUNCH();
     int info = 0;
@@ -1263,7 +1278,7 @@ static int gmres_(fr_ctx *C, const double *q, const double *Rq, const double *b,
     TRY(gmres_alloc(C, K));
     long long n = C->L[0].ndof;
     double *w = C->gw, *r = C->gr;
-    std::vector<double> H((size_t)(K + 1) * K, 0.0), cs(K), sn(K), g(K + 1), y(K), h(32), h2(32);
+    std::vector<double> H((size_t)(K + 1) * K, 0.0), cs(K), sn(K), g(K + 1), y(K), h(K + 1), h2(K + 1);
     CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     frk64_copy(n, b, r, s);
     double bnorm, beta, est;

@@ -9,7 +9,8 @@
 //   panel phase j     one CTA per block factors the panel (columns k0 .. k0+31, rows
 //                     k0 .. nd-1) in shared memory: partial pivoting (first maximal |a|),
 //                     whole panel rows interchanged, multipliers a / pivot, 1/u_kk left
-//                     on the diagonal; the pivot rows go to ipiv (the perm array);
+//                     on the diagonal; the pivot rows go to ipiv (the perm array) and L21,
+//                     split into TF32 head and tail, to a scratch buffer;
 //   trailing phase j  one CTA per (block, 32-column tile of the trailing columns) takes
 //                     the tile's rows k0 .. nd-1 in the panel's interchange order, solves
 //                     U12 = L11^-1 A12 (unit lower L11), and forms A22 - L21 U12 with the
@@ -93,14 +94,13 @@ __device__ __forceinline__ int compose_swaps(const int *piv, int k0, int n, int 
 // the pivot search (first maximal |a| below the diagonal), the interchange of the two rows
 // across the panel (thread t swaps column t), then the multipliers a / pivot and the
 // rank-1 update of the columns to the right; 1/u_kk replaces the pivots at the end.
-__global__ void __launch_bounds__(128) k_lutc_panel(float *__restrict__ M, int *__restrict__ ipiv, int nd, int k0,
-                                                    int *info) {
-    extern __shared__ __align__(16) unsigned char pn_raw[];
-    float *P = reinterpret_cast<float *>(pn_raw);
+// Block e (A its matrix), panel k0; P: (nd - k0) x TC_NB floats of shared memory; 128
+// threads.  Also writes the trailing phase's split L21 operand into l21 (block e's slabs).
+__device__ __forceinline__ void factor_panel(float *__restrict__ A, int *__restrict__ ipiv, int nd, int k0, int *info,
+                                          float *__restrict__ l21, int mtiles, float *P, int e) {
     __shared__ float wbest[4];
     __shared__ int widx[4];
-    const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float *A = M + (size_t)e * nd * nd;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = nd - k0, kb = min(TC_NB, R);
     for (int c = 0; c < kb; ++c) {
         const float *gc = A + (size_t)(k0 + c) * nd + k0;
@@ -157,12 +157,43 @@ __global__ void __launch_bounds__(128) k_lutc_panel(float *__restrict__ M, int *
         float *gc = A + (size_t)(k0 + c) * nd + k0;
         for (int i = tid; i < R; i += 128) gc[i] = P[c * R + i];
     }
+    // the trailing phase's A operand, once per block: L21 (rows k0+32 .. nd-1 of the panel)
+    // split into TF32 head and tail, in the K-major core-matrix layout of 128-row slabs
+    // ([slab][head, tail][128 x TC_NB]), rows past the block zero
+    if (mtiles > 0) {
+        float *out = l21 + (size_t)e * mtiles * 2 * 128 * TC_NB;
+        for (int m = 0; m < mtiles; ++m) {
+            const int i = TC_NB + 128 * m + tid;   // panel row
+            const bool live = i < R;
+            float *oh = out + (size_t)(2 * m) * 128 * TC_NB, *ol = oh + 128 * TC_NB;
+#pragma unroll
+            for (int q = 0; q < TC_NB / 4; ++q) {
+                float h[4], lo[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float x = live ? P[(4 * q + j) * R + i] : 0.f;
+                    h[j] = tf32_round(x);
+                    lo[j] = tf32_round(x - h[j]);
+                }
+                *reinterpret_cast<float4 *>(oh + core_off(tid, 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<float4 *>(ol + core_off(tid, 4 * q)) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            }
+        }
+    }
+}
+
+// the first panel: one CTA per block
+__global__ void __launch_bounds__(128) k_lutc_panel(float *__restrict__ M, int *__restrict__ ipiv, int nd, int k0,
+                                                    int *info, float *__restrict__ l21, int mtiles) {
+    extern __shared__ __align__(16) unsigned char pn_raw[];
+    const int e = blockIdx.x;
+    factor_panel(M + (size_t)e * nd * nd, ipiv, nd, k0, info, l21, mtiles, reinterpret_cast<float *>(pn_raw), e);
 }
 
 // ---------------------------------------------------------------------- trailing
 // Shared memory: A operand head/tail (2 x 128 x TC_NB), B operand head/tail
 // (2 x TC_NT x TC_NB), L11 and the tile's panel rows (TC_NB x TC_NB each), 48 KB in all,
-// so four CTAs share an SM; each holds 32 tensor-memory columns (one 128 x 32 product).
+// so four CTAs share an SM; each holds 64 tensor-memory columns (two 128 x 32 products).
 //
 // The panel's interchanges move rows only between the panel rows k0 .. k0+31 and the rows
 // below: row i >= k0+32 of the tile ends up holding either itself or one of the panel rows
@@ -175,7 +206,7 @@ __global__ void __launch_bounds__(128) k_lutc_panel(float *__restrict__ M, int *
 #define TC_SMEM_FLOATS (2 * 128 * TC_NB + 2 * TC_NT * TC_NB + 2 * TC_NB * TC_NB)
 
 __global__ void __launch_bounds__(128, 4) k_lutc_trail(float *__restrict__ M, const int *__restrict__ ipiv, int nd,
-                                                    int k0, int ntiles) {
+                                                       int k0, int ntiles, const float *__restrict__ l21) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     float *sAh = reinterpret_cast<float *>(tc_raw);
     float *sAl = sAh + 128 * TC_NB;
@@ -187,7 +218,7 @@ __global__ void __launch_bounds__(128, 4) k_lutc_trail(float *__restrict__ M, co
     __shared__ int pv[TC_NB];
     __shared__ unsigned tmem_base;
     __shared__ int s_ok;
-    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ __align__(8) unsigned long long mbar, cbar;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int e = blockIdx.x / ntiles, tile = blockIdx.x - e * ntiles;
@@ -197,11 +228,12 @@ __global__ void __launch_bounds__(128, 4) k_lutc_trail(float *__restrict__ M, co
     const int mtiles = (mt + 127) / 128;
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&cbar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid < TC_NB) pv[tid] = ipiv[(size_t)e * nd + k0 + tid];
@@ -259,53 +291,58 @@ __global__ void __launch_bounds__(128, 4) k_lutc_trail(float *__restrict__ M, co
     constexpr unsigned idesc = umma_idesc_tf32(128, TC_NT);
     const unsigned LBO = 128, SBO = TC_NB * 32;
     bool ok = true;
-    // per 128-row slab m of the trailing rows: thread tid owns row i = 128 m + tid, for which
-    // it loads the L21 row (the product's A row) and the tile's source values, stages the
-    // A row, and after the product takes its D row back: A22 row = sources - D row
+    // per 128-row slab m of the trailing rows: the slab's A operand (the panel kernel's
+    // split L21) comes by two bulk copies while thread tid loads the tile's source values
+    // of its row i = 128 m + tid; after the product, A22 row = sources - D row
+    const float *slabs = l21 + (size_t)e * mtiles * 2 * 128 * TC_NB;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B (generic stores) before the products
+    __syncthreads();
     for (int m = 0; m < mtiles; ++m) {
         const int i = 128 * m + tid, row = r0 + i;
         const bool live = i < mt;
         const int sr = live ? src[TC_NB + i] : 0;
-        float x[TC_NB], a[TC_NT];
-#pragma unroll
-        for (int c = 0; c < TC_NB; ++c) x[c] = live ? A[(size_t)(k0 + c) * nd + row] : 0.f;
+        if (tid == 0 && ok) {
+            // sA is free: the previous slab's product has completed (waited below)
+            const unsigned bytes = 2u * 128u * TC_NB * 4u;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&cbar)), "r"(bytes)
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(sAh)), "l"(slabs + (size_t)(2 * m) * 128 * TC_NB), "r"(bytes),
+                           "r"(smem_u32(&cbar)) : "memory");
+        }
+        float a[TC_NT];
 #pragma unroll
         for (int n = 0; n < TC_NT; ++n) a[n] = (live && n < nt) ? A[(size_t)(j0 + n) * nd + sr] : 0.f;
-#pragma unroll
-        for (int q = 0; q < TC_NB / 4; ++q) {
-            float h[4], lo[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) { h[j] = tf32_round(x[4 * q + j]); lo[j] = tf32_round(x[4 * q + j] - h[j]); }
-            *reinterpret_cast<float4 *>(sAh + core_off(tid, 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<float4 *>(sAl + core_off(tid, 4 * q)) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        if (tid == 0) {
+            bool okk = ok && mbar_wait(&cbar, (unsigned)m & 1u);
+            if (ok && !okk && !mbar_wait(&cbar, (unsigned)m & 1u))
+                atomicOr(&g_lutc_err, 2);   // the slab's copy is still in flight: shared memory undefined
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (okk) {
+                const float *As[3] = {sAh, sAh, sAl};
+                const float *Bs[3] = {sBh, sBl, sBh};
+                for (int pass = 0; pass < 3; ++pass)
+                    for (int s = 0; s < TC_NB / 8; ++s) {
+                        uint64_t ad = umma_desc(smem_u32(As[pass]) + 256u * s, LBO, SBO);
+                        uint64_t bd = umma_desc(smem_u32(Bs[pass]) + 256u * s, LBO, SBO);
+                        unsigned acc = (pass > 0 || s > 0) ? 1u : 0u;
+                        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                     " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                     ::"r"(tmem + 32u * (m & 1)), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_u32(&mbar)) : "memory");
+                okk = mbar_wait(&mbar, (unsigned)m & 1u);
+            }
+            s_ok = okk;
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        // the others wait at the CTA barrier (no issue slots) while thread 0 polls
         __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0 && ok) {
-            const float *As[3] = {sAh, sAh, sAl};
-            const float *Bs[3] = {sBh, sBl, sBh};
-            for (int pass = 0; pass < 3; ++pass)
-                for (int s = 0; s < TC_NB / 8; ++s) {
-                    uint64_t ad = umma_desc(smem_u32(As[pass]) + 256u * s, LBO, SBO);
-                    uint64_t bd = umma_desc(smem_u32(Bs[pass]) + 256u * s, LBO, SBO);
-                    unsigned acc = (pass > 0 || s > 0) ? 1u : 0u;
-                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                 ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-                }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_u32(&mbar)) : "memory");
-        }
-        // one thread polls the barrier; the others wait at the CTA barrier (no issue slots)
-        if (tid == 0) s_ok = ok && mbar_wait(&mbar, (unsigned)m & 1u);
-        __syncthreads();              // also: sA is free for the next slab once every thread is here
         ok = s_ok;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) break;
         unsigned d[32];
-        unsigned ta = tmem + ((unsigned)(32 * warp) << 16);
+        unsigned ta = tmem + ((unsigned)(32 * warp) << 16) + 32u * (m & 1);
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
                      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
                      : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]),
@@ -319,8 +356,9 @@ __global__ void __launch_bounds__(128, 4) k_lutc_trail(float *__restrict__ M, co
 #pragma unroll
             for (int n = 0; n < TC_NT; ++n)
                 if (n < nt) A[(size_t)(j0 + n) * nd + row] = a[n] - __uint_as_float(d[n]);
-        // the next slab's product overwrites these tensor-memory columns: every warp's
-        // tcgen05.ld has completed (wait::ld) before it passes the next slab's barrier
+        // the products alternate between two 32-column halves of tensor memory: slab m+1's
+        // product is issued after the barrier of slab m, which every warp reaches only
+        // after its tcgen05.ld of slab m-1 (the same half) has completed
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
     if (ok) {
@@ -335,7 +373,7 @@ __global__ void __launch_bounds__(128, 4) k_lutc_trail(float *__restrict__ M, co
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
 }
 
 // ------------------------------------------------------------------------- final
@@ -399,13 +437,14 @@ static size_t final_smem(int nd) {
 // For the block solves of the smoother, the factors of a block at half the bytes: L
 // (unit, |l| <= 1 under partial pivoting) as binary16; column k of U (rows < k) divided by
 // its largest magnitude g_k, as binary16 (entries in [-1, 1]); per column, in FP32,
-// (1/u_kk, g_k).  binary16 keeps 10 mantissa bits, the precision of TF32.  One CTA per
-// block, one warp per column.
+// (1/u_kk, g_k).  binary16 keeps 10 mantissa bits, the precision of TF32.  Columns are
+// ldh = nd rounded up to even halves apart (so that two rows load as one 4-byte word).
+// One CTA per block, one warp per column.
 __global__ void __launch_bounds__(256) k_lutc_to_half(const float *__restrict__ M, __half *__restrict__ H,
-                                                      float2 *__restrict__ dg, int nd) {
+                                                      float2 *__restrict__ dg, int nd, int ldh) {
     const int e = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float *Ab = M + (size_t)e * nd * nd;
-    __half *Hb = H + (size_t)e * nd * nd;
+    __half *Hb = H + (size_t)e * nd * ldh;
     for (int k = warp; k < nd; k += 8) {
         const float *col = Ab + (size_t)k * nd;
         float m = 0.f;
@@ -415,106 +454,122 @@ __global__ void __launch_bounds__(256) k_lutc_to_half(const float *__restrict__ 
         const float g = m > 0.f ? m : 1.f, ig = 1.f / g;
         for (int i = lane; i < nd; i += 32) {
             float v = col[i];
-            Hb[(size_t)k * nd + i] = __float2half_rn(i < k ? v * ig : (i > k ? v : 0.f));
+            Hb[(size_t)k * ldh + i] = __float2half_rn(i < k ? v * ig : (i > k ? v : 0.f));
         }
-        if (lane == 0) dg[(size_t)e * nd + k] = make_float2(col[k], g);
+        if (lane == 0) {
+            dg[(size_t)e * nd + k] = make_float2(col[k], g);
+            if (ldh > nd) Hb[(size_t)k * ldh + nd] = __float2half_rn(0.f);   // the pad row
+        }
     }
 }
 
-// x <- M_e^{-1} x with the half-width factors: the register solve of the FP32 factors
-// (one warp per element, rows lane + 32 s in registers, G columns fetched ahead), with
-// x_k = b_k (1/u_kk) and the rows above updated by the scaled column times g_k x_k.
-template <int NR, int G>
+// x <- M_e^{-1} x with the half-width factors.  One warp per element; lane l holds rows
+// 64 s + 2 l and 64 s + 2 l + 1 (s < NR2) in registers, so one 4-byte load per lane
+// brings two rows of a column and a warp reads 128 bytes of it at once; G columns are
+// fetched ahead of the dependent fma chain.  Forward: rows below k take y_k (unit L);
+// backward: x_k = b_k (1/u_kk), then the rows above k take the scaled column times
+// g_k x_k.
+template <int NR2, int G>
 __global__ void __launch_bounds__(128) k_lu_solve_half(const __half *__restrict__ H, const float2 *__restrict__ dg,
                                                        const int *__restrict__ perm, float *__restrict__ x, int nd,
-                                                       int E) {
+                                                       int ldh, int E) {
     int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= E) return;
-    const __half *A = H + (size_t)e * nd * nd;
+    const __half *A = H + (size_t)e * nd * ldh;
     const float2 *D = dg + (size_t)e * nd;
     const int *pv = perm + (size_t)e * nd;
-    float b[NR];
+    float2 b[NR2];
 #pragma unroll
-    for (int s = 0; s < NR; ++s) {
-        int i = lane + 32 * s;
-        b[s] = i < nd ? x[(size_t)pv[i] * E + e] : 0.f;
+    for (int s = 0; s < NR2; ++s) {
+        int r = 64 * s + 2 * lane;
+        b[s].x = r < nd ? x[(size_t)pv[r] * E + e] : 0.f;
+        b[s].y = r + 1 < nd ? x[(size_t)pv[r + 1] * E + e] : 0.f;
     }
 #pragma unroll
-    for (int sk = 0; sk < NR; ++sk) {
-        const int kend = min(nd, 32 * sk + 32);
-        for (int k0 = 32 * sk; k0 < kend; k0 += G) {
-            float cv[G][NR];
+    for (int sk = 0; sk < NR2; ++sk) {
+        const int kend = min(nd, 64 * sk + 64);
+        for (int k0 = 64 * sk; k0 < kend; k0 += G) {
+            float2 cv[G][NR2];
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 int k = k0 + g;
-                const __half *col = A + (size_t)(k < kend ? k : kend - 1) * nd;
+                const __half *col = A + (size_t)(k < kend ? k : kend - 1) * ldh;
 #pragma unroll
-                for (int s = sk; s < NR; ++s) {
-                    int i = lane + 32 * s;
-                    bool need = k < kend && i < nd && (s > sk || lane > (k & 31));
-                    cv[g][s] = need ? __half2float(col[i]) : 0.f;
+                for (int s = sk; s < NR2; ++s) {
+                    int r = 64 * s + 2 * lane;
+                    bool need = k < kend && r < nd && (s > sk || r + 1 > (k & 63) + 64 * sk);
+                    cv[g][s] = need ? __half22float2(*reinterpret_cast<const __half2 *>(col + r)) : make_float2(0.f, 0.f);
                 }
             }
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 int k = k0 + g;
                 if (k >= kend) break;
-                float yk = __shfl_sync(0xffffffffu, b[sk], k & 31);
+                int kl = k & 63, owner = kl >> 1;
+                float yk = __shfl_sync(0xffffffffu, (kl & 1) ? b[sk].y : b[sk].x, owner);
 #pragma unroll
-                for (int s = sk; s < NR; ++s) {
-                    int i = lane + 32 * s;
-                    if (i < nd && (s > sk || lane > (k & 31))) b[s] = fmaf(-cv[g][s], yk, b[s]);
+                for (int s = sk; s < NR2; ++s) {
+                    int r = 64 * s + 2 * lane;
+                    if (s > sk || r > k) b[s].x = fmaf(-cv[g][s].x, yk, b[s].x);
+                    if (s > sk || r + 1 > k) b[s].y = fmaf(-cv[g][s].y, yk, b[s].y);
                 }
             }
         }
     }
 #pragma unroll
-    for (int sk = NR - 1; sk >= 0; --sk) {
-        const int kbeg = min(nd, 32 * sk + 32) - 1;
-        for (int kt = kbeg; kt >= 32 * sk; kt -= G) {
-            float cv[G][NR];
+    for (int sk = NR2 - 1; sk >= 0; --sk) {
+        const int kbeg = min(nd, 64 * sk + 64) - 1;
+        for (int kt = kbeg; kt >= 64 * sk; kt -= G) {
+            float2 cv[G][NR2];
             float2 dk[G];
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 int k = kt - g;
-                int kk = k >= 32 * sk ? k : 32 * sk;
-                const __half *col = A + (size_t)kk * nd;
+                int kk = k >= 64 * sk ? k : 64 * sk;
+                const __half *col = A + (size_t)kk * ldh;
                 dk[g] = D[kk];
 #pragma unroll
                 for (int s = 0; s <= sk; ++s) {
-                    int i = lane + 32 * s;
-                    bool need = k >= 32 * sk && (s < sk || lane < (k & 31));
-                    cv[g][s] = need ? __half2float(col[i]) : 0.f;
+                    int r = 64 * s + 2 * lane;
+                    bool need = k >= 64 * sk && (s < sk || r < k);
+                    cv[g][s] = need ? __half22float2(*reinterpret_cast<const __half2 *>(col + r)) : make_float2(0.f, 0.f);
                 }
             }
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 int k = kt - g;
-                if (k < 32 * sk) break;
-                int owner = k & 31;
-                float xk = __shfl_sync(0xffffffffu, b[sk], owner) * dk[g].x;
+                if (k < 64 * sk) break;
+                int kl = k & 63, owner = kl >> 1;
+                float xk = __shfl_sync(0xffffffffu, (kl & 1) ? b[sk].y : b[sk].x, owner) * dk[g].x;
                 float xs = xk * dk[g].y;
 #pragma unroll
-                for (int s = 0; s < sk; ++s) b[s] = fmaf(-cv[g][s], xs, b[s]);
-                if (lane == owner) b[sk] = xk;
-                else if (lane < owner) b[sk] = fmaf(-cv[g][sk], xs, b[sk]);
+                for (int s = 0; s < sk; ++s) {
+                    b[s].x = fmaf(-cv[g][s].x, xs, b[s].x);
+                    b[s].y = fmaf(-cv[g][s].y, xs, b[s].y);
+                }
+                int r = 64 * sk + 2 * lane;
+                if (r == k) b[sk].x = xk;
+                else if (r < k) b[sk].x = fmaf(-cv[g][sk].x, xs, b[sk].x);
+                if (r + 1 == k) b[sk].y = xk;
+                else if (r + 1 < k) b[sk].y = fmaf(-cv[g][sk].y, xs, b[sk].y);
             }
         }
     }
     __syncwarp();
 #pragma unroll
-    for (int s = 0; s < NR; ++s) {
-        int i = lane + 32 * s;
-        if (i < nd) x[(size_t)i * E + e] = b[s];
+    for (int s = 0; s < NR2; ++s) {
+        int r = 64 * s + 2 * lane;
+        if (r < nd) x[(size_t)r * E + e] = b[s].x;
+        if (r + 1 < nd) x[(size_t)(r + 1) * E + e] = b[s].y;
     }
 }
 
-template <int NR>
+template <int NR2>
 static void solve_half_nr(int g, int grid, const __half *H, const float2 *dg, const int *perm, float *x, int nd,
-                          int E, cudaStream_t s) {
-    if (g >= 8) k_lu_solve_half<NR, 8><<<grid, 128, 0, s>>>(H, dg, perm, x, nd, E);
-    else if (g >= 4) k_lu_solve_half<NR, 4><<<grid, 128, 0, s>>>(H, dg, perm, x, nd, E);
-    else k_lu_solve_half<NR, 2><<<grid, 128, 0, s>>>(H, dg, perm, x, nd, E);
+                          int ldh, int E, cudaStream_t s) {
+    if (g >= 8) k_lu_solve_half<NR2, 8><<<grid, 128, 0, s>>>(H, dg, perm, x, nd, ldh, E);
+    else if (g >= 4) k_lu_solve_half<NR2, 4><<<grid, 128, 0, s>>>(H, dg, perm, x, nd, ldh, E);
+    else k_lu_solve_half<NR2, 2><<<grid, 128, 0, s>>>(H, dg, perm, x, nd, ldh, E);
 }
 
 }  // namespace
@@ -522,8 +577,14 @@ static void solve_half_nr(int g, int grid, const __half *H, const float2 *dg, co
 // the tensor-core factorisation handles blocks with TC_NB < nd <= TC_MAXND
 int frktc_lu_supported(int nd) { return nd > 2 * TC_NB && nd <= TC_MAXND; }
 
-int frktc_lu_factor(int E, int nd, float *M, int *perm, int *info, cudaStream_t s) {
-    if (!frktc_lu_supported(nd) || E <= 0) return 1;
+// each phase's split L21 operand (the panel kernel writes it, the trailing kernel reads it)
+size_t frktc_lu_scratch_floats(int E, int nd) {
+    int mt0 = nd - TC_NB, mtiles = mt0 > 0 ? (mt0 + 127) / 128 : 0;
+    return (size_t)E * mtiles * 2 * 128 * TC_NB;
+}
+
+int frktc_lu_factor(int E, int nd, float *M, int *perm, int *info, float *l21, cudaStream_t s) {
+    if (!frktc_lu_supported(nd) || E <= 0 || !l21) return 1;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_lutc_trail, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -534,15 +595,15 @@ int frktc_lu_factor(int E, int nd, float *M, int *perm, int *info, cudaStream_t 
         attr = true;
     }
     for (int k0 = 0; k0 < nd; k0 += TC_NB) {
-        int rows = nd - k0;
+        int rows = nd - k0, mt = rows - TC_NB, mtiles = mt > 0 ? (mt + 127) / 128 : 0;
         CNT();
-        k_lutc_panel<<<E, 128, sizeof(float) * TC_NB * rows, s>>>(M, perm, nd, k0, info);
-        if (k0 + TC_NB < nd) {
-            int ntiles = (nd - k0 - TC_NB + TC_NT - 1) / TC_NT;
+        k_lutc_panel<<<E, 128, sizeof(float) * TC_NB * rows, s>>>(M, perm, nd, k0, info, l21, mtiles);
+        if (mt > 0) {
+            int ntiles = (mt + TC_NT - 1) / TC_NT;
             long long grid = (long long)ntiles * E;
             if (grid > 0x7fffffffLL) return 1;
             CNT();
-            k_lutc_trail<<<(unsigned)grid, 128, sizeof(float) * TC_SMEM_FLOATS, s>>>(M, perm, nd, k0, ntiles);
+            k_lutc_trail<<<(unsigned)grid, 128, sizeof(float) * TC_SMEM_FLOATS, s>>>(M, perm, nd, k0, ntiles, l21);
         }
     }
     CNT();
@@ -557,32 +618,33 @@ int frktc_lu_error(int clear) {
         int z = 0;
         cudaMemcpyToSymbol(g_lutc_err, &z, sizeof(int));
     }
-    return h ? 4 : 0;
+    return (h & 1 ? 4 : 0) | (h & 2 ? 2 : 0);
 }
+
+int frktc_half_ld(int nd) { return (nd + 1) & ~1; }
 
 int frktc_lu_to_half(int E, int nd, const float *M, void *H, float *dg, cudaStream_t s) {
     if (E <= 0 || nd <= 0) return 1;
     CNT();
-    k_lutc_to_half<<<E, 256, 0, s>>>(M, (__half *)H, (float2 *)dg, nd);
+    k_lutc_to_half<<<E, 256, 0, s>>>(M, (__half *)H, (float2 *)dg, nd, frktc_half_ld(nd));
     return 0;
 }
 
+// g: columns in flight (2, 4, 8; 0 or 1: the default, 4)
 int frktc_lu_solve_half(int E, int nd, int g, const void *H, const float *dg, const int *perm, float *x,
                         cudaStream_t s) {
-    int nr = (nd + 31) / 32, grid = (E * 32 + 127) / 128;
+    int nr2 = (nd + 63) / 64, grid = (E * 32 + 127) / 128, ldh = frktc_half_ld(nd);
     const __half *h = (const __half *)H;
     const float2 *d = (const float2 *)dg;
+    if (g < 2) g = 4;
     CNT();
-    switch (nr) {
-        case 1: solve_half_nr<1>(g, grid, h, d, perm, x, nd, E, s); break;
-        case 2: solve_half_nr<2>(g, grid, h, d, perm, x, nd, E, s); break;
-        case 3: solve_half_nr<3>(g, grid, h, d, perm, x, nd, E, s); break;
-        case 4: solve_half_nr<4>(g, grid, h, d, perm, x, nd, E, s); break;
-        case 5: solve_half_nr<5>(g, grid, h, d, perm, x, nd, E, s); break;
-        case 6: solve_half_nr<6>(g, grid, h, d, perm, x, nd, E, s); break;
-        case 7: solve_half_nr<7>(g, grid, h, d, perm, x, nd, E, s); break;
-        case 8: solve_half_nr<8>(g, grid, h, d, perm, x, nd, E, s); break;
-        case 10: solve_half_nr<10>(g, grid, h, d, perm, x, nd, E, s); break;
+    switch (nr2) {
+        case 1: solve_half_nr<1>(g, grid, h, d, perm, x, nd, ldh, E, s); break;
+        case 2: solve_half_nr<2>(g, grid, h, d, perm, x, nd, ldh, E, s); break;
+        case 3: solve_half_nr<3>(g, grid, h, d, perm, x, nd, ldh, E, s); break;
+        case 4: solve_half_nr<4>(g, grid, h, d, perm, x, nd, ldh, E, s); break;
+        case 5: solve_half_nr<5>(g, grid, h, d, perm, x, nd, ldh, E, s); break;
+        case 6: solve_half_nr<6>(g, grid, h, d, perm, x, nd, ldh, E, s); break;
         default: return -1;
     }
     return 0;

@@ -4,7 +4,9 @@ external profilers (ncu):  python -m paper_2202_09733_gb300.profile_case --case 
 Operations: residual (FP64), residual32 (the FP32 residual of the mixed preconditioner:
 a cycle with no smoothing, one FP32 residual per level), jvp, pmg (one preconditioner
 application, --precision fp64|mixed; its block solves, transfers and residuals can be
-picked out with the profiler's kernel filter), row_step (from the same state every run),
+picked out with the profiler's kernel filter), lu_factor (the FP32 LU of the fine level's
+element blocks, --lu auto|cuda_cores|tensor_cores, from a fresh copy of the blocks each
+run), row_step (from the same state every run),
 esdirk_step (ESDIRK3 at the 1e-8 Newton tolerance, successive steps).  The setup (context, blocks and
 factors where the operation needs them) runs first; then --reps runs of the operation,
 each followed by a device synchronisation.
@@ -26,7 +28,9 @@ def main(argv=None):
     ap.add_argument("--case", default="tgv3d", choices=["tgv3d", "cylinder_unsteady", "vortex2d"])
     ap.add_argument("--n", type=int, default=32, help="tgv3d: elements per direction")
     ap.add_argument("--op", default="residual",
-                    choices=["residual", "residual32", "jvp", "pmg", "row_step", "esdirk_step"])
+                    choices=["residual", "residual32", "jvp", "pmg", "row_step", "esdirk_step", "lu_factor"])
+    ap.add_argument("--lu", default="auto", choices=["auto", "cuda_cores", "tensor_cores"],
+                    help="lu_factor: the FP32 factorisation of the fine level's element blocks")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--reps", type=int, default=4)
     ap.add_argument("--autotune", action="store_true")
@@ -66,6 +70,9 @@ def main(argv=None):
             api.pmg_precondition(ctx, q, R, v)
         elif a.op == "jvp":
             api.fr_jvp(ctx, q, R, v, 1e-6, c)
+        elif a.op == "lu_factor":
+            Mw.copy_(M0)
+            api.fr_block_factor_f32(ctx, 0, Mw, a.lu, perm=pw)
         elif a.op == "pmg":
             api.pmg_precondition(ctx, q, R, v)
         elif a.op == "esdirk_step":
@@ -81,6 +88,12 @@ def main(argv=None):
             api.row_step(ctx, g, aa, cc, m, dt, qq, o)
 
     qs = q.clone()   # esdirk_step: successive runs advance this state
+    if a.op == "lu_factor":
+        # the FP32 element blocks of the fine level at q (the mixed preconditioner's), copied
+        # afresh before every factorisation
+        M0 = api.fr_elem_blocks_f32(ctx, 0, q.float().contiguous(), c)
+        Mw = torch.empty_like(M0)
+        pw = torch.empty((ctx.E, ctx.nd(0)), dtype=torch.int32, device="cuda")
     if a.op == "residual32":
         api.pmg_setup(ctx, q, (0,) * len(W.levels), c, 1.0 / dt, precision="mixed")
     from . import _native as N

@@ -210,6 +210,25 @@ def test_esdirk_step_converged_state(scheme):
     assert relerr(qg, q0) > 1e-4          # the step did move the state
 
 
+def test_gmres_long_krylov_basis():
+    """Krylov dimensions past 64 (the CGS2 sums of one Arnoldi step then exceed the first
+    fixed host and device buffers the solver had): 70 fixed iterations with no restart
+    equal the oracle's as 12 do."""
+    mesh = w.box2d(4, 4, 10, 10, qg=2, warp=0.1)
+    ph = w.Physics(mu=0.01, qinf=w.freestream(2, 0.3))
+    O = oracle.Oracle(mesh, ph, [3, 2])
+    G = api.fr_create(mesh, ph, [3, 2])
+    q = _wavy_state(mesh, 3)
+    c = 1.0          # 1024 unknowns: 70 iterations leave a relative residual near 0.14
+    Rq = O.residual(q)
+    b = np.random.default_rng(12).standard_normal(q.shape)
+    x_or, st_or = O.gmres(q, Rq, b, kdim=70, tol=0.0, maxit=70, shift=c, use_pmg=False)
+    x_gpu, st_gpu = api.gmres_solve(G, dev(q), dev(Rq), dev(b), kdim=70, maxit=70, tol=0.0, shift=c, use_pmg=False)
+    assert st_gpu["iters"] == st_or["iters"] == 70 and st_gpu["restarts"] == 0
+    assert abs(st_gpu["relres"] - st_or["relres"]) <= 1e-2 * st_or["relres"] + 1e-12
+    assert relerr(x_gpu, x_or) <= 1e-4
+
+
 def test_row_step_converged_state():
     mesh = w.box2d(4, 4, 10, 10, qg=2, warp=0.1)
     ph = w.Physics(mu=0.01, qinf=w.freestream(2, 0.5))
