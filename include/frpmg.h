@@ -203,6 +203,18 @@ int fr_block_to_half(fr_ctx *ctx, int level, const float *M, void *H, float *dg,
  * fr_block_factor_f32 */
 int fr_block_solve_half(fr_ctx *ctx, int level, const void *H, const float *dg, const int *perm, float *x,
                         void *stream);
+/* 1: the FP64 preconditioner cycle (pmg_setup precision 0, as used by FGMRES) is driven
+ * like the FP32 one: X scaled so that the correction is about 1e-2 of the state per
+ * variable, the result scaled back (a nonlinear preconditioner; FGMRES allows it).  For
+ * states whose magnitude dwarfs a unit-norm Krylov vector (the pressure ~ 1/(gamma Ma^2)
+ * at low Mach) an unscaled correction is lost in the rounding of R(q + Y) - R(q).  0 (the
+ * default): unscaled, the oracle's cycle.  The nonlinear pMG solvers are never scaled.
+ * Takes effect at the next pmg_setup. */
+int fr_set_cycle_scaling(fr_ctx *ctx, int on);
+/* ptc_steady with the FP32 preconditioner: 1 (the default) switches to the FP64 cycle
+ * when FGMRES stalls (all its iterations used and the residual fell by less than half, or
+ * five pseudo steps in a row each gained less than 10%); 0 keeps the FP32 cycle. */
+int fr_set_precision_fallback(fr_ctx *ctx, int on);
 /* 1: pmg_setup also stores the mixed preconditioner's FP32 factors at half width and the
  * smoother's block solves read those (half the bytes per solve); 0 (the default): FP32
  * factors.  Takes effect at the next pmg_setup. */

@@ -214,6 +214,16 @@ def fr_block_solve_half(ctx, level, H, dg, perm, x, stream=None):
     return x
 
 
+def fr_set_cycle_scaling(ctx, on):
+    """Drive the FP64 preconditioner cycle with a scaled X (as the FP32 one is)."""
+    N.check(N.load().fr_set_cycle_scaling(ctx.handle, int(bool(on))), "fr_set_cycle_scaling")
+
+
+def fr_set_precision_fallback(ctx, on):
+    """ptc_steady: switch a stalled FP32 preconditioner to the FP64 cycle (default True)."""
+    N.check(N.load().fr_set_precision_fallback(ctx.handle, int(bool(on))), "fr_set_precision_fallback")
+
+
 def fr_set_lu_storage(ctx, storage):
     """How pmg_setup keeps the FP32 factors for the smoother's solves: "fp32" (default) or
     "half" (binary16 entries with per-column scales, half the bytes per solve)."""

@@ -110,6 +110,9 @@ struct fr_ctx {
     int ad_method;                // FP32 blocks: 0 element by element, 1 whole-level colours
     int lu_method;                // FP32 LU: 0 tensor cores where the block size allows, 1 CUDA cores
     int lu_half;                  // FP32 block solves from half-width factors (pmg_setup converts)
+    int scale64;                  // the FP64 cycle driven with a scaled X, as the FP32 cycle is
+    int no_fallback;              // ptc_steady: keep the FP32 cycle when it stalls
+    double *x64s;                 // the scaled FP64 cycle's right-hand side
     float *lu_scr;                // tensor-core LU: each phase's split L21 operand
     size_t lu_scr_cap;
     float *ad_nt;                 // element-local FP32 blocks: the other sides' frozen face data
@@ -840,6 +843,19 @@ extern "C" int fr_set_lu_method(fr_ctx *C, int method) {
     return FR_OK;
 }
 
+extern "C" int fr_set_cycle_scaling(fr_ctx *C, int on) {
+    if (!C || on < 0 || on > 1) return fail(FR_ERR_INVALID_ARG, "on must be 0 or 1");
+    C->scale64 = on;
+    C->pmg_ready = 0;
+    return FR_OK;
+}
+
+extern "C" int fr_set_precision_fallback(fr_ctx *C, int on) {
+    if (!C || on < 0 || on > 1) return fail(FR_ERR_INVALID_ARG, "on must be 0 or 1");
+    C->no_fallback = !on;
+    return FR_OK;
+}
+
 extern "C" int fr_set_lu_storage(fr_ctx *C, int half) {
     if (!C || half < 0 || half > 1) return fail(FR_ERR_INVALID_ARG, "half must be 0 or 1");
     C->lu_half = half;
@@ -1017,14 +1033,20 @@ static int pmg_setup_(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, cuda
     C->mbnk_maxit = o->mbnk_maxit;
     C->mbnk_tol = o->mbnk_tol;
     C->pmg_gain = o->c + o->inv_dtau_star > 0.0 ? 1.0 / (o->c + o->inv_dtau_star) : 1.0;
-    if (o->precision == 0) {
+    if (o->precision == 0 && !C->scale64) {
         TRY(pmg_alloc_t<double>(C, o->nlevels));
         TRY(pmg_factor_levels<double>(C, q_ref, o, s));
     } else {
-        TRY(ensure_levels32(C));
-        TRY(pmg_alloc_t<float>(C, o->nlevels));
+        if (o->precision != 0) {
+            TRY(ensure_levels32(C));
+            TRY(pmg_alloc_t<float>(C, o->nlevels));
+        } else {
+            TRY(pmg_alloc_t<double>(C, o->nlevels));
+            if (!C->x64s) TRY(dalloc_t(C, &C->x64s, C->L[0].ndof));
+        }
         long long n = C->L[0].ndof;
         if (!C->ymax) TRY(dalloc_t(C, &C->ymax, 5));
+        if (!C->xmax) TRY(dalloc_t(C, &C->xmax, 1));
         int rc_m = C->has_comm ? frk32_absmax_var_owned(C->nv, C->L[0].np, C->E, C->comm.n_owned, q_ref, C->ymax, s)
                                : frk32_absmax_var(C->nv, n / C->nv, q_ref, C->ymax, s);
         if (rc_m != 0) return fail(FR_ERR_CUDA, "absmax");
@@ -1041,8 +1063,12 @@ static int pmg_setup_(fr_ctx *C, const double *q_ref, const fr_pmg_opts *o, cuda
         }
         if (!(qsmall > 0.0)) return fail(FR_ERR_INVALID_ARG, "reference state is zero");
         C->pmg_gain /= qsmall;
-        frk32_d2f(n, q_ref, C->q32, s);
-        TRY(pmg_factor_levels<float>(C, C->q32, o, s));
+        if (o->precision != 0) {
+            frk32_d2f(n, q_ref, C->q32, s);
+            TRY(pmg_factor_levels<float>(C, C->q32, o, s));
+        } else {
+            TRY(pmg_factor_levels<double>(C, q_ref, o, s));
+        }
     }
     int info = 0;
     CK(cudaMemcpyAsync(&info, C->info, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1170,13 +1196,53 @@ static int vcycle_t(fr_ctx *C, int l, const T *b, const T *Rb, const T *d, T *qh
 static const double kMixedAlpha = 1e-2;
 static const double kMixedSlack = 30.0;
 
-static int pmg_apply(fr_ctx *C, const double *q, const double *Rq, const double *X, double *Y, cudaStream_t s) {
+// nonlinear = true: the cycle is a nonlinear solver's update (pMG solver, pMG stage
+// solver), whose X may not be scaled
+static int pmg_apply(fr_ctx *C, const double *q, const double *Rq, const double *X, double *Y, cudaStream_t s,
+                     bool nonlinear = false) {
     long long n = C->L[0].ndof;
-    if (C->pmg_prec == 0) {
+    if (C->pmg_prec == 0 && (!C->scale64 || nonlinear)) {
         PmgBuf<double> &P = C->p64;
         frk64_copy(n, q, P.qh[0], s);
         TRY(vcycle_t<double>(C, 0, q, Rq, X, P.qh[0], s));
         frk64_sub(n, P.qh[0], q, Y, s);
+        CKLAUNCH();
+        return FR_OK;
+    }
+    if (C->pmg_prec == 0) {
+        // the FP64 cycle driven like the FP32 one: X scaled so that the correction is about
+        // kMixedAlpha of the state per variable, the result scaled back (for states whose
+        // magnitude dwarfs a unit-norm Krylov vector, e.g. p ~ 1/(gamma Ma^2) at low Mach,
+        // where an unscaled correction is lost in the rounding of R(q + Y) - R(q))
+        PmgBuf<double> &P = C->p64;
+        int rc_x = C->has_comm ? frk32_absmax_owned(n / C->E, C->E, C->comm.n_owned, X, C->xmax, s)
+                               : frk32_absmax(n, X, C->xmax, s);
+        if (rc_x != 0) return fail(FR_ERR_CUDA, "absmax");
+        TRY(allreduce_dev(C, C->xmax, 1, 1, s));
+        double xm;
+        CK(cudaMemcpyAsync(&xm, C->xmax, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!(xm > 0.0) || !isfinite(xm)) return fail(FR_ERR_NONFINITE, "preconditioner input max %g", xm);
+        double want = kMixedAlpha, target = want / C->pmg_gain;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            if (attempt) target = want / C->pmg_gain;
+            frk64_scale(n, target / xm, X, C->x64s, s);
+            frk64_copy(n, q, P.qh[0], s);
+            TRY(vcycle_t<double>(C, 0, q, Rq, C->x64s, P.qh[0], s));
+            frk64_sub(n, P.qh[0], q, Y, s);
+            int rc_y = C->has_comm ? frk32_absmax_var_owned(C->nv, C->L[0].np, C->E, C->comm.n_owned, Y, C->ymax, s)
+                                   : frk32_absmax_var(C->nv, n / C->nv, Y, C->ymax, s);
+            if (rc_y != 0) return fail(FR_ERR_CUDA, "absmax");
+            TRY(allreduce_dev(C, C->ymax, C->nv, 1, s));
+            double yv[5], ym = 0.0;
+            CK(cudaMemcpyAsync(yv, C->ymax, sizeof(double) * C->nv, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int v = 0; v < C->nv; ++v) ym = fmax(ym, yv[v] / C->pmg_qref[v]);
+            if (!(ym > 0.0) || !isfinite(ym)) break;
+            C->pmg_gain = ym / target;
+            if (ym <= want * kMixedSlack && ym >= want / kMixedSlack) break;
+        }
+        frk64_scale(n, xm / target, Y, Y, s);
         CKLAUNCH();
         return FR_OK;
     }
@@ -1648,7 +1714,7 @@ extern "C" int esdirk_step(fr_ctx *C, const fr_esdirk_tableau *tab, double dt, d
             NvtxRange nv_upd("pseudo-time update");
             frk64_neg(n, F, F, s);
             if (o->nonlinear == 1) {
-                TRY(pmg_apply(C, q, Rk, F, dq, s));       // one V-cycle of the stage's pseudo-time equation
+                TRY(pmg_apply(C, q, Rk, F, dq, s, true));   // one V-cycle of the stage's pseudo-time equation
             } else {
                 fr_gmres_stats gs;
                 TRY(gmres(C, q, Rk, F, dq, &go, &gs, s));
@@ -1777,7 +1843,7 @@ extern "C" int ptc_steady(fr_ctx *C, double *q, double dtau_init, double dtau_ma
         // 1/dtau -> 0 the element blocks grow too ill-conditioned for FP32 LU, so the rest of
         // the pseudo-time march takes the FP64 cycle
         stall = rn > 0.9 * rk ? stall + 1 : 0;
-        if (prec == 1 && o->use_pmg && ((gs.iters >= o->maxit_gmres && rn > 0.5 * rk) || stall >= 5)) {
+        if (prec == 1 && o->use_pmg && !C->no_fallback && ((gs.iters >= o->maxit_gmres && rn > 0.5 * rk) || stall >= 5)) {
             prec = 0;
             loc.prec_switch_it = k + 1;
         }
@@ -1923,7 +1989,7 @@ extern "C" int pmg_solve_steady(fr_ctx *C, double *q, double dtau_init, double d
         po.precision = 0;
         coarse_opts_copy(o, &po);
         TRY(pmg_setup_(C, q, &po, s));
-        TRY(pmg_apply(C, q, R, R, Y, s));
+        TRY(pmg_apply(C, q, R, R, Y, s, true));
         frk64_add(n, q, Y, q, s);
         TRY(residual(C, 0, q, R, s));
         double rn;

@@ -320,6 +320,41 @@ def test_pmg_precondition_mixed_vs_fp64_oracle(case):
     assert relerr(Y_gpu, Y_or) <= tol
 
 
+def test_pmg_precondition_scaled_fp64_vs_oracle(case):
+    """The FP64 cycle driven with a scaled X (fr_set_cycle_scaling): the oracle's cycle at
+    the same scale, 1e-10 (the scale factors round differently on the two sides)."""
+    O, G, q = case["O"], case["G"], case["q"]
+    if case["mesh"]["E"] > 128:
+        pytest.skip("oracle pMG on the small meshes only")
+    nl = len(case["levels"])
+    nsm = [2, 2, 5][:nl]
+    dt = 0.3
+    c = 1.0 / dt + 1.0 / (0.4358665215084590 * dt)
+    Rq = O.residual(q)
+    X = np.random.default_rng(13).standard_normal(q.shape)
+    X /= np.linalg.norm(X)
+    qref = np.abs(q).max(axis=(1, 2))
+    qref = np.maximum(qref, 1e-3 * qref.max())
+    want, gain = 1e-2, 1.0 / ((c + 1.0 / dt) * qref.min())
+    O.pmg_setup(q, nsm, c, 1.0 / dt)
+    for attempt in range(2):
+        target = want / gain
+        s = target / np.abs(X).max()
+        Y_or = O.pmg_apply(q, Rq, s * X)
+        ym = (np.abs(Y_or).max(axis=(1, 2)) / qref).max()
+        gain = ym / target
+        if want / 30 <= ym <= want * 30:
+            break
+    Y_or = Y_or / s
+    api.fr_set_cycle_scaling(G, True)
+    try:
+        api.pmg_setup(G, dev(q), nsm, c, 1.0 / dt, precision="fp64")
+        Y_gpu = api.pmg_precondition(G, dev(q), dev(Rq), dev(X))
+    finally:
+        api.fr_set_cycle_scaling(G, False)
+    assert relerr(Y_gpu, Y_or) <= 1e-10
+
+
 def test_esdirk_step_mixed_converged_state():
     """The converged implicit step does not depend on the preconditioner's precision."""
     mesh = w.box2d(4, 4, 10, 10, qg=2, warp=0.1)
