@@ -203,6 +203,26 @@ int fr_block_to_half(fr_ctx *ctx, int level, const float *M, void *H, float *dg,
  * fr_block_factor_f32 */
 int fr_block_solve_half(fr_ctx *ctx, int level, const void *H, const float *dg, const int *perm, float *x,
                         void *stream);
+/* ------------------------------------------------------------------ p-adaptation
+ * Sec. 3.3: the spectral-decay smoothness indicator eta_e = ||s_p - s_{p-1}|| / ||s_p||
+ * (L2 norms on the reference element) of variable var (the paper's default: 1, the
+ * x-momentum) of the level state q (device FP64 [nv][Np][E]), per element into eta
+ * (device, E doubles): s_p's expansion in tensor products of orthonormal Legendre
+ * polynomials, s_{p-1} the modes whose largest index is below p, so eta_e^2 is the
+ * energy of the others over all; 0 for s = 0.  FR_ERR_UNIMPLEMENTED beyond p = 5 (2-D)
+ * or p = 4 (3-D). */
+int fr_spectral_decay(fr_ctx *ctx, int level, const double *q, int var, double *eta, void *stream);
+/* Sec. 3.3 marking rule: p_out[e] = p_in[e] + 1 where eta_e > nu_max max(eta) (if below
+ * p_max), p_in[e] - 1 where eta_e < nu_min max(eta) (if above p_min), else p_in[e]; the
+ * paper takes nu_max = 0.2, nu_min = 1e-3, p_min = 1.  eta, p_in, p_out: device, E each. */
+int fr_padapt_mark(fr_ctx *ctx, const double *eta, const int *p_in, int p_min, int p_max, double nu_min,
+                   double nu_max, int *p_out, void *stream);
+/* Sec. 3.3 nested p-hierarchy of an element of degree p over nlevels sublevels with order
+ * gap: degrees[0] = p, degrees[l] = min(max(p - gap l, nlevels - 1 - l), max(degrees[l-1]
+ * - 1, 0)) (host; this rule reproduces the paper's eight examples, e.g. gap 2: p{4-2-0},
+ * p{3-1-0}, p{2-1-0}, p{1-0-0}). */
+int fr_nested_hierarchy(int p_elem, int gap, int nlevels, int *degrees);
+
 /* 1: the FP64 preconditioner cycle (pmg_setup precision 0, as used by FGMRES) is driven
  * like the FP32 one: X scaled so that the correction is about 1e-2 of the state per
  * variable, the result scaled back (a nonlinear preconditioner; FGMRES allows it).  For

@@ -19,7 +19,7 @@ ERRORS = {-1: "FR_ERR_INVALID_ARG", -2: "FR_ERR_CUDA", -3: "FR_ERR_OOM", -4: "FR
 # every symbol the header declares
 EXPORTS = ["fr_create", "fr_destroy", "fr_last_error", "fr_kernel_launches", "fr_level_info", "fr_num_colors", "fr_residual",
            "fr_residual_noalloc", "fr_jvp",
-           "fr_elem_blocks", "fr_elem_blocks_f32", "fr_set_block_method", "fr_set_comm", "fr_nbr_blocks", "fr_neighbour_table", "fr_mbnk_last", "fr_mbnk_operator", "fr_block_factor", "fr_block_solve", "fr_block_factor_f32", "fr_block_solve_f32", "fr_set_lu_method", "fr_block_to_half", "fr_block_solve_half", "fr_set_lu_storage", "fr_set_cycle_scaling", "fr_set_precision_fallback", "fr_restrict", "fr_prolong", "pmg_setup",
+           "fr_elem_blocks", "fr_elem_blocks_f32", "fr_set_block_method", "fr_set_comm", "fr_nbr_blocks", "fr_neighbour_table", "fr_mbnk_last", "fr_mbnk_operator", "fr_block_factor", "fr_block_solve", "fr_block_factor_f32", "fr_block_solve_f32", "fr_set_lu_method", "fr_block_to_half", "fr_block_solve_half", "fr_set_lu_storage", "fr_set_cycle_scaling", "fr_set_precision_fallback", "fr_spectral_decay", "fr_padapt_mark", "fr_nested_hierarchy", "fr_restrict", "fr_prolong", "pmg_setup",
            "pmg_precondition", "gmres_solve", "esdirk_step", "row_step", "ptc_steady",
            "mlp_create", "mlp_destroy", "mlp_get_params", "mlp_forward", "mlp_train_step", "fr_mlp_dims",
            "fr_set_mlp", "fr_reset_history", "fr_guess_features", "fr_batch_create", "fr_batch_destroy",
@@ -126,6 +126,9 @@ def load(path: str = LIB_PATH):
         "fr_block_solve_half": ([VP, C.c_int, VP, VP, VP, VP, VP], C.c_int),
         "fr_set_lu_storage": ([VP, C.c_int], C.c_int),
         "fr_set_cycle_scaling": ([VP, C.c_int], C.c_int),
+        "fr_spectral_decay": ([VP, C.c_int, VP, C.c_int, VP, VP], C.c_int),
+        "fr_padapt_mark": ([VP, VP, VP, C.c_int, C.c_int, C.c_double, C.c_double, VP, VP], C.c_int),
+        "fr_nested_hierarchy": ([C.c_int, C.c_int, C.c_int, PI], C.c_int),
         "fr_set_precision_fallback": ([VP, C.c_int], C.c_int),
         "fr_restrict": ([VP, C.c_int, VP, VP, VP], C.c_int),
         "fr_prolong": ([VP, C.c_int, VP, VP, VP], C.c_int),

@@ -214,6 +214,30 @@ def fr_block_solve_half(ctx, level, H, dg, perm, x, stream=None):
     return x
 
 
+def fr_spectral_decay(ctx, level, q, var=1, eta=None, stream=None):
+    """Sec. 3.3 spectral-decay indicator per element (device float64 [E]) of variable var."""
+    eta = torch.empty(ctx.E, dtype=torch.float64, device="cuda") if eta is None else eta
+    N.check(N.load().fr_spectral_decay(ctx.handle, int(level), _dev(q), int(var), _dev(eta, torch.float64, "eta"),
+                                       _stream(stream)), "fr_spectral_decay")
+    return eta
+
+
+def fr_padapt_mark(ctx, eta, p_in, p_min=1, p_max=4, nu_min=1e-3, nu_max=0.2, stream=None):
+    """Sec. 3.3 marking rule: the new element degrees (device int32 [E])."""
+    p_out = torch.empty_like(p_in)
+    N.check(N.load().fr_padapt_mark(ctx.handle, _dev(eta, torch.float64, "eta"), _dev(p_in, torch.int32, "p_in"),
+                                    int(p_min), int(p_max), float(nu_min), float(nu_max),
+                                    _dev(p_out, torch.int32, "p_out"), _stream(stream)), "fr_padapt_mark")
+    return p_out
+
+
+def fr_nested_hierarchy(p_elem, gap, nlevels):
+    """Sec. 3.3 nested p-hierarchy of one element (host)."""
+    out = (C.c_int * int(nlevels))()
+    N.check(N.load().fr_nested_hierarchy(int(p_elem), int(gap), int(nlevels), out), "fr_nested_hierarchy")
+    return [int(x) for x in out]
+
+
 def fr_set_cycle_scaling(ctx, on):
     """Drive the FP64 preconditioner cycle with a scaled X (as the FP32 one is)."""
     N.check(N.load().fr_set_cycle_scaling(ctx.handle, int(bool(on))), "fr_set_cycle_scaling")

@@ -10,6 +10,7 @@ Translation units:
   csrc/batch_kernels.cu  segmented (per-problem) vector kernels of the batched solver
   csrc/mbnk.cu        matrix-based Newton-Krylov smoother of the coarsest pMG level
   csrc/lu_tc.cu       batched LU of the FP32 element blocks, trailing updates on tcgen05
+  csrc/padapt.cu      p-adaptation: spectral-decay indicator and marking (Sec. 3.3)
   csrc/host_tables.c  binary128 operator tables         (gcc -ffp-contract=off)
   csrc/host_geometry.c geometric factors, connectivity  (gcc -ffp-contract=off)
 build_rates() compiles csrc/rates.cu (pipe-rate microbenchmarks) into librates.so.
@@ -50,6 +51,7 @@ def _units():
         ([nv] + common + ["-fmad=false", "-c"], "batch_kernels.cu"),
         ([nv] + common + ["-fmad=false", "-c"], "mbnk.cu"),
         ([nv] + common + ["-c"], "lu_tc.cu"),
+        ([nv] + common + ["-fmad=false", "-c"], "padapt.cu"),
         (["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC"] + inc + ["-c"], "host_tables.c"),
         (["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC"] + inc + ["-c"], "host_geometry.c"),
     ]

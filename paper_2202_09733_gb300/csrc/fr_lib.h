@@ -129,6 +129,13 @@ int frktc_lu_to_half(int E, int nd, const float *M, void *H, float *dg, cudaStre
 int frktc_lu_solve_half(int E, int nd, int g, const void *H, const float *dg, const int *perm, float *x,
                         cudaStream_t s);
 
+// p-adaptation indicator and marking (padapt.cu)
+unsigned long long frpa_launch_count();
+int frpa_upload(const double *modal /* [6][6][6]: [p][a][i] */);
+int frpa_spectral_decay(int d, int p, int E, const double *q, int var, double *eta, double *emax_dev, cudaStream_t s);
+void frpa_mark(int E, const double *eta, const double *emax_dev, const int *p_in, int p_min, int p_max,
+               double nu_min, double nu_max, int *p_out, cudaStream_t s);
+
 // segmented vector kernels of the batched solver (batch_kernels.cu)
 unsigned long long frkb_launch_count();
 int frkb_segdots(int rows, int E, int nitems, const int4 *items, int nprob, const int *item_off, const double *w,

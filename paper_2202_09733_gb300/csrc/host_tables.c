@@ -23,6 +23,12 @@
 
 typedef _Float128 Q;
 
+static Q sqrtq_(Q v) {
+    Q r = (Q)sqrt((double)v);
+    for (int it = 0; it < 3; ++it) r = (r + v / r) / 2;
+    return r;
+}
+
 static double to_d(Q v) {
     double d = (double)v;
     return fabs(d) < 1e-25 ? 0.0 : d;
@@ -163,6 +169,30 @@ void frh_make_transfer(int p0, int p1, double Gam[FRH_MAXN][FRH_MAXN], double Pi
         for (int i = 0; i < n1; ++i) {
             Gam[i][j] = to_d(w0[j] * val[i] / w1[i]);
             Pi[j][i] = to_d(val[i]);
+        }
+    }
+}
+
+/* Sec. 3.3 spectral-decay indicator: M[a][i] = w_i phi_a(x_i), phi_a = sqrt((2a + 1)/2) P_a
+ * the orthonormal Legendre polynomials, so that sum_i M[a][i] s_i is the coefficient of
+ * phi_a in the degree-p polynomial through the nodal values s (the (p+1)-point rule is
+ * exact for the products). */
+void frh_modal(int p, double M[FRH_MAXN][FRH_MAXN]) {
+    int n = p + 1;
+    Q x[FRH_MAXN], w[FRH_MAXN];
+    gauss_nodes(n, x, w);
+    memset(M, 0, sizeof(double) * FRH_MAXN * FRH_MAXN);
+    for (int i = 0; i < n; ++i) {
+        Q P0 = 1, P1 = x[i];
+        for (int a = 0; a < n; ++a) {
+            Q Pa;
+            if (a == 0) Pa = 1;
+            else if (a == 1) Pa = x[i];
+            else {
+                Q P2 = ((Q)(2 * a - 1) * x[i] * P1 - (Q)(a - 1) * P0) / (Q)a;
+                P0 = P1; P1 = P2; Pa = P2;
+            }
+            M[a][i] = to_d(w[i] * sqrtq_((Q)(2 * a + 1) / 2) * Pa);
         }
     }
 }

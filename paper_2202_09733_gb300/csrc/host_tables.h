@@ -21,6 +21,8 @@ typedef struct {
 
 void frh_make_tables(int p, int g, frh_tab *T);
 void frh_make_transfer(int p0, int p1, double Gam[FRH_MAXN][FRH_MAXN], double Pi[FRH_MAXN][FRH_MAXN]);
+/* M[a][i] = w_i phi_a(x_i): nodal values -> orthonormal Legendre coefficients (degree p) */
+void frh_modal(int p, double M[FRH_MAXN][FRH_MAXN]);
 
 /* geometric factors of one level: S, G [d][d][np][E]; invJ, Jdet [np][E];
  * Sf, Gf [d][d][nfp][E]  (arrays allocated by the caller) */

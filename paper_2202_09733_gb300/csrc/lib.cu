@@ -113,6 +113,7 @@ struct fr_ctx {
     int scale64;                  // the FP64 cycle driven with a scaled X, as the FP32 cycle is
     int no_fallback;              // ptc_steady: keep the FP32 cycle when it stalls
     double *x64s;                 // the scaled FP64 cycle's right-hand side
+    double *pa_max;               // max of the spectral-decay indicators (device)
     float *lu_scr;                // tensor-core LU: each phase's split L21 operand
     size_t lu_scr_cap;
     float *ad_nt;                 // element-local FP32 blocks: the other sides' frozen face data
@@ -193,7 +194,7 @@ static std::atomic<unsigned long long> g_capture_kernels{0};  // launch-counter 
 
 extern "C" unsigned long long fr_kernel_launches(void) {
     return frk64_launch_count() + frk32_launch_count() + frkad_launch_count() + frkmlp_launch_count() +
-           frkb_launch_count() + frmb_launch_count() + frktc_launch_count() - g_capture_kernels + g_graph_kernels;
+           frkb_launch_count() + frmb_launch_count() + frktc_launch_count() + frpa_launch_count() - g_capture_kernels + g_graph_kernels;
 }
 
 // ---------------------------------------------------------------- context set-up
@@ -220,8 +221,17 @@ static int upload_tables() {
             memcpy(pi[p][p1], P, sizeof P);
         }
     }
+    static double modal[6][6][6];
+    memset(modal, 0, sizeof modal);
+    for (int p = 0; p <= 5; ++p) {
+        double Mp[FRH_MAXN][FRH_MAXN];
+        frh_modal(p, Mp);
+        for (int a = 0; a <= p; ++a)
+            for (int i = 0; i <= p; ++i) modal[p][a][i] = Mp[a][i];
+    }
     if (frk64_upload_tables(tabs, &gam[0][0][0][0], &pi[0][0][0][0]) != 0 ||
-        frk32_upload_tables(tabs, &gam[0][0][0][0], &pi[0][0][0][0]) != 0 || frkad_upload_tables(tabs) != 0)
+        frk32_upload_tables(tabs, &gam[0][0][0][0], &pi[0][0][0][0]) != 0 || frkad_upload_tables(tabs) != 0 ||
+        frpa_upload(&modal[0][0][0]) != 0)
         return fail(FR_ERR_CUDA, "uploading operator tables: %s", cudaGetErrorString(cudaGetLastError()));
     return FR_OK;
 }
@@ -840,6 +850,44 @@ extern "C" int fr_block_factor(fr_ctx *C, int l, double *M, int *perm, void *str
 extern "C" int fr_set_lu_method(fr_ctx *C, int method) {
     if (!C || method < 0 || method > 1) return fail(FR_ERR_INVALID_ARG, "method must be 0 or 1");
     C->lu_method = method;
+    return FR_OK;
+}
+
+// ------------------------------------------------------------- p-adaptation
+extern "C" int fr_spectral_decay(fr_ctx *C, int l, const double *q, int var, double *eta, void *stream) {
+    if (!C || l < 0 || l >= C->nlev || !q || !eta) return fail(FR_ERR_INVALID_ARG, "bad argument");
+    if (var < 0 || var >= C->nv) return fail(FR_ERR_INVALID_ARG, "variable %d outside 0..%d", var, C->nv - 1);
+    if (!C->pa_max) TRY(dalloc_t(C, &C->pa_max, 1));
+    const FrLevel &L = C->L[l];
+    if (frpa_spectral_decay(L.d, L.p, L.E, q, var, eta, C->pa_max, S_(stream)) != 0)
+        return fail(FR_ERR_UNIMPLEMENTED, "spectral-decay indicator for d = %d, p = %d", L.d, L.p);
+    CKLAUNCH();
+    return FR_OK;
+}
+
+extern "C" int fr_padapt_mark(fr_ctx *C, const double *eta, const int *p_in, int p_min, int p_max, double nu_min,
+                              double nu_max, int *p_out, void *stream) {
+    if (!C || !eta || !p_in || !p_out) return fail(FR_ERR_INVALID_ARG, "NULL argument");
+    if (p_min < 0 || p_max < p_min || !(nu_min >= 0.0) || !(nu_max >= nu_min))
+        return fail(FR_ERR_INVALID_ARG, "need 0 <= p_min <= p_max and 0 <= nu_min <= nu_max");
+    if (!C->pa_max) TRY(dalloc_t(C, &C->pa_max, 1));
+    cudaStream_t s = S_(stream);
+    // max(eta) of the given indicators (not necessarily the last fr_spectral_decay's)
+    if (frk32_absmax(C->E, eta, C->pa_max, s) != 0) return fail(FR_ERR_CUDA, "max");
+    frpa_mark(C->E, eta, C->pa_max, p_in, p_min, p_max, nu_min, nu_max, p_out, s);
+    CKLAUNCH();
+    return FR_OK;
+}
+
+extern "C" int fr_nested_hierarchy(int p_elem, int gap, int nlevels, int *degrees) {
+    if (p_elem < 0 || gap < 1 || nlevels < 1 || nlevels > FRL_MAXLEV || !degrees)
+        return fail(FR_ERR_INVALID_ARG, "need p >= 0, gap >= 1, 1 <= nlevels <= %d", FRL_MAXLEV);
+    degrees[0] = p_elem;
+    for (int l = 1; l < nlevels; ++l) {
+        int a = p_elem - gap * l, b = nlevels - 1 - l, c = degrees[l - 1] - 1;
+        int lo = a > b ? a : b, hi = c > 0 ? c : 0;
+        degrees[l] = lo < hi ? lo : hi;
+    }
     return FR_OK;
 }
 
