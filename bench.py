@@ -6,9 +6,12 @@ affine hexes (2.1 M solution points x 5 variables), Taylor-Green field plus seed
 Fourier noise (modes <= 4, amplitude 1e-3), Ma = 0.1, Re = 1600.  One step = one
 ROS34PW2 step (dt = 20x the explicit limit) with the nonlinear pMG p{3-2} n{2-2}
 preconditioner (element blocks and their LU evaluated at q^n inside the step, as the
-paper does once per physical step) and FGMRES(30) to the paper's ROW tolerance 1e-6,
-all FP64.  Inputs are larger than L2 (84 MB state, 31 GB of element blocks), so no L2
-flush is needed between steps.
+paper does once per physical step) and FGMRES(30) to the paper's ROW tolerance 1e-6:
+FP64 residual, Jv, Gram-Schmidt and update; the preconditioner's cycle, blocks and LU in
+FP32 (the LU's trailing updates on the tensor cores), its block solves from factors
+stored as binary16 with FP32 column scales (--lu-storage fp32 keeps them FP32).  The
+plain FP64 step is timed beside it.  Inputs are larger than L2 (84 MB state, 13 GB of
+FP32 element blocks), so no L2 flush is needed between steps.
 
 Output: one JSON line with the step wall time (value), the FP64 residual throughput
 (GDOF/s), the roofline of the residual, the end-to-end time through host buffers, the
@@ -68,8 +71,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ESDIRK3 initial-guess comparison (cylinder) and the batched step")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--lu-storage", default="fp32", choices=["fp32", "half"],
-                    help="mixed preconditioner: the smoother's block solves read FP32 factors or half-width ones")
+    ap.add_argument("--lu-storage", default="half", choices=["fp32", "half"],
+                    help="mixed preconditioner: the smoother's block solves read half-width factors (binary16 "
+                         "with FP32 column scales: TF32's 10-bit mantissa) or FP32 ones")
     return ap.parse_args()
 
 
@@ -81,6 +85,43 @@ def hbm_peak():
             return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy, burst)"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+def half_solve_roofline(api, torch, ctx, q0, c, E, nd, reps=10):
+    """Roofline of the step's dominant kernel with half-width factors, the fine-level
+    block solve k_lu_solve_half: the level's FP32 blocks at q0 (shift c), factored and
+    converted as pmg_setup does, one application timed with CUDA events on the stream it
+    runs on (the mean of reps, after one warm-up), against its algorithmic bytes: the
+    binary16 factors (nd x ldh per block), the (1/u_kk, g_k) pairs, the permutation and the
+    vector read and written."""
+    M = api.fr_elem_blocks_f32(ctx, 0, q0.float().contiguous(), c)
+    perm = api.fr_block_factor_f32(ctx, 0, M)
+    H, dg = api.fr_block_to_half(ctx, 0, M)
+    del M
+    x = torch.randn((nd, E), device="cuda", dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+    api.fr_block_solve_half(ctx, 0, H, dg, perm, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        api.fr_block_solve_half(ctx, 0, H, dg, perm, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1) / reps
+    ldh = H.shape[2]
+    algo = E * nd * ldh * 2 + E * nd * 8 + E * nd * 4 + 2 * E * nd * 4
+    peak, src = hbm_peak()
+    t16 = profile_figure("lu_solve_half_tgv3d16", "dram_bytes_per_launch_half")
+    del H, dg
+    return {"kernel": f"k_lu_solve_half (fine-level block solve from binary16 factors, {E} blocks of {nd}x{nd}, "
+                      "one application)",
+            "bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": src, "algorithmic_bytes": algo,
+            "achieved": algo / (t_ms * 1e-3) / 1e9, "frac": algo / (t_ms * 1e-3) / 1e9 / peak, "ms_per_launch": t_ms,
+            "traffic": t16 * E / 4096 if t16 else None,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on tgv3d 16^3 "
+                              "(4096 elements), scaled by the element count (committed ncu summary)",
+            "share_of_step": "the largest kernel family of the mixed step (committed launch list)"}
 
 
 def solve_roofline(tune, E, nd):
@@ -421,6 +462,29 @@ def steady_lowmach(api, w, np, torch, max_it=150):
     return out
 
 
+def padapt_indicator(api, w, np, torch):
+    """The p-adaptation indicator and marking (Sec. 3.3) on the 32^3 Taylor-Green state
+    (p = 3, x-momentum): the marking the paper's rule (nu_max 0.2, nu_min 1e-3, p in
+    [1, 4]) makes, and the indicator's time per launch (CUDA events, 20 launches)."""
+    W = w.tgv3d(n=32)
+    G = api.fr_create(W.mesh, W.phys, W.levels)
+    q = torch.from_numpy(np.ascontiguousarray(W.q0)).cuda()
+    eta = api.fr_spectral_decay(G, 0, q, var=1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        api.fr_spectral_decay(G, 0, q, var=1, eta=eta)
+    e1.record()
+    torch.cuda.synchronize()
+    p_in = torch.full((G.E,), 3, dtype=torch.int32, device="cuda")
+    p_out = api.fr_padapt_mark(G, eta, p_in, 1, 4).cpu().numpy()
+    e = eta.cpu().numpy()
+    return {"workload": "tgv3d 32^3 p=3 initial state, indicator of rho u", "ms_per_launch": e0.elapsed_time(e1) / 20,
+            "eta_max": float(e.max()), "eta_median": float(np.median(e)),
+            "raised": int((p_out > 3).sum()), "kept": int((p_out == 3).sum()), "lowered": int((p_out < 3).sum())}
+
+
 def run_extras_in_child():
     """The ESDIRK guess comparison and the batched step, in a child process of their own
     (a clean library state, and a failure there cannot take the main measurement down)."""
@@ -429,7 +493,8 @@ def run_extras_in_child():
             "torch.cuda.set_device(0); "
             "out = {'esdirk_cylinder': bench.esdirk_guess_compare(api, w, T, np, torch), "
             "'batched_vortex': bench.batched_step(api, w, T, np, torch, N), "
-            "'steady_lowmach_cylinder': bench.steady_lowmach(api, w, np, torch)}; "
+            "'steady_lowmach_cylinder': bench.steady_lowmach(api, w, np, torch), "
+            "'padapt_indicator': bench.padapt_indicator(api, w, np, torch)}; "
             "print('EXTRAS ' + json.dumps(out))") % ROOT
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
     for line in r.stdout.splitlines():
@@ -517,6 +582,22 @@ def gpu_arm(args):
 
     q_mixed = q.clone()
 
+    # ---- the same mixed step with FP32 factors for the smoother's solves (the other storage)
+    t_other = None
+    if args.precision != "fp64" and part is None:
+        other = "fp32" if args.lu_storage == "half" else "half"
+        api.fr_set_lu_storage(ctx, other)
+        step()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        st_other = step()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        t_other = {"lu_storage": other, "s_per_step": g0.elapsed_time(g1) / 1e3,
+                   "gmres_iterations": st_other["n_gmres"]}
+        api.fr_set_lu_storage(ctx, args.lu_storage)
+
     # ---- the plain FP64 JFNK-pMG step on the same input, for comparison
     t_fp64, st64, dq = None, None, None
     if args.precision != "fp64" and not args.no_fp64_compare:
@@ -570,6 +651,11 @@ def gpu_arm(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_baseline_in_child()
 
+    roof = roof32 = solve_roofline(tune, E, 5 * 64)
+    if rank == 0 and args.lu_storage == "half" and args.precision != "fp64" and part is None:
+        cshift = 1.0 / W.dt + 1.0 / (0.4358665215084590 * W.dt)
+        roof = half_solve_roofline(api, torch, ctx, q0, cshift, E, 5 * 64)
+
     if rank == 0:
         ng = [s_["n_gmres"] for s_ in stats]
         line = {
@@ -581,8 +667,12 @@ def gpu_arm(args):
             "config": {"workload": f"tgv3d {args.n}^3 hex p=3 (Ma 0.1, Re 1600), ROS34PW2 step dt=20x explicit, "
                                    "pMG p{3-2} n{2-2} (blocks + LU at q^n inside the step), FGMRES(30) tol 1e-6",
                        "precision": ("FP64 throughout" if args.precision == "fp64" else
-                                     "mixed: FP64 residual, Jv, Gram-Schmidt, update; FP32 pMG cycle, blocks, LU"),
-                       "ndof": ndof, "elements": E, "l2": "inputs larger than L2 (state 84 MB, blocks 31 GB): no flush",
+                                     "mixed: FP64 residual, Jv, Gram-Schmidt, update; FP32 pMG cycle, blocks, LU "
+                                     "(tensor-core trailing updates)" +
+                                     ("; the smoother's block solves read the factors stored as binary16 with FP32 "
+                                      "column scales (TF32's 10-bit mantissa), FP32 arithmetic"
+                                      if args.lu_storage == "half" else "; FP32 factors")),
+                       "ndof": ndof, "elements": E, "l2": "inputs larger than L2 (state 84 MB, FP32 blocks 13 GB): no flush",
                        "parallelism": (f"element partition over {ws} GPUs (recursive bisection, one ghost "
                                        "layer; ghost exchange and inner-product sums over NCCL)") if ws > 1
                                       else "single GPU"},
@@ -593,7 +683,9 @@ def gpu_arm(args):
             "residual_gdofs": gdofs,
             "residual_ms": t_R * 1e3,
             "gmres_iterations_per_step": statistics.mean(ng),
-            "roofline": solve_roofline(tune, E, 5 * 64),
+            "roofline": roof,
+            "roofline_fp32_solve": roof32 if args.lu_storage == "half" else None,
+            "other_lu_storage_step": t_other,
             "roofline_residual": {"kernel": "fr_residual (FP64 FR residual, 7 kernels per launch)", "bound": "alu",
                          "achieved": flops / t_R / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
                          "frac": (flops / t_R) / FP64_PEAK_NOMINAL,

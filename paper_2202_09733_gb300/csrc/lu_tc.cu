@@ -567,8 +567,9 @@ __global__ void __launch_bounds__(128) k_lu_solve_half(const __half *__restrict_
 template <int NR2>
 static void solve_half_nr(int g, int grid, const __half *H, const float2 *dg, const int *perm, float *x, int nd,
                           int ldh, int E, cudaStream_t s) {
-    if (g >= 8) k_lu_solve_half<NR2, 8><<<grid, 128, 0, s>>>(H, dg, perm, x, nd, ldh, E);
-    else if (g >= 4) k_lu_solve_half<NR2, 4><<<grid, 128, 0, s>>>(H, dg, perm, x, nd, ldh, E);
+    // 8 columns in flight is the slowest on every level measured (register pressure):
+    // the FP32 solve's choice 8 becomes 4 here
+    if (g >= 4) k_lu_solve_half<NR2, 4><<<grid, 128, 0, s>>>(H, dg, perm, x, nd, ldh, E);
     else k_lu_solve_half<NR2, 2><<<grid, 128, 0, s>>>(H, dg, perm, x, nd, ldh, E);
 }
 
@@ -630,7 +631,7 @@ int frktc_lu_to_half(int E, int nd, const float *M, void *H, float *dg, cudaStre
     return 0;
 }
 
-// g: columns in flight (2, 4, 8; 0 or 1: the default, 4)
+// g: columns in flight (2 or 4; 8 is taken as 4; 0 or 1: the default, 4)
 int frktc_lu_solve_half(int E, int nd, int g, const void *H, const float *dg, const int *perm, float *x,
                         cudaStream_t s) {
     int nr2 = (nd + 63) / 64, grid = (E * 32 + 127) / 128, ldh = frktc_half_ld(nd);

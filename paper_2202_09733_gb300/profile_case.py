@@ -29,6 +29,8 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=32, help="tgv3d: elements per direction")
     ap.add_argument("--op", default="residual",
                     choices=["residual", "residual32", "jvp", "pmg", "row_step", "esdirk_step", "lu_factor"])
+    ap.add_argument("--lu-storage", default="fp32", choices=["fp32", "half"],
+                    help="mixed preconditioner: the smoother's solves from FP32 or half-width factors")
     ap.add_argument("--lu", default="auto", choices=["auto", "cuda_cores", "tensor_cores"],
                     help="lu_factor: the FP32 factorisation of the fine level's element blocks")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
@@ -45,6 +47,7 @@ def main(argv=None):
     else:
         W = w.vortex2d()
     ctx = api.fr_create(W.mesh, W.phys, W.levels)
+    api.fr_set_lu_storage(ctx, a.lu_storage)
     if a.autotune:
         api.fr_autotune(ctx, fp64=True, fp32=True, reps=3)
     if a.solve_g:
