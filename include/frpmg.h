@@ -200,7 +200,7 @@ int fr_set_lu_method(fr_ctx *ctx, int method);
  * column's scale, an absolute one up to 2^-25 of it). */
 int fr_block_to_half(fr_ctx *ctx, int level, const float *M, void *H, float *dg, void *stream);
 /* x <- M_e^{-1} x with the half-width factors (x device FP32 [nv][Np][E]); perm as from
- * fr_block_factor_f32 */
+ * fr_block_factor_f32.  FR_ERR_UNIMPLEMENTED for blocks of more than 384 rows. */
 int fr_block_solve_half(fr_ctx *ctx, int level, const void *H, const float *dg, const int *perm, float *x,
                         void *stream);
 /* ------------------------------------------------------------------ p-adaptation
@@ -236,8 +236,9 @@ int fr_set_cycle_scaling(fr_ctx *ctx, int on);
  * five pseudo steps in a row each gained less than 10%); 0 keeps the FP32 cycle. */
 int fr_set_precision_fallback(fr_ctx *ctx, int on);
 /* 1: pmg_setup also stores the mixed preconditioner's FP32 factors at half width and the
- * smoother's block solves read those (half the bytes per solve); 0 (the default): FP32
- * factors.  Takes effect at the next pmg_setup. */
+ * smoother's block solves read those (half the bytes per solve; levels whose blocks have
+ * more than 384 rows keep FP32 factors); 0 (the default): FP32 factors.  Takes effect at
+ * the next pmg_setup. */
 int fr_set_lu_storage(fr_ctx *ctx, int half);
 
 /* Eqs. (17)-(18): L2 restriction level -> level+1 and prolongation level+1 -> level,

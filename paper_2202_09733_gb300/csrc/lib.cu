@@ -788,7 +788,9 @@ static int tc_scratch(fr_ctx *C, int E, int nd) {
 }
 static int tc_factor(fr_ctx *C, int l, float *M, int *perm, cudaStream_t s) {
     TRY(tc_scratch(C, C->L32[l].E, C->L32[l].nd));
-    frktc_lu_factor(C->L32[l].E, C->L32[l].nd, M, perm, C->info, C->lu_scr, s);
+    if (frktc_lu_factor(C->L32[l].E, C->L32[l].nd, M, perm, C->info, C->lu_scr, s) != 0)
+        return fail(FR_ERR_UNIMPLEMENTED, "tensor-core LU: %d blocks of %d rows exceed its launch grid",
+                    C->L32[l].E, C->L32[l].nd);
     return FR_OK;
 }
 static int tc_factor(fr_ctx *, int, double *, int *, cudaStream_t) { return FR_OK; }
@@ -797,8 +799,8 @@ static int tc_factor(fr_ctx *, int, double *, int *, cudaStream_t) { return FR_O
 static int half_factors(fr_ctx *C, int l, const float *M, cudaStream_t s) {
     PmgBuf<float> &P = C->p32;
     P.half_ok[l] = 0;
-    if (!C->lu_half) return FR_OK;
     const FrLevel32 &L = C->L32[l];
+    if (!C->lu_half || (L.nd + 63) / 64 > 6) return FR_OK;   // blocks over 384 rows keep FP32 factors
     size_t need = (size_t)L.E * L.nd * frktc_half_ld(L.nd);
     if (!P.H[l] || P.H_cap[l] < need) {
         dfree(C, P.H[l]);
@@ -940,8 +942,12 @@ extern "C" int fr_block_factor_f32(fr_ctx *C, int l, float *M, int *perm, int me
         return fail(FR_ERR_UNIMPLEMENTED, "tensor-core LU: block size %d outside 65..384", L.nd);
     if (tc) TRY(tc_scratch(C, L.E, L.nd));
     CK(cudaMemsetAsync(C->info, 0, sizeof(int), s));
-    if (tc) frktc_lu_factor(L.E, L.nd, M, perm, C->info, C->lu_scr, s);
-    else frk32_lu_factor(L, M, perm, C->info, s);
+    if (tc) {
+        if (frktc_lu_factor(L.E, L.nd, M, perm, C->info, C->lu_scr, s) != 0)
+            return fail(FR_ERR_UNIMPLEMENTED, "tensor-core LU: %d blocks of %d rows exceed its launch grid", L.E, L.nd);
+    } else {
+        frk32_lu_factor(L, M, perm, C->info, s);
+    }
     CKLAUNCH();
     int info = 0;
     CK(cudaMemcpyAsync(&info, C->info, sizeof(int), cudaMemcpyDeviceToHost, s));
