@@ -15,10 +15,10 @@ FP32 element blocks), so no L2 flush is needed between steps.
 
 Output: one JSON line with the step wall time (value), the FP64 residual throughput
 (GDOF/s), the roofline of the residual, the end-to-end time through host buffers, the
-oracle baseline on this machine's host cores, the kernel-launch count and the SM clocks.
+oracle baseline on the host cores, the kernel-launch count and the SM clocks.
 
---impl reference times the FP64 CPU oracle (the reference arm of this build) on a
-bounded sample of the same workload (an 8^3 slice at the same CFL on all host cores,
+--impl reference times the FP64 CPU oracle (the method has no other implementation to
+compare with) on a bounded sample of the same workload (an 8^3 slice at the same CFL on all host cores,
 scaled to 32^3 by the element count).
 """
 from __future__ import annotations
